@@ -1,0 +1,135 @@
+"""Pins of the oracle's eigensolvers: Jacobi against LAPACK and a 2x2 closed
+form; block LOBPCG (Algorithm 1 with the block constraint and the final
+Rayleigh-Ritz) against dense diagonalisation, Courant-Fischer bounds and its
+special cases m = M and m = 1 (the single-band method of Eq. 2)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis, checks, hamiltonian, jacobi, lobpcg
+
+
+def _rand_herm(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return A + A.conj().T
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 40])
+def test_jacobi_matches_lapack(n):
+    A = _rand_herm(n, n)
+    w, V = jacobi.jacobi_eigh(A)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * max(1.0, np.abs(A).max())
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() < 1e-13
+    assert np.abs(A @ V - V * w[None, :]).max() < 1e-12 * max(1.0, np.abs(A).max())
+
+
+def test_jacobi_2x2_closed_form():
+    a, d, b = 0.3, -1.1, 0.4 - 0.7j
+    w, _ = jacobi.jacobi_eigh(np.array([[a, b], [np.conj(b), d]]))
+    r = np.sqrt(((a - d) / 2) ** 2 + abs(b) ** 2)
+    assert np.allclose(w, [(a + d) / 2 - r, (a + d) / 2 + r], atol=1e-15)
+
+
+def test_jacobi_on_dense_hamiltonian():
+    w = synth.tiny_workload(a=5.0, N=8, natoms=1)
+    H = hamiltonian.for_workload(w)
+    Hd = H.dense()
+    ev, _ = jacobi.jacobi_eigh(Hd)
+    assert np.abs(ev - np.linalg.eigvalsh(Hd)).max() < 1e-12
+
+
+def _tiny(kpt=(0.0, 0.0, 0.0), nb=8, m=4, seed=11):
+    w = synth.tiny_workload(a=6.0, N=12, natoms=2, kpt=kpt, nbands=nb, block=m, seed=seed)
+    H = hamiltonian.for_workload(w)
+    return w, H
+
+
+@pytest.mark.parametrize("kpt", [(0.0, 0.0, 0.0), (0.25, 0.125, -0.375)])
+def test_lobpcg_matches_dense(kpt):
+    w, H = _tiny(kpt)
+    ref = np.linalg.eigvalsh(H.dense())[:8]
+    r = lobpcg.solve(H, w.x0(H.npw), block=4, nline=4, tol=1e-10)
+    assert r.converged
+    assert np.abs(r.eig - ref).max() < 1e-10
+    assert checks.orthonormality_error(r.X) < 1e-12
+    assert checks.residuals(H, r.X, r.eig).max() < 1e-10
+
+
+def test_lobpcg_single_block_is_plain_rayleigh_ritz_iteration():
+    """m = M: one block, the constraint is empty; converges to the same pairs."""
+    w, H = _tiny(nb=6, m=6)
+    ref = np.linalg.eigvalsh(H.dense())[:6]
+    r = lobpcg.solve(H, w.x0(H.npw, M=6), block=6, nline=4, tol=1e-10)
+    assert r.converged and np.abs(r.eig - ref).max() < 1e-10
+
+
+def test_lobpcg_block_size_one_band_by_band():
+    """m = 1: the single-band locally optimal method of Eq. 2, band by band."""
+    w, H = _tiny(nb=4, m=1)
+    ref = np.linalg.eigvalsh(H.dense())[:4]
+    r = lobpcg.solve(H, w.x0(H.npw, M=4), block=1, nline=4, tol=1e-10, max_sweeps=400)
+    assert r.converged and np.abs(r.eig - ref).max() < 1e-10
+
+
+def test_lobpcg_ritz_values_bound_and_decrease():
+    """Courant-Fischer: the k-th Ritz value of the first block is >= the k-th
+    eigenvalue, and within a block visit it never increases."""
+    w, H = _tiny(nb=8, m=4)
+    exact = np.linalg.eigvalsh(H.dense())
+    r = lobpcg.solve(H, w.x0(H.npw), block=4, nline=4, tol=1e-9, keep_trace=True)
+    nblk = 2
+    for visit, trace in enumerate(r.ritz_trace):
+        b = visit % nblk
+        for th in trace:
+            if b == 0:
+                assert np.all(th >= exact[:4] - 1e-11)
+        for t0, t1 in zip(trace[:-1], trace[1:]):
+            assert np.all(t1 <= t0 + 1e-10)
+
+
+def test_lobpcg_free_electrons_degenerate_shells():
+    """V = 0: the lowest shells of 1/2|G|^2 are highly degenerate; the solver must
+    return the closed-form eigenvalues and the right spectral projectors."""
+    a, N = 6.0, 12
+    k = np.zeros(3)
+    miller = basis.sphere(a, N, synth.default_ecut(a, N), k)
+    H = hamiltonian.Hamiltonian(a, N, k, miller, np.zeros((N, N, N)))
+    T = np.sort(H.T)
+    X0 = synth.start_vectors(5, H.npw, 8)
+    r = lobpcg.solve(H, X0, block=4, nline=4, tol=1e-10)
+    assert r.converged
+    assert np.abs(r.eig - T[:8]).max() < 1e-10
+    evals, evecs = np.linalg.eigh(H.dense())
+    assert checks.projector_distance(r.X, evecs[:, :8], evals[:8]) < 1e-8
+
+
+def test_lobpcg_workload_gamma24_matches_dense():
+    """The 24^3 / 925 plane-wave cell, 16 bands in one block, to 1e-10."""
+    w = synth.make_workload("gamma24")
+    H = hamiltonian.for_workload(w)
+    ref = np.linalg.eigvalsh(H.dense())[:16]
+    r = lobpcg.solve(H, w.x0(H.npw), block=16, nline=4, tol=1e-10)
+    assert r.converged and np.abs(r.eig - ref).max() < 1e-10
+
+
+def test_projector_distance_detects_wrong_subspace():
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((20, 6)) + 1j * rng.standard_normal((20, 6)))
+    eig = np.array([0, 0, 1, 1, 2, 3.0])
+    assert checks.projector_distance(Q, Q @ np.diag(np.exp(1j * np.arange(6))), eig) < 1e-12
+    Q2 = Q.copy()
+    Q2[:, 2] = Q[:, 4]
+    assert checks.projector_distance(Q2, Q, eig) > 0.5
+
+
+def test_golden_files_reproduce():
+    """The stored expected eigenvalues are what the oracle computes today."""
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    w = synth.make_workload("gamma24")
+    ev = np.linalg.eigvalsh(hamiltonian.for_workload(w).dense())[:16]
+    assert np.abs(np.loadtxt(os.path.join(here, "gamma24_eig.txt")) - ev).max() < 1e-12
+    t = synth.tiny_workload(a=6.0, N=12, natoms=2, kpt=(0.25, 0.125, -0.375))
+    ev = np.linalg.eigvalsh(hamiltonian.for_workload(t).dense())[:24]
+    assert np.abs(np.loadtxt(os.path.join(here, "tiny_kb_eig.txt")) - ev).max() < 1e-12
