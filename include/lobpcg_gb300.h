@@ -1,0 +1,198 @@
+/*
+ * lobpcg_gb300.h -- C ABI of a GB300 (sm_103a) block LOBPCG plane-wave eigensolver.
+ *
+ * The library finds the lowest Kohn-Sham eigenpairs of a FIXED plane-wave
+ * Hamiltonian (Bottin, Leroux, Knyazev, Zerah 2007, "Large scale ab initio
+ * calculations based on three levels of parallelization"):
+ *
+ *   H = T + V_loc + V_KB   on the sphere  1/2 |k+G|^2 <= Ecut      (Sec. 2.1)
+ *
+ *   T      kinetic diagonal 1/2 |k+G|^2,
+ *   V_loc  local potential applied through a zero-padded 3D FFT: inverse FFT
+ *          of the sphere to the N^3 grid, pointwise V(r), forward FFT back
+ *          to the sphere (Sec. 2.2 item iii, Sec. 4.1),
+ *   V_KB   Kleinman-Bylander non-local part  sum_p E_p |beta_p><beta_p|
+ *          (Sec. 2.2 item iv, Sec. 4.3),
+ *
+ * by block LOBPCG (Sec. 3.2, Algorithm 1) iterated block after block with
+ * each block orthogonal to the previous ones, each sweep closed by a
+ * Rayleigh-Ritz step over all bands (Sec. 3.2, last paragraph).  The overlap
+ * operator O is the identity (norm-conserving case, Sec. 2.1).
+ *
+ * Conventions shared by every call
+ *   - Cell: cubic, side a (bohr), volume Omega = a^3; G_n = (2 pi / a) n for
+ *     integer triplets n; k-points in reduced coordinates, q = (2 pi/a)(n + k).
+ *   - Grid: N^3 points r_j = a j / N; real-space arrays are C-order [x][y][z].
+ *   - Sphere: n is in the basis of k-point k when
+ *         |n + k|^2 <= 2 Ecut (a / 2 pi)^2 + 1e-9
+ *     (index units; lattice points exactly on the sphere are kept).  Every
+ *     basis index must lie in [-N/2, N/2-1] or lobpcg_create fails.
+ *   - Plane-wave order ("G order") of k-point k: sorted by n_x, then n_y,
+ *     then n_z (signed); lobpcg_gvectors returns it.  Every coefficient
+ *     array below is in this order.
+ *   - Complex numbers are interleaved (re, im): complex128 = 2 x double,
+ *     complex64 = 2 x float.  Blocks of vectors are column-major
+ *     npw_k x nb (each band's npw_k coefficients contiguous, ld = npw_k).
+ *   - V_loc matrix elements: the grid potential's discrete Fourier
+ *     coefficient Vt((n - n') mod N), Vt(n) = N^-3 sum_j V(r_j) e^{-2 pi i n.j/N}.
+ *
+ * Ownership and streams
+ *   - The library copies the potential, projectors and energies at create
+ *     and owns every device buffer it allocates; it never frees caller memory.
+ *   - All device work is enqueued on the CUDA stream given at create
+ *     (lobpcg_set_stream changes it); calls return after enqueueing unless
+ *     stated otherwise.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *
+ * Errors
+ *   - Every call returns an int status: LOBPCG_OK (0) on success, a negative
+ *     LOBPCG_ERR_* code on failure, LOBPCG_NOT_CONVERGED (positive) when a
+ *     solve ran out of sweeps with its outputs filled.  The library never
+ *     calls exit/abort.  lobpcg_last_error returns a message for the last
+ *     failure on a handle.
+ */
+#ifndef LOBPCG_GB300_H
+#define LOBPCG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOBPCG_OK               0
+#define LOBPCG_NOT_CONVERGED    1   /* solve: outputs filled, max residual > tol */
+#define LOBPCG_ERR_ARG         -1   /* invalid argument (sizes, pointers, k index, options) */
+#define LOBPCG_ERR_OOM         -2   /* a device allocation failed or exceeded the handle's cap */
+#define LOBPCG_ERR_CUDA        -3   /* a CUDA runtime call failed; message has the CUDA error */
+#define LOBPCG_ERR_TIMEOUT     -4   /* a bounded device wait ran out (never a hang) */
+#define LOBPCG_ERR_BREAKDOWN   -5   /* the Rayleigh-Ritz basis collapsed beyond recovery */
+#define LOBPCG_ERR_UNSUPPORTED -6   /* grid size or option not supported by this build */
+
+/* Arithmetic of lobpcg_apply_H (element type of X and Y, and compute precision). */
+#define LOBPCG_C128 0               /* complex128 in/out, FP64 FFT and GEMMs */
+#define LOBPCG_C64  1               /* complex64  in/out, FP32 FFT and GEMMs */
+
+/* Precision schedule of lobpcg_solve (lobpcg_options.precision). */
+#define LOBPCG_FP64  0              /* every step in FP64 */
+#define LOBPCG_MIXED 1              /* FP32 FFTs / reduced-precision GEMMs for W and P,
+                                       FP64 for X, HX, the XX Gram block, Cholesky,
+                                       Rayleigh-Ritz and residuals */
+
+typedef struct lobpcg_ctx lobpcg_ctx;   /* opaque handle */
+
+/* Cubic cell: side a (bohr), FFT grid edge N, plane-wave cutoff ecut (Ha). */
+typedef struct {
+    double a;
+    int    N;
+    double ecut;
+} lobpcg_cell;
+
+typedef struct {
+    int    block_size;   /* m: bands per LOBPCG block (Sec. 3.2); M must be a multiple */
+    int    nline;        /* Algorithm 1 iterations per block visit (paper: 4) */
+    int    max_sweeps;   /* sweeps over all blocks before giving up */
+    int    precision;    /* LOBPCG_FP64 or LOBPCG_MIXED */
+    int    gemm_split;   /* mixed path GEMM mode: 0 = auto, 1 = BF16x3, 2 = TF32x3, 3 = FP32 SIMT */
+    int    use_graph;    /* 1: replay block iterations as CUDA graphs */
+    int    autotune;     /* 1: time kernel variants once per shape and keep the fastest */
+    double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */
+    long long mem_cap;   /* 0: no cap; else maximum bytes the handle may allocate (ERR_OOM above it) */
+} lobpcg_options;
+
+typedef struct {
+    int    sweeps;            /* sweeps done */
+    int    iterations;        /* Algorithm 1 iterations done (all blocks, all k) */
+    int    converged;         /* 1 if every band of every k met tol */
+    int    restarts;          /* Rayleigh-Ritz basis vectors dropped as dependent */
+    double max_resid;         /* final max residual over all k and bands (Ha) */
+    double ms_total;          /* wall time of the solve, ms */
+    double ms_apply;          /* time in H applications (CUDA events), ms */
+    double ms_gram;           /* Gram / projection GEMMs, ms */
+    double ms_rr;             /* Cholesky + Rayleigh-Ritz eigensolves, ms */
+    double ms_update;         /* Ritz updates, residual, preconditioner, constraint, ms */
+    long long band_applies_fp64;  /* single-band H applications done in FP64 */
+    long long band_applies_fp32;  /* single-band H applications done in FP32 */
+} lobpcg_stats;
+
+/* Fill *opt with defaults: m = 64, nline = 4, max_sweeps = 100, FP64, tol = 1e-8. */
+int lobpcg_default_options(lobpcg_options *opt);
+
+/*
+ * Create a solver for nk k-points of one cell (Sec. 2.1 basis; Sec. 5.2 k-points).
+ *   cell      a, N, ecut as above.  Supported N: products of 2, 3 and 5, 4 <= N <= 256.
+ *   kpts      host, nk x 3 doubles, reduced coordinates.
+ *   vloc_r    host, N^3 doubles, the real local potential V(r_j), C-order [x][y][z].
+ *   nproj     number of KB projectors (>= 0), the same set for every k.
+ *   proj_E    host, nproj doubles: KB energies E_p (Ha); may be NULL when nproj = 0.
+ *   beta      host, nk pointers; beta[k] is npw_k x nproj complex128, column-major,
+ *             rows in G order.  Because npw_k and the G order are only known
+ *             after the basis is built, pass beta = NULL here and give the
+ *             projectors afterwards with lobpcg_set_projectors, or precompute
+ *             the order with the same rule.  May be NULL when nproj = 0.
+ *   opt       options (NULL = defaults).
+ *   stream    cudaStream_t to enqueue on (NULL = legacy default stream).
+ * On success *out receives a handle.  Errors: ERR_ARG, ERR_UNSUPPORTED,
+ * ERR_OOM, ERR_CUDA (then *out is NULL).
+ */
+int lobpcg_create(lobpcg_ctx **out, const lobpcg_cell *cell, int nk, const double *kpts,
+                  const double *vloc_r, int nproj, const double *proj_E,
+                  const void *const *beta, const lobpcg_options *opt, void *stream);
+
+/* Upload (or replace) the projectors of k-point k: host npw_k x nproj complex128,
+ * column-major, G order.  Synchronous with respect to the host buffer. */
+int lobpcg_set_projectors(lobpcg_ctx *ctx, int k, const void *beta_k);
+
+/* Change the stream later calls enqueue on. */
+int lobpcg_set_stream(lobpcg_ctx *ctx, void *stream);
+
+/* Replace the options of an existing handle (block size, tolerance, precision ...). */
+int lobpcg_set_options(lobpcg_ctx *ctx, const lobpcg_options *opt);
+
+/* Number of plane waves npw_k of k-point k (>= 1), or a negative error code. */
+int lobpcg_npw(const lobpcg_ctx *ctx, int k);
+
+/* Write the G order of k-point k: miller is host int32 npw_k x 3 (row g = (n_x, n_y, n_z)). */
+int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller);
+
+/*
+ * Y = H X for nb bands of k-point k (Sec. 2.2 items iii and iv).
+ *   X, Y       npw_k x nb, column-major (ld = npw_k), complex128 when
+ *              precision = LOBPCG_C128 or complex64 when LOBPCG_C64.  Device
+ *              pointers run fully asynchronously on the handle's stream; host
+ *              pointers are staged through device buffers and the call returns
+ *              after Y has been written back (synchronous).  X and Y must not
+ *              overlap.
+ *   nb         >= 0 (0 is a no-op).
+ * Errors: ERR_ARG (k, nb, NULL pointers, overlapping X/Y), ERR_OOM, ERR_CUDA.
+ */
+int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int precision);
+
+/*
+ * Lowest nbands eigenpairs of every k-point by block LOBPCG (Algorithm 1),
+ * block by block with the orthogonality constraint, each sweep closed by an
+ * all-band Rayleigh-Ritz step (Sec. 3.2).
+ *   nbands     M, a multiple of the block size, 1 <= M <= npw_k for every k.
+ *   X          nk device pointers; X[k] is npw_k x M complex128 (column-major).
+ *              In: start vectors (any full-rank block).  Out: orthonormal
+ *              eigenvectors, ascending eigenvalues.
+ *   eig        host nk x M doubles (out): eigenvalues, ascending per k.
+ *   resid      host nk x M doubles (out): ||H x_i - eps_i x_i||_2 in FP64.
+ *   stats      optional (NULL allowed) statistics.
+ * Synchronous: returns once eig/resid are on the host.
+ * Returns OK, NOT_CONVERGED (outputs filled) or an error code.
+ */
+int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid,
+                 lobpcg_stats *stats);
+
+/* Message describing the last error on ctx ("" if none); ctx may be NULL for create errors. */
+const char *lobpcg_last_error(const lobpcg_ctx *ctx);
+
+/* Free every resource of the handle.  NULL is ignored. */
+void lobpcg_destroy(lobpcg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOBPCG_GB300_H */

@@ -1,0 +1,88 @@
+/*
+ * lobpcg_gb300_kernels.h -- C ABI of the solver's dense building blocks.
+ *
+ * These are the contractions and small dense eigen-solves that one block
+ * iteration of LOBPCG (Algorithm 1 of Bottin, Leroux, Knyazev, Zerah 2007)
+ * is made of, exposed one by one so that each can be checked against a CPU
+ * reference and timed on its own.  lobpcg_solve uses the same kernels.
+ *
+ * Common rules
+ *   - Matrices are column-major with a leading dimension (elements).
+ *   - Complex numbers are interleaved (re, im); prec = LOBPCG_C128 selects
+ *     complex128 with FP64 arithmetic, LOBPCG_C64 complex64 with FP32.
+ *   - Pointers are device pointers; work is enqueued on `stream`
+ *     (cudaStream_t, NULL = legacy default stream) and the call returns
+ *     without synchronising, except where noted.
+ *   - Return LOBPCG_OK or a negative LOBPCG_ERR_* code (header lobpcg_gb300.h);
+ *     lobpcg_k_last_error() gives the message of the last failure.
+ *   - Scratch memory the kernels need is allocated by the library and kept
+ *     for later calls (one pool per device).
+ */
+#ifndef LOBPCG_GB300_KERNELS_H
+#define LOBPCG_GB300_KERNELS_H
+
+#include "lobpcg_gb300.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * C = alpha * A^H B + beta * C: the Gram and projection contractions of
+ * Algorithm 1, step 4 (blocks of [Psi W P]^H [Psi W P] and of
+ * [Psi W P]^H H[Psi W P]; Sec. 4.1 computes them with zgemm) and of the
+ * KB projection beta^H X (Sec. 4.3).
+ *   A is K x m (lda >= K), B is K x n (ldb >= K), C is m x n (ldc >= m).
+ *   alpha, beta are real.  K may be large (the plane-wave count); the
+ *   reduction over K is split across the GPU and summed in a fixed order, so
+ *   results are bitwise reproducible for a given shape.
+ */
+int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A, int lda,
+                     const void *B, int ldb, double beta, void *C, int ldc, void *stream);
+
+/*
+ * D = alpha * A B + beta * C: the Ritz updates of Algorithm 1, steps 4-5
+ * (Psi Delta + W Lambda + P Gamma and W Lambda + P Gamma), the KB
+ * back-projection beta (E B) and the block-constraint update Y (Y^H W).
+ *   A is M x k (lda >= M), B is k x n (ldb >= k), C and D are M x n
+ *   (ldc, ldd >= M).  C may equal D (in-place accumulate) or be NULL when
+ *   beta = 0.  alpha, beta are real.
+ */
+int lobpcg_k_gemm_nn(int prec, int M, int n, int k, double alpha, const void *A, int lda,
+                     const void *B, int ldb, double beta, const void *C, int ldc,
+                     void *D, int ldd, void *stream);
+
+/*
+ * Rayleigh-Ritz step of Algorithm 1, step 4, in FP64: the lowest m
+ * eigenpairs of the Hermitian pencil A c = theta S c, where S is the Gram
+ * matrix of a basis Z and A = Z^H H Z (n x n complex128, column-major,
+ * lower triangles used).
+ *   S is scaled to unit diagonal and factored by Cholesky; a basis vector
+ *   whose pivot falls below drop_tol (relative to its own norm) is taken as
+ *   dependent on the earlier ones and removed from the subspace.
+ *   theta  (device, m doubles)          Ritz values, ascending.
+ *   C      (device, n x m complex128, ld n) coefficients: Z C are the Ritz vectors,
+ *          C^H S C = I.
+ *   ndropped (device int, may be NULL)  number of basis vectors removed.
+ * S and A are not modified.  Errors: ERR_ARG (m > n, n > 4096), ERR_OOM, ERR_CUDA.
+ */
+int lobpcg_k_rayleigh_ritz(int n, int m, const void *S, const void *A, double drop_tol,
+                           double *theta, void *C, int *ndropped, void *stream);
+
+/*
+ * Hermitian eigen-decomposition in FP64: A = V diag(w) V^H, eigenvalues ascending.
+ *   A   (device, n x n complex128, ld n; lower triangle used, not modified),
+ *   w   (device, n doubles), V (device, n x n complex128, ld n).
+ * Householder tridiagonalisation, bisection and inverse iteration on the
+ * tridiagonal matrix, back-transformation.
+ */
+int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream);
+
+/* Message of the last failure of a lobpcg_k_* call on this host thread. */
+const char *lobpcg_k_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOBPCG_GB300_KERNELS_H */

@@ -1,0 +1,333 @@
+"""GB300 (sm_103a) block LOBPCG plane-wave eigensolver -- Python binding.
+
+A thin ctypes layer over the C ABI in ``include/lobpcg_gb300.h`` and
+``include/lobpcg_gb300_kernels.h``.  It only marshals arguments: every step
+of the computation runs in the CUDA library ``_lib/liblobpcg_gb300.so``.
+PyTorch is used for device memory and CUDA streams.
+
+Array conventions: a block of nb bands of one k-point is a tensor of shape
+``(nb, npw)`` (row b = band b), which is the library's column-major
+npw x nb layout.  Projectors are given as ``(npw, nproj)`` numpy arrays.
+
+There is no fallback: if the library has not been built, importing the
+binding succeeds but every call raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblobpcg_gb300.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BREAKDOWN, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+C128, C64 = 0, 1
+FP64, MIXED = 0, 1
+
+EXPORTED = (
+    "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
+    "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
+    "lobpcg_last_error", "lobpcg_destroy",
+    "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_heev", "lobpcg_k_last_error",
+)
+
+
+class Cell(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("N", ctypes.c_int), ("ecut", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int), ("nline", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("gemm_split", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("max_resid", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_apply", ctypes.c_double), ("ms_gram", ctypes.c_double), ("ms_rr", ctypes.c_double),
+                ("ms_update", ctypes.c_double), ("band_applies_fp64", ctypes.c_longlong),
+                ("band_applies_fp32", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class LobpcgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lobpcg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library; raises RuntimeError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "lobpcg_default_options": (i, [ctypes.POINTER(Options)]),
+        "lobpcg_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(Cell), i, vp, vp, i, vp, vp, ctypes.POINTER(Options), vp]),
+        "lobpcg_set_projectors": (i, [vp, i, vp]),
+        "lobpcg_set_stream": (i, [vp, vp]),
+        "lobpcg_set_options": (i, [vp, ctypes.POINTER(Options)]),
+        "lobpcg_npw": (i, [vp, i]),
+        "lobpcg_gvectors": (i, [vp, i, vp]),
+        "lobpcg_apply_H": (i, [vp, i, vp, vp, i, i]),
+        "lobpcg_solve": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Stats)]),
+        "lobpcg_last_error": (ctypes.c_char_p, [vp]),
+        "lobpcg_destroy": (None, [vp]),
+        "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
+        "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
+        "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
+        "lobpcg_k_heev": (i, [i, vp, vp, vp, vp]),
+        "lobpcg_k_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _ = ll
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int:
+    """Device or host address of a torch tensor or numpy array."""
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream_handle(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def default_options() -> Options:
+    o = Options()
+    _check(load().lobpcg_default_options(ctypes.byref(o)), None)
+    return o
+
+
+def _check(rc: int, handle, kernels: bool = False) -> int:
+    if rc < 0:
+        lib = load()
+        if kernels:
+            msg = lib.lobpcg_k_last_error()
+        else:
+            msg = lib.lobpcg_last_error(handle)
+        raise LobpcgError(rc, (msg or b"").decode(errors="replace"))
+    return rc
+
+
+@dataclass
+class SolveResult:
+    eig: np.ndarray      # (nk, M)
+    resid: np.ndarray    # (nk, M)
+    status: int
+    stats: dict
+
+
+class Solver:
+    """One cell, its k-points, potential and projectors: ``lobpcg_create``.
+
+    ``kpts`` (nk, 3) reduced; ``vloc`` (N, N, N) float64 [x][y][z];
+    ``proj_E`` (nproj,) KB energies; ``beta`` optional callable
+    ``beta(miller (npw,3) int, k_index) -> (npw, nproj) complex128`` giving the
+    projectors in the library's plane-wave order.
+    """
+
+    def __init__(self, a: float, N: int, ecut: float, kpts, vloc, proj_E=None, beta=None,
+                 block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
+                 tol: float = 1e-8, mem_cap: int = 0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+        v = np.ascontiguousarray(np.asarray(vloc, dtype=np.float64))
+        if v.shape != (N, N, N):
+            raise ValueError("vloc must have shape (N, N, N)")
+        E = np.ascontiguousarray(np.zeros(0) if proj_E is None else np.asarray(proj_E, dtype=np.float64))
+        self.nproj = int(E.shape[0])
+        self.nk = int(kp.shape[0])
+        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap)
+        cell = Cell(a, N, ecut)
+        self._stream = stream
+        rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
+                               v.ctypes.data, self.nproj, E.ctypes.data if self.nproj else None, None,
+                               ctypes.byref(opt), _stream_handle(stream))
+        if rc < 0:
+            raise LobpcgError(rc, (lib.lobpcg_last_error(None) or b"").decode(errors="replace"))
+        self.a, self.N, self.ecut = a, N, ecut
+        self.kpts = kp
+        if self.nproj and beta is not None:
+            for k in range(self.nk):
+                self.set_projectors(k, beta(self.gvectors(k), k))
+
+    @staticmethod
+    def _options(block_size, nline, max_sweeps, precision, tol, mem_cap) -> Options:
+        o = default_options()
+        o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
+        o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+        o.tol = tol
+        o.mem_cap = mem_cap
+        return o
+
+    def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0):
+        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap)
+        _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(self._lib.lobpcg_set_stream(self.handle, _stream_handle(stream)), self.handle)
+
+    def npw(self, k: int = 0) -> int:
+        return _check(self._lib.lobpcg_npw(self.handle, k), self.handle)
+
+    def gvectors(self, k: int = 0) -> np.ndarray:
+        out = np.empty((self.npw(k), 3), dtype=np.int32)
+        _check(self._lib.lobpcg_gvectors(self.handle, k, out.ctypes.data), self.handle)
+        return out
+
+    def set_projectors(self, k: int, beta: np.ndarray):
+        b = np.asarray(beta, dtype=np.complex128)
+        if b.shape != (self.npw(k), self.nproj):
+            raise ValueError("beta must have shape (npw_k, nproj)")
+        colmajor = np.ascontiguousarray(b.T)
+        _check(self._lib.lobpcg_set_projectors(self.handle, k, colmajor.ctypes.data), self.handle)
+
+    def apply_H(self, k: int, X, Y=None):
+        """Y = H X for a (nb, npw) block: torch CUDA tensor (asynchronous on the
+        handle's stream) or numpy array (staged, synchronous).  complex128 runs
+        in FP64, complex64 in FP32."""
+        import torch
+        if isinstance(X, np.ndarray):
+            prec = C128 if X.dtype == np.complex128 else C64
+            if X.dtype not in (np.complex128, np.complex64):
+                raise TypeError("X must be complex64 or complex128")
+            X = np.ascontiguousarray(X)
+            if Y is None:
+                Y = np.empty_like(X)
+        else:
+            prec = C128 if X.dtype == torch.complex128 else C64
+            if X.dtype not in (torch.complex128, torch.complex64):
+                raise TypeError("X must be complex64 or complex128")
+            if not X.is_contiguous():
+                raise ValueError("X must be contiguous")
+            if Y is None:
+                Y = torch.empty_like(X)
+        nb = 0 if X.shape[0] == 0 else int(X.shape[0])
+        if nb and X.shape[-1] != self.npw(k):
+            raise ValueError("X must have shape (nb, npw_k)")
+        _check(self._lib.lobpcg_apply_H(self.handle, k, _ptr(X), _ptr(Y), nb, prec), self.handle)
+        return Y
+
+    def solve(self, X, nbands: int | None = None) -> SolveResult:
+        """Lowest eigenpairs; ``X`` is a list (one per k-point) of (M, npw_k)
+        complex128 CUDA tensors holding start vectors, overwritten by the
+        eigenvectors."""
+        if not isinstance(X, (list, tuple)):
+            X = [X]
+        if len(X) != self.nk:
+            raise ValueError("one start block per k-point is needed")
+        M = int(X[0].shape[0]) if nbands is None else nbands
+        ptrs = (ctypes.c_void_p * self.nk)(*[ctypes.c_void_p(_ptr(x)) for x in X])
+        eig = np.zeros((self.nk, M))
+        res = np.zeros((self.nk, M))
+        st = Stats()
+        rc = _check(self._lib.lobpcg_solve(self.handle, M, ptrs, eig.ctypes.data, res.ctypes.data,
+                                           ctypes.byref(st)), self.handle)
+        return SolveResult(eig, res, rc, st.as_dict())
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self._lib.lobpcg_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------- dense building blocks
+def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None):
+    """C = alpha A^H B + beta C for torch CUDA tensors given as (cols, rows) row-major
+    (i.e. column-major matrices): A is (m, K), B is (n, K), C is (n, m)."""
+    import torch
+    lib = load()
+    prec = C128 if A.dtype == torch.complex128 else C64
+    m, K = A.shape
+    n = B.shape[0]
+    if C is None:
+        C = torch.zeros((n, m), dtype=A.dtype, device=A.device)
+    _check(lib.lobpcg_k_gemm_cn(prec, m, n, K, alpha, _ptr(A), K, _ptr(B), K, beta, _ptr(C), m,
+                                _stream_handle(stream)), None, kernels=True)
+    return C
+
+
+def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None):
+    """D = alpha A B + beta C, column-major stored as transposed torch tensors:
+    A is (k, M), B is (n, k), C and D are (n, M)."""
+    import torch
+    lib = load()
+    prec = C128 if A.dtype == torch.complex128 else C64
+    k, M = A.shape
+    n = B.shape[0]
+    if D is None:
+        D = torch.empty((n, M), dtype=A.dtype, device=A.device)
+    _check(lib.lobpcg_k_gemm_nn(prec, M, n, k, alpha, _ptr(A), M, _ptr(B), k, beta,
+                                _ptr(C) if C is not None else None, M, _ptr(D), M, _stream_handle(stream)),
+           None, kernels=True)
+    return D
+
+
+def rayleigh_ritz(S, A, m, drop_tol=1e-12, stream=None):
+    """Lowest m pairs of A c = theta S c (n x n complex128 CUDA tensors, column-major
+    i.e. pass the transpose of a numpy matrix).  Returns (theta (m,), C (m, n) whose
+    row j is column j of the coefficient matrix, ndropped)."""
+    import torch
+    lib = load()
+    n = S.shape[0]
+    theta = torch.empty(m, dtype=torch.float64, device=S.device)
+    C = torch.empty((m, n), dtype=torch.complex128, device=S.device)
+    nd = torch.zeros(1, dtype=torch.int32, device=S.device)
+    _check(lib.lobpcg_k_rayleigh_ritz(n, m, _ptr(S), _ptr(A), drop_tol, _ptr(theta), _ptr(C), _ptr(nd),
+                                      _stream_handle(stream)), None, kernels=True)
+    return theta, C, nd
+
+
+def heev(A, stream=None):
+    """Eigen-decomposition of an n x n complex128 CUDA tensor (column-major; lower
+    triangle used).  Returns (w (n,), V (n, n) whose row j is eigenvector j)."""
+    import torch
+    lib = load()
+    n = A.shape[0]
+    w = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = torch.empty((n, n), dtype=torch.complex128, device=A.device)
+    _check(lib.lobpcg_k_heev(n, _ptr(A), _ptr(w), _ptr(V), _stream_handle(stream)), None, kernels=True)
+    return w, V

@@ -1,0 +1,189 @@
+// Internal declarations shared by the library's translation units.
+// Complex numbers are interleaved (re, im) pairs, layout-compatible with
+// float2 / double2 and with numpy complex64 / complex128.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lobpcg_gb300.h"
+
+namespace lg {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) cx {
+    R x, y;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mkc(R a, R b) { cx<R> r; r.x = a; r.y = b; return r; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mkc<R>(a.x + b.x, a.y + b.y); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mkc<R>(a.x - b.x, a.y - b.y); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+    return mkc<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mkc<R>(s * a.x, s * a.y); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> conjc(cx<R> a) { return mkc<R>(a.x, -a.y); }
+// a * conj(b)
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mul_conj(cx<R> a, cx<R> b) {
+    return mkc<R>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// acc += conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ void fma_cn(cx<R> &acc, cx<R> a, cx<R> b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void fma_nn(cx<R> &acc, cx<R> a, cx<R> b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ R abs2(cx<R> a) { return a.x * a.x + a.y * a.y; }
+
+template <typename To, typename From>
+__host__ __device__ __forceinline__ cx<To> cvt(cx<From> a) { return mkc<To>((To)a.x, (To)a.y); }
+
+typedef cx<double> z64;   // complex128
+typedef cx<float> c32;    // complex64
+
+// ------------------------------------------------------------------ status
+struct Status {
+    int code = LOBPCG_OK;
+    std::string msg;
+};
+
+// Thread-local message for calls that have no handle (create, lobpcg_k_*).
+void set_global_error(const std::string &m);
+const char *global_error();
+
+#define LG_CUDA_TRY(...)                                                                    \
+    do {                                                                                    \
+        cudaError_t _e = (__VA_ARGS__);                                                     \
+        if (_e != cudaSuccess) {                                                            \
+            return ::lg::fail(LOBPCG_ERR_CUDA, std::string(#__VA_ARGS__ " failed: ") +       \
+                                                   cudaGetErrorString(_e));                 \
+        }                                                                                   \
+    } while (0)
+
+#define LG_TRY(...)                                  \
+    do {                                             \
+        int _s = (__VA_ARGS__);                      \
+        if (_s < 0) return _s;                       \
+    } while (0)
+
+// Records a message for the current call and returns `code`.
+int fail(int code, const std::string &m);
+// Message recorded by the last fail() on this host thread.
+const std::string &last_fail();
+
+// Checks a kernel launch (configuration errors are reported at launch time).
+int check_launch(const char *what);
+
+// ------------------------------------------------------------------ device memory
+// A grow-only device buffer owned by the library.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Allocation accounting with an optional cap (lobpcg_options.mem_cap).
+struct Allocator {
+    long long cap = 0;
+    long long used = 0;
+    int alloc(void **p, size_t bytes);
+    void free(void *p, size_t bytes);
+    // Make `b` at least `bytes` large (contents are not preserved).
+    int ensure(DevBuf &b, size_t bytes);
+    void release(DevBuf &b);
+};
+
+// ------------------------------------------------------------------ FFT geometry (one k-point)
+struct FFTGeom {
+    int N = 0;
+    int Px = 0, Py = 0;           // active x planes and y rows of the sphere
+    int nx0 = 0, ny0 = 0;         // signed index of plane 0 / row 0
+    int npw = 0;
+    // device tables
+    int *plane_begin = nullptr;   // Px+1: sphere range of each x plane
+    int2 *plane_yrange = nullptr; // Px: [py_lo, py_hi] rows holding coefficients
+    int *gmap = nullptr;          // npw: py * N + (n_z mod N)
+};
+
+// Radix plan of a length-N 1D FFT (Stockham, radices 8, 4, 2, 5, 3).
+struct FFTPlan {
+    int N = 0;
+    int nstage = 0;
+    int radix[12];
+};
+bool make_fft_plan(int N, FFTPlan &plan);
+
+// Local-potential application Y = V_loc X (+ T X) for a block of bands on one k-point.
+//   X, Y: npw x nb column-major (ld = ldx / ldy) of cx<R>; T: npw kinetic (nullable)
+//   vt:   device potential pre-scaled by 1/N^3, layout [z][x][y]
+//   tw:   device twiddles e^{-2 pi i t / N}, t < N
+//   T2:   scratch of at least nbatch * Px * N * N cx<R>
+template <typename R>
+int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy,
+                   int nb, const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch,
+                   cudaStream_t s);
+// Shared memory the passes need; 0 when the grid does not fit on one SM.
+template <typename R>
+size_t fft_smem_need(const FFTGeom &g);
+
+// ------------------------------------------------------------------ BLAS-like kernels
+// Scratch for split-K partial sums (grown on demand).
+struct GemmWork {
+    Allocator *alloc = nullptr;
+    DevBuf part;
+};
+template <typename R>
+int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
+            R beta, cx<R> *C, int ldc, cudaStream_t s);
+template <typename R>
+int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb, R beta,
+            const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s);
+// Small general complex128 product: C = alpha op(A) op(B) + beta C, op in {'N','C'}.
+int zgemm_small(char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
+                const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s);
+
+// ------------------------------------------------------------------ dense FP64 eigen-solvers
+struct EigWork {
+    Allocator *alloc = nullptr;
+    DevBuf buf;      // generic workspace
+    DevBuf ibuf;     // integer workspace
+    GemmWork gw;
+};
+// Rayleigh-Ritz: lowest m pairs of A c = theta S c (n x n, ld n). See lobpcg_k_rayleigh_ritz.
+int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,
+                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s);
+// Copy the lower triangle of A (n x n, ld n) onto the upper one (imaginary diagonal cleared).
+int hermitize_lower(EigWork &w, int n, z64 *A, cudaStream_t s);
+// Lowest m eigenpairs of a Hermitian matrix (n x n, ld lda, lower triangle; overwritten).
+int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V, int ldv, cudaStream_t s);
+
+// ------------------------------------------------------------------ vector kernels
+template <typename R>
+int residual_precond(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
+                     const double *kin, cx<R> *W, int ldw, double *work, cudaStream_t s);
+int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
+                       double *out, cudaStream_t s);
+template <typename Ro, typename Ri>
+int copy_cast(int rows, int cols, const cx<Ri> *A, int lda, cx<Ro> *B, int ldb, cudaStream_t s);
+int scale_rows_real(int rows, int cols, const double *d, z64 *A, int lda, cudaStream_t s);
+template <typename R>
+int scale_rows(int rows, int cols, const R *d, cx<R> *A, int lda, cudaStream_t s);
+
+}  // namespace lg

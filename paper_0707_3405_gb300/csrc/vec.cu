@@ -1,0 +1,159 @@
+// Per-column and elementwise kernels of Algorithm 1 (Bottin et al. 2007, Sec. 3.2):
+//   step 2  R = H Psi - Psi Upsilon (O = I),
+//   step 3  W = K(R) with the Teter-Payne-Allan plane-wave preconditioner,
+// the FP64 residual norms of the convergence test, precision casts and
+// row scalings.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace lg {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Two deterministic block sums at once (256 threads).
+__device__ void block_sum2(double &a, double &b) {
+    __shared__ double sa[8], sb[8];
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    double ta = 0.0, tb = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { ta += sa[i]; tb += sb[i]; }
+    a = ta;
+    b = tb;
+}
+
+// Kinetic energy of each band, Ekin_i = sum T |x|^2 / sum |x|^2 (one block per column).
+__global__ void __launch_bounds__(256)
+k_ekin(int npw, const z64 *__restrict__ X, int ldx, const double *__restrict__ kin, double *__restrict__ ekin) {
+    const int j = blockIdx.x;
+    const z64 *x = X + (size_t)j * ldx;
+    double num = 0.0, den = 0.0;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+        const double a = abs2(x[g]);
+        num += kin[g] * a;
+        den += a;
+    }
+    block_sum2(num, den);
+    if (threadIdx.x == 0) ekin[j] = den > 0.0 ? num / den : 1.0;
+}
+
+// W = K(x) (HX - theta X),  x = T(q) / Ekin_i,
+// K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4)  (Teter, Payne, Allan 1989).
+template <typename R>
+__global__ void k_resid_precond(int npw, int m, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX,
+                                int ldhx, const double *__restrict__ theta, const double *__restrict__ kin,
+                                const double *__restrict__ ekin, cx<R> *__restrict__ W, int ldw) {
+    const int j = blockIdx.y;
+    const double th = theta[j];
+    const double ie = 1.0 / ekin[j];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+        const z64 x = X[(size_t)j * ldx + g], hx = HX[(size_t)j * ldhx + g];
+        const double t = kin[g] * ie;
+        const double p = 27.0 + t * (18.0 + t * (12.0 + 8.0 * t));
+        const double t2 = t * t;
+        const double k = p / (p + 16.0 * t2 * t2);
+        const z64 r = mkc(hx.x - th * x.x, hx.y - th * x.y);
+        W[(size_t)j * ldw + g] = mkc<R>((R)(k * r.x), (R)(k * r.y));
+    }
+}
+
+// ||HX_j - theta_j X_j|| / ||X_j|| (one block per column, FP64).
+__global__ void __launch_bounds__(256)
+k_resid_norm(int npw, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX, int ldhx,
+             const double *__restrict__ theta, double *__restrict__ out) {
+    const int j = blockIdx.x;
+    const double th = theta[j];
+    double rr = 0.0, xx = 0.0;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+        const z64 x = X[(size_t)j * ldx + g], hx = HX[(size_t)j * ldhx + g];
+        const double a = hx.x - th * x.x, b = hx.y - th * x.y;
+        rr += a * a + b * b;
+        xx += abs2(x);
+    }
+    block_sum2(rr, xx);
+    if (threadIdx.x == 0) out[j] = xx > 0.0 ? sqrt(rr / xx) : 0.0;
+}
+
+template <typename Ro, typename Ri>
+__global__ void k_copy_cast(int rows, int cols, const cx<Ri> *__restrict__ A, int lda, cx<Ro> *__restrict__ B,
+                            int ldb) {
+    const size_t tot = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        B[(size_t)j * ldb + i] = cvt<Ro, Ri>(A[(size_t)j * lda + i]);
+    }
+}
+
+template <typename R>
+__global__ void k_scale_rows(int rows, int cols, const R *__restrict__ d, cx<R> *__restrict__ A, int lda) {
+    const size_t tot = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        A[(size_t)j * lda + i] = d[i] * A[(size_t)j * lda + i];
+    }
+}
+
+int grid_for(size_t n, int threads) {
+    return (int)std::max<size_t>(1, std::min<size_t>((n + threads - 1) / threads, 152 * 16));
+}
+
+}  // namespace
+
+template <typename R>
+int residual_precond(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
+                     const double *kin, cx<R> *W, int ldw, double *work, cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, work);
+    LG_TRY(check_launch("ekin"));
+    const int gx = std::max(1, std::min((npw + 255) / 256, 64));
+    k_resid_precond<R><<<dim3(gx, m), 256, 0, s>>>(npw, m, X, ldx, HX, ldhx, theta, kin, work, W, ldw);
+    return check_launch("residual/preconditioner");
+}
+
+int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
+                       double *out, cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    k_resid_norm<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, theta, out);
+    return check_launch("residual norms");
+}
+
+template <typename Ro, typename Ri>
+int copy_cast(int rows, int cols, const cx<Ri> *A, int lda, cx<Ro> *B, int ldb, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_copy_cast<Ro, Ri><<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, B, ldb);
+    return check_launch("copy/cast");
+}
+
+int scale_rows_real(int rows, int cols, const double *d, z64 *A, int lda, cudaStream_t s) {
+    return scale_rows<double>(rows, cols, d, A, lda, s);
+}
+
+template <typename R>
+int scale_rows(int rows, int cols, const R *d, cx<R> *A, int lda, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_scale_rows<R><<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, d, A, lda);
+    return check_launch("scale rows");
+}
+
+template int residual_precond<double>(int, int, const z64 *, int, const z64 *, int, const double *, const double *,
+                                      z64 *, int, double *, cudaStream_t);
+template int residual_precond<float>(int, int, const z64 *, int, const z64 *, int, const double *, const double *,
+                                     c32 *, int, double *, cudaStream_t);
+template int copy_cast<double, double>(int, int, const z64 *, int, z64 *, int, cudaStream_t);
+template int copy_cast<float, double>(int, int, const z64 *, int, c32 *, int, cudaStream_t);
+template int copy_cast<double, float>(int, int, const c32 *, int, z64 *, int, cudaStream_t);
+template int copy_cast<float, float>(int, int, const c32 *, int, c32 *, int, cudaStream_t);
+template int scale_rows<double>(int, int, const double *, z64 *, int, cudaStream_t);
+template int scale_rows<float>(int, int, const float *, c32 *, int, cudaStream_t);
+
+}  // namespace lg

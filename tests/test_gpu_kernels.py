@@ -1,0 +1,140 @@
+"""Parity of the dense building blocks (GEMMs, FP64 Rayleigh-Ritz, Hermitian
+eigensolver) with FP64 numpy/scipy on odd shapes.
+
+Tolerances: FP64 GEMMs 1e-13 relative to sum |a||b|; FP32 GEMMs 1e-5 relative;
+eigenvalues 1e-12 relative to ||A||; eigenvector residuals 1e-11 ||A||;
+orthonormality 1e-12.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from tests._helpers import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _c(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.mark.parametrize("m,n,K", [(1, 1, 1), (16, 16, 925), (64, 37, 5000), (192, 192, 57925), (432, 19, 3001),
+                                   (7, 130, 100)])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_gemm_cn(m, n, K, prec):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(m * 7 + n)
+    A, B, C0 = _c(rng, K, m), _c(rng, K, n), _c(rng, m, n)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    At = torch.tensor(A.T.copy(), dtype=dt, device="cuda")
+    Bt = torch.tensor(B.T.copy(), dtype=dt, device="cuda")
+    Ct = torch.tensor(C0.T.copy(), dtype=dt, device="cuda")
+    lg.gemm_cn(At, Bt, alpha=0.5, beta=-2.0, C=Ct)
+    got = Ct.cpu().numpy().T
+    ref = 0.5 * A.conj().T @ B - 2.0 * C0
+    scale = 0.5 * np.abs(A).T @ np.abs(B) + 2.0 * np.abs(C0)
+    tol = 1e-13 if prec == "c128" else 1e-5
+    assert (np.abs(got - ref) / scale).max() < tol
+
+
+@pytest.mark.parametrize("M,n,k", [(1, 1, 1), (925, 16, 16), (57925, 64, 128), (3001, 7, 432), (100, 130, 65)])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_gemm_nn(M, n, k, prec):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(M + n + k)
+    A, B, C0 = _c(rng, M, k), _c(rng, k, n), _c(rng, M, n)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    At = torch.tensor(A.T.copy(), dtype=dt, device="cuda")
+    Bt = torch.tensor(B.T.copy(), dtype=dt, device="cuda")
+    Ct = torch.tensor(C0.T.copy(), dtype=dt, device="cuda")
+    D = lg.gemm_nn(At, Bt, alpha=-1.0, beta=1.0, C=Ct, D=Ct)   # in-place accumulate
+    got = D.cpu().numpy().T
+    ref = -A @ B + C0
+    scale = np.abs(A) @ np.abs(B) + np.abs(C0)
+    tol = 1e-13 if prec == "c128" else 1e-5
+    assert (np.abs(got - ref) / scale).max() < tol
+
+
+def _herm(rng, n):
+    A = _c(rng, n, n)
+    return A + A.conj().T
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 33, 48, 192, 257])
+def test_heev(n):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(n)
+    A = _herm(rng, n)
+    w, V = lg.heev(torch.tensor(A.T.copy(), device="cuda"))
+    w = w.cpu().numpy()
+    V = V.cpu().numpy().T                  # columns = eigenvectors
+    nrm = np.abs(A).sum(1).max()
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * nrm
+    assert np.abs(A @ V - V * w[None, :]).max() < 1e-11 * nrm
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() < 1e-12
+
+
+def test_heev_degenerate_clusters():
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(5)
+    n = 60
+    U, _ = np.linalg.qr(_c(rng, n, n))
+    ev = np.concatenate([[0.0] * 6, [1.0] * 12, np.linspace(2, 5, n - 18)])
+    A = (U * ev) @ U.conj().T
+    w, V = lg.heev(torch.tensor(A.T.copy(), device="cuda"))
+    w = w.cpu().numpy()
+    V = V.cpu().numpy().T
+    assert np.abs(w - ev).max() < 1e-12 * 5
+    assert np.abs(A @ V - V * w[None, :]).max() < 1e-11 * 5
+    assert np.abs(V.conj().T @ V - np.eye(n)).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(3, 1), (48, 16), (192, 64), (384, 128)])
+def test_rayleigh_ritz_generalized(n, m):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(n + m)
+    Z = _c(rng, 4 * n, n)
+    H = _herm(rng, 4 * n)
+    S = Z.conj().T @ Z
+    A = Z.conj().T @ H @ Z
+    theta, C, nd = lg.rayleigh_ritz(torch.tensor(S.T.copy(), device="cuda"), torch.tensor(A.T.copy(), device="cuda"), m)
+    theta = theta.cpu().numpy()
+    C = C.cpu().numpy().T
+    ref = scipy.linalg.eigh(A, S, eigvals_only=True)[:m]
+    sc = np.abs(ref).max()
+    assert int(nd.item()) == 0
+    assert np.abs(theta - ref).max() < 1e-10 * sc
+    assert np.abs(C.conj().T @ S @ C - np.eye(m)).max() < 1e-10
+    assert np.abs(A @ C - S @ C * theta[None, :]).max() < 1e-9 * sc * np.abs(S).max()
+
+
+def test_rayleigh_ritz_drops_dependent_columns():
+    """A basis with two (nearly) repeated columns: they are dropped and the Ritz
+    pairs of the remaining subspace are returned."""
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(9)
+    npw = 300
+    X = _c(rng, npw, 6)
+    Z = np.hstack([X, X[:, :2] + 1e-9 * _c(rng, npw, 2), _c(rng, npw, 3)])
+    H = _herm(rng, npw)
+    S = Z.conj().T @ Z
+    A = Z.conj().T @ H @ Z
+    keep = [0, 1, 2, 3, 4, 5, 8, 9, 10]
+    ref = scipy.linalg.eigh(A[np.ix_(keep, keep)], S[np.ix_(keep, keep)], eigvals_only=True)[:4]
+    theta, C, nd = lg.rayleigh_ritz(torch.tensor(S.T.copy(), device="cuda"), torch.tensor(A.T.copy(), device="cuda"),
+                                    4, drop_tol=1e-10)
+    assert int(nd.item()) == 2
+    assert np.abs(theta.cpu().numpy() - ref).max() < 1e-8 * np.abs(ref).max()
+    C = C.cpu().numpy().T
+    assert np.abs(C[[6, 7]]).max() < 1e-12 * np.abs(C).max()
