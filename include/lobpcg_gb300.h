@@ -98,7 +98,17 @@ typedef struct {
     int    autotune;     /* 1: time kernel variants once per shape and keep the fastest */
     double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */
     long long mem_cap;   /* 0: no cap; else maximum bytes the handle may allocate (ERR_OOM above it) */
+    int    timing;       /* 1: time each phase of lobpcg_solve with CUDA events on the handle's stream */
 } lobpcg_options;
+
+/* Phases of a solve, for the per-phase timers of lobpcg_stats. */
+#define LOBPCG_PH_FFT        0   /* V_loc + kinetic through the FFT passes */
+#define LOBPCG_PH_NONLOCAL   1   /* KB projection and back-projection GEMMs */
+#define LOBPCG_PH_GRAM       2   /* Gram matrices of the Rayleigh-Ritz basis */
+#define LOBPCG_PH_CONSTRAINT 3   /* orthogonality constraint against earlier blocks */
+#define LOBPCG_PH_RR         4   /* FP64 Cholesky + Rayleigh-Ritz eigensolves */
+#define LOBPCG_PH_UPDATE     5   /* Ritz updates, residual, preconditioner, casts, copies */
+#define LOBPCG_PH_COUNT      6
 
 typedef struct {
     int    sweeps;            /* sweeps done */
@@ -107,12 +117,15 @@ typedef struct {
     int    restarts;          /* Rayleigh-Ritz basis vectors dropped as dependent */
     double max_resid;         /* final max residual over all k and bands (Ha) */
     double ms_total;          /* wall time of the solve, ms */
-    double ms_apply;          /* time in H applications (CUDA events), ms */
-    double ms_gram;           /* Gram / projection GEMMs, ms */
-    double ms_rr;             /* Cholesky + Rayleigh-Ritz eigensolves, ms */
-    double ms_update;         /* Ritz updates, residual, preconditioner, constraint, ms */
     long long band_applies_fp64;  /* single-band H applications done in FP64 */
     long long band_applies_fp32;  /* single-band H applications done in FP32 */
+    long long kernel_launches;    /* kernels launched by the solve */
+    /* per phase (index LOBPCG_PH_*), filled when options.timing = 1: */
+    double    ph_ms[LOBPCG_PH_COUNT];      /* device time, CUDA events on the handle's stream */
+    double    ph_flops[LOBPCG_PH_COUNT];   /* algorithmic floating-point operations */
+    double    ph_bytes[LOBPCG_PH_COUNT];   /* algorithmic DRAM bytes */
+    long long ph_calls[LOBPCG_PH_COUNT];   /* timed calls */
+    double    ph_fp64_flops[LOBPCG_PH_COUNT];  /* part of ph_flops done in FP64 arithmetic */
 } lobpcg_stats;
 
 /* Fill *opt with defaults: m = 64, nline = 4, max_sweeps = 100, FP64, tol = 1e-8. */
@@ -173,9 +186,11 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
  * block by block with the orthogonality constraint, each sweep closed by an
  * all-band Rayleigh-Ritz step (Sec. 3.2).
  *   nbands     M, a multiple of the block size, 1 <= M <= npw_k for every k.
- *   X          nk device pointers; X[k] is npw_k x M complex128 (column-major).
+ *   X          nk pointers; X[k] is npw_k x M complex128 (column-major).
  *              In: start vectors (any full-rank block).  Out: orthonormal
- *              eigenvectors, ascending eigenvalues.
+ *              eigenvectors, ascending eigenvalues.  Device pointers are used
+ *              in place; host pointers (pinned or pageable) are copied to a
+ *              library device buffer and the result copied back.
  *   eig        host nk x M doubles (out): eigenvalues, ascending per k.
  *   resid      host nk x M doubles (out): ||H x_i - eps_i x_i||_2 in FP64.
  *   stats      optional (NULL allowed) statistics.
@@ -184,6 +199,9 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
  */
 int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid,
                  lobpcg_stats *stats);
+
+/* Number of kernels the library has launched in this process so far (all handles). */
+long long lobpcg_launch_count(void);
 
 /* Message describing the last error on ctx ("" if none); ctx may be NULL for create errors. */
 const char *lobpcg_last_error(const lobpcg_ctx *ctx);

@@ -31,7 +31,7 @@ FP64, MIXED = 0, 1
 EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
-    "lobpcg_last_error", "lobpcg_destroy",
+    "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count",
     "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_heev", "lobpcg_k_last_error",
 )
 
@@ -43,18 +43,29 @@ class Cell(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("nline", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gemm_split", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong)]
+                ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong),
+                ("timing", ctypes.c_int)]
+
+
+PHASES = ("fft", "nonlocal", "gram", "constraint", "rr", "update")
+NPH = len(PHASES)
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("restarts", ctypes.c_int), ("max_resid", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ms_apply", ctypes.c_double), ("ms_gram", ctypes.c_double), ("ms_rr", ctypes.c_double),
-                ("ms_update", ctypes.c_double), ("band_applies_fp64", ctypes.c_longlong),
-                ("band_applies_fp32", ctypes.c_longlong)]
+                ("band_applies_fp64", ctypes.c_longlong), ("band_applies_fp32", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong),
+                ("ph_ms", ctypes.c_double * NPH), ("ph_flops", ctypes.c_double * NPH),
+                ("ph_bytes", ctypes.c_double * NPH), ("ph_calls", ctypes.c_longlong * NPH),
+                ("ph_fp64_flops", ctypes.c_double * NPH)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = {p: v[i] for i, p in enumerate(PHASES)} if f.startswith("ph_") else v
+        return out
 
 
 class LobpcgError(RuntimeError):
@@ -91,6 +102,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_solve": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Stats)]),
         "lobpcg_last_error": (ctypes.c_char_p, [vp]),
         "lobpcg_destroy": (None, [vp]),
+        "lobpcg_launch_count": (ctypes.c_longlong, []),
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
         "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
@@ -156,7 +168,7 @@ class Solver:
 
     def __init__(self, a: float, N: int, ecut: float, kpts, vloc, proj_E=None, beta=None,
                  block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
-                 tol: float = 1e-8, mem_cap: int = 0, stream=None):
+                 tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, stream=None):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -167,7 +179,7 @@ class Solver:
         E = np.ascontiguousarray(np.zeros(0) if proj_E is None else np.asarray(proj_E, dtype=np.float64))
         self.nproj = int(E.shape[0])
         self.nk = int(kp.shape[0])
-        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap)
+        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing)
         cell = Cell(a, N, ecut)
         self._stream = stream
         rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
@@ -182,16 +194,18 @@ class Solver:
                 self.set_projectors(k, beta(self.gvectors(k), k))
 
     @staticmethod
-    def _options(block_size, nline, max_sweeps, precision, tol, mem_cap) -> Options:
+    def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False) -> Options:
         o = default_options()
         o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         o.tol = tol
         o.mem_cap = mem_cap
+        o.timing = 1 if timing else 0
         return o
 
-    def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0):
-        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap)
+    def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0,
+                    timing=False):
+        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing)
         _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
 
     def set_stream(self, stream):
@@ -272,6 +286,11 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(load().lobpcg_launch_count())
 
 
 # ---------------------------------------------------------------- dense building blocks

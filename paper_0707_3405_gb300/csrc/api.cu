@@ -4,8 +4,11 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -24,10 +27,66 @@ const std::string &last_fail() { return g_last_fail; }
 void set_global_error(const std::string &m) { g_last_fail = m; }
 const char *global_error() { return g_last_fail.c_str(); }
 
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+
 int check_launch(const char *what) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LOBPCG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
     return LOBPCG_OK;
+}
+
+cudaEvent_t Prof::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+cudaEvent_t Prof::begin(int) {
+    if (!on) return nullptr;
+    cudaEvent_t a = get();
+    if (a) cudaEventRecord(a, s);
+    return a;
+}
+
+void Prof::end(int ph, cudaEvent_t a, double fl, double by, bool fp64) {
+    if (!on) return;
+    flops[ph] += fl;
+    bytes[ph] += by;
+    if (fp64) fp64_flops[ph] += fl;
+    calls[ph] += 1;
+    cudaEvent_t b = get();
+    if (!a || !b) return;
+    cudaEventRecord(b, s);
+    recs.push_back({ph, a, b});
+    if (recs.size() > 4096) collect();
+}
+
+void Prof::collect() {
+    if (recs.empty()) return;
+    cudaEventSynchronize(recs.back().b);
+    for (auto &r : recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.ph] += t;
+        else cudaGetLastError();
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    recs.clear();
+}
+
+Prof::~Prof() {
+    collect();
+    for (auto e : pool) cudaEventDestroy(e);
 }
 
 int Allocator::alloc(void **p, size_t bytes) {
@@ -110,6 +169,7 @@ struct lobpcg_ctx {
     EigWork ew;
     // solver buffers
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
+    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32;
     std::string err;
 };
 
@@ -237,21 +297,33 @@ template <> struct Tables<float> {
 // Y = H X on device buffers (Sec. 2.2 items iii and iv): FFT route for
 // T + V_loc, then the KB projection B = beta^H X, B <- E B, Y += beta B.
 template <typename R>
-int apply_H_dev(lobpcg_ctx *c, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb) {
+int apply_H_dev(lobpcg_ctx *c, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb, Prof *prof = nullptr) {
     if (nb <= 0) return LOBPCG_OK;
     KPoint &K = c->kp[k];
     const FFTGeom &g = K.geom;
-    const size_t per_band = sizeof(cx<R>) * (size_t)g.Px * g.N * g.N;
+    const bool f64 = sizeof(R) == 8;
+    const size_t cb = sizeof(cx<R>);
+    const size_t per_band = cb * (size_t)g.Px * g.N * g.N;
     int nbatch = (int)std::max<size_t>(1, c->fft_budget / per_band);
     nbatch = std::min(std::min(nbatch, nb), 65535);
     LG_TRY(c->alloc.ensure(c->T2, per_band * nbatch));
-    LG_TRY(fft_vloc_apply<R>(g, c->plan, X, ldx, Y, ldy, nb, Tables<R>::kin(K), Tables<R>::vt(c),
-                             Tables<R>::tw(c), reinterpret_cast<cx<R> *>(c->T2.p), nbatch, c->stream));
+    {
+        // algorithmic DRAM bytes: sphere X read twice (scatter, kinetic), Y written,
+        // kinetic table, half-box written / read-written / read (4 Px N^2), V once per batch
+        const double by = nb * (3.0 * cb * K.npw + sizeof(R) * (double)K.npw + 4.0 * per_band) +
+                          std::ceil((double)nb / nbatch) * sizeof(R) * (double)g.N * g.N * g.N;
+        PhaseScope ps(prof, LOBPCG_PH_FFT, nb * fft_flops_per_band(g), by, f64);
+        LG_TRY(fft_vloc_apply<R>(g, c->plan, X, ldx, Y, ldy, nb, Tables<R>::kin(K), Tables<R>::vt(c),
+                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(c->T2.p), nbatch, c->stream));
+    }
     if (c->nproj > 0) {
         if (!K.has_beta) return fail(LOBPCG_ERR_ARG, "projectors of this k-point were not given");
-        LG_TRY(c->alloc.ensure(c->nlB, sizeof(cx<R>) * (size_t)c->nproj * nb));
+        LG_TRY(c->alloc.ensure(c->nlB, cb * (size_t)c->nproj * nb));
         cx<R> *B = reinterpret_cast<cx<R> *>(c->nlB.p);
         const cx<R> *beta = Tables<R>::beta(K);
+        const double fl = 16.0 * K.npw * (double)c->nproj * nb;
+        const double by = cb * (2.0 * K.npw * c->nproj + 3.0 * K.npw * nb);
+        PhaseScope ps(prof, LOBPCG_PH_NONLOCAL, fl, by, f64);
         LG_TRY(gemm_cn<R>(c->gw, c->nproj, nb, K.npw, (R)1, beta, K.npw, X, ldx, (R)0, B, c->nproj, c->stream));
         LG_TRY(scale_rows<R>(c->nproj, nb, Tables<R>::E(c), B, c->nproj, c->stream));
         LG_TRY(gemm_nn<R>(K.npw, nb, c->nproj, (R)1, beta, K.npw, B, c->nproj, (R)1, Y, ldy, Y, ldy, c->stream));
@@ -269,108 +341,296 @@ bool is_device_ptr(const void *p) {
 }
 
 // ------------------------------------------------------------------ LOBPCG driver
+// Algorithm 1 of the paper (Sec. 3.2) on one k-point, block after block with the
+// orthogonality constraint, each sweep closed by an all-band Rayleigh-Ritz step.
+//
+// FP64 schedule: every vector, product and Gram matrix in FP64.
+//
+// Mixed schedule (the block iteration in FP32 around FP64 X and H X):
+//   * X_b and H X_b are kept in FP64; R = H X_b - X_b Theta is formed in FP64;
+//   * W = K(R), the constraint, H W (FP32 FFT and KB GEMMs), P and H P are FP32;
+//   * W and P are projected out of span(X_b) in FP32, so the Rayleigh-Ritz basis
+//     [X_b, W, P] has X-rows S = [I 0 0], A = [Theta, R^H W, R^H P]: the X-W and
+//     X-P couplings come from the FP64 residual (relatively accurate however small
+//     the residual is), never from X^H H W;
+//   * the Gram blocks of W and P are FP32 GEMMs, the Rayleigh-Ritz solve is FP64;
+//   * X_b <- X_b C_X + P and H X_b <- H X_b C_X + H P are FP64;
+//   * every sweep ends with an FP64 H X refresh, the FP64 all-band Rayleigh-Ritz
+//     step and FP64 residual norms, which decide convergence.
 struct Solver {
     lobpcg_ctx *c;
+    Prof *prof;
     int k, npw, M, m, nblk;
     bool mixed;
-    z64 *X;  // user block, npw x M
-    z64 *Z[2], *HZ[2];
-    c32 *Z32, *HZ32;
-    z64 *HX, *Tmp, *S, *A, *C, *G;
+    cudaStream_t s;
+    z64 *X, *HX;             // all bands, FP64 (X is the caller's buffer)
+    z64 *Z[2], *HZ[2];       // FP64 block bases [X W P] (mixed: only the X part)
+    z64 *Tmp;                // npw x max(M, m) FP64 scratch
+    z64 *S, *A, *C;          // Gram / projected / coefficient matrices, FP64
+    z64 *G;                  // constraint coefficients, FP64
     double *theta, *res, *work;
     int *ndrop;
-    double drop_tol;
+    double drop_tol;          // dependence threshold for FP64 Grams
+    double drop_tol32;        // dependence threshold for FP32 Grams (mixed schedule)
+    // mixed-only FP32 buffers
+    c32 *X32all, *HX32all;   // FP32 copies of X and H X (all bands)
+    c32 *Q32[2], *HQ32[2];   // [R W P] and [. HW HP], npw x 3m
+    c32 *X32, *HX32;         // FP32 copies of X_b, H X_b
+    c32 *S32, *A32, *C32, *G32, *D32;
     long long applies64 = 0, applies32 = 0;
     int iterations = 0;
-    cudaStream_t s;
+    int verbose = 0;          // LOBPCG_VERBOSE: 1 per sweep, 2 per iteration (synchronising diagnostics)
+    std::vector<double> dbg;
+
+    // Diagnostic print of the estimated residual max of a block (FP64 from X, HX).
+    void trace(const char *tag, int b, int it, const z64 *Xb, const z64 *HXb, int nb) {
+        if (verbose < 2) return;
+        dbg.assign(2 * nb + 1, 0.0);
+        double *dres = res;
+        column_resid_norms(npw, nb, Xb, npw, HXb, npw, theta, dres, s);
+        cudaMemcpyAsync(dbg.data(), dres, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(dbg.data() + nb, theta, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
+        int nd = 0;
+        cudaMemcpyAsync(&nd, ndrop, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        double mx = 0.0;
+        for (int i = 0; i < nb; ++i) mx = std::max(mx, dbg[i]);
+        fprintf(stderr, "[lobpcg] k=%d %s block=%d it=%d max_resid_est=%.3e theta0=%.12f dropped=%d\n", k, tag, b,
+                it, mx, dbg[nb], nd);
+    }
 
     z64 *col(z64 *base, int j) const { return base + (size_t)j * npw; }
+    c32 *col(c32 *base, int j) const { return base + (size_t)j * npw; }
+    double cbytes64(double cols) const { return 16.0 * npw * cols; }
+    double cbytes32(double cols) const { return 8.0 * npw * cols; }
 
     int applyH64(const z64 *Xin, z64 *Yout, int nb) {
         applies64 += nb;
-        return apply_H_dev<double>(c, k, Xin, npw, Yout, npw, nb);
+        return apply_H_dev<double>(c, k, Xin, npw, Yout, npw, nb, prof);
     }
-    // H W in FP32 for the mixed schedule: W is rounded to complex64 first and the
-    // rounded W is kept in the basis so that W and HW stay consistent.
-    int applyH32_inplace(z64 *W, z64 *HW, int nb) {
+    int applyH32(const c32 *Xin, c32 *Yout, int nb) {
         applies32 += nb;
-        LG_TRY(copy_cast<float, double>(npw, nb, W, npw, Z32, npw, s));
-        LG_TRY(copy_cast<double, float>(npw, nb, Z32, npw, W, npw, s));
-        LG_TRY(apply_H_dev<float>(c, k, Z32, npw, HZ32, npw, nb));
-        return copy_cast<double, float>(npw, nb, HZ32, npw, HW, npw, s);
+        return apply_H_dev<float>(c, k, Xin, npw, Yout, npw, nb, prof);
+    }
+
+    // ---------------------------------------------------------- FP64 helpers
+    int gemm_cn64(int ph, int mm, int nn, const z64 *Aa, const z64 *Bb, z64 *Cc, int ldc) {
+        PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes64(mm + nn), true);
+        return gemm_cn<double>(c->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
+    }
+    int gemm_nn64(int ph, int nn, int kk, double alpha, const z64 *Aa, const z64 *Bb, int ldb, double beta,
+                  const z64 *Cc, z64 *Dd) {
+        PhaseScope ps(prof, ph, 8.0 * nn * kk * (double)npw, cbytes64(kk + nn * (beta != 0.0 ? 2 : 1)), true);
+        return gemm_nn<double>(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
+    }
+    int gemm_cn32(int ph, int mm, int nn, const c32 *Aa, const c32 *Bb, c32 *Cc, int ldc) {
+        PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes32(mm + nn), false);
+        return gemm_cn<float>(c->gw, mm, nn, npw, 1.0f, Aa, npw, Bb, npw, 0.0f, Cc, ldc, s);
+    }
+    int gemm_nn32(int ph, int nn, int kk, float alpha, const c32 *Aa, const c32 *Bb, int ldb, float beta,
+                  const c32 *Cc, c32 *Dd) {
+        PhaseScope ps(prof, ph, 8.0 * nn * kk * (double)npw, cbytes32(kk + nn * (beta != 0.f ? 2 : 1)), false);
+        return gemm_nn<float>(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
+    }
+    // Rayleigh-Ritz on the pencil in S, A.  `tol` is the dependence threshold on the squared
+    // Cholesky pivot of the unit-diagonal Gram: a kept direction amplifies the Gram's rounding
+    // by 1/pivot^2, so tol is ~1e3 x the Gram's unit roundoff (FP64 Grams 1e-12, FP32 Grams 1e-3).
+    int rr(int nz, int mm, double tol) {
+        const double n3 = (double)nz * nz * nz;
+        PhaseScope ps(prof, LOBPCG_PH_RR, 8.0 * (3.0 * n3 + 2.0 * nz * (double)nz * mm), 0.0, true);
+        return rayleigh_ritz(c->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s);
+    }
+    template <typename Ro, typename Ri>
+    int cast(int cols, const cx<Ri> *a, cx<Ro> *b) {
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, (double)npw * cols * (sizeof(cx<Ri>) + sizeof(cx<Ro>)), false);
+        return copy_cast<Ro, Ri>(npw, cols, a, npw, b, npw, s);
+    }
+    int copy64(z64 *dst, const z64 *src, int cols) {
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 2.0 * cbytes64(cols), false);
+        LG_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(z64) * (size_t)npw * cols, cudaMemcpyDeviceToDevice, s));
+        return LOBPCG_OK;
     }
 
     // V <- V - Y (Y^H V), twice (classical Gram-Schmidt repeated); Y = first j bands.
-    int constrain(z64 *V, int nv, int j) {
+    int constrain64(z64 *V, int nv, int j) {
         if (j <= 0) return LOBPCG_OK;
         for (int rep = 0; rep < 2; ++rep) {
-            LG_TRY(gemm_cn<double>(c->gw, j, nv, npw, 1.0, X, npw, V, npw, 0.0, G, j, s));
-            LG_TRY(gemm_nn<double>(npw, nv, j, -1.0, X, npw, G, j, 1.0, V, npw, V, npw, s));
+            LG_TRY(gemm_cn64(LOBPCG_PH_CONSTRAINT, j, nv, X, V, G, j));
+            LG_TRY(gemm_nn64(LOBPCG_PH_CONSTRAINT, nv, j, -1.0, X, G, j, 1.0, V, V));
+        }
+        return LOBPCG_OK;
+    }
+    int constrain32(c32 *V, int nv, const c32 *Y, int j, int ph) {
+        if (j <= 0) return LOBPCG_OK;
+        for (int rep = 0; rep < 2; ++rep) {
+            LG_TRY(gemm_cn32(ph, j, nv, Y, V, G32, j));
+            LG_TRY(gemm_nn32(ph, nv, j, -1.0f, Y, G32, j, 1.0f, V, V));
         }
         return LOBPCG_OK;
     }
 
-    int gram(const z64 *Zc, const z64 *HZc, int nz) {
-        LG_TRY(gemm_cn<double>(c->gw, nz, nz, npw, 1.0, Zc, npw, Zc, npw, 0.0, S, nz, s));
-        return gemm_cn<double>(c->gw, nz, nz, npw, 1.0, Zc, npw, HZc, npw, 0.0, A, nz, s);
-    }
-
-    int block(int b) {
+    // ---------------------------------------------------------- FP64 block visit
+    int block64(int b) {
         int cur = 0;
         z64 *Xu = col(X, b * m);
-        LG_CUDA_TRY(cudaMemcpyAsync(Z[cur], Xu, sizeof(z64) * (size_t)npw * m, cudaMemcpyDeviceToDevice, s));
-        LG_TRY(constrain(Z[cur], m, b * m));
+        LG_TRY(copy64(Z[cur], Xu, m));
+        LG_TRY(constrain64(Z[cur], m, b * m));
         LG_TRY(applyH64(Z[cur], HZ[cur], m));
         // Rayleigh-Ritz on the block alone: orthonormal Ritz basis, Upsilon (step 1)
-        LG_TRY(gram(Z[cur], HZ[cur], m));
-        LG_TRY(rayleigh_ritz(c->ew, m, m, S, m, A, m, drop_tol, theta, C, m, ndrop, s));
-        LG_TRY(gemm_nn<double>(npw, m, m, 1.0, Z[cur], npw, C, m, 0.0, nullptr, npw, Z[1 - cur], npw, s));
-        LG_TRY(gemm_nn<double>(npw, m, m, 1.0, HZ[cur], npw, C, m, 0.0, nullptr, npw, HZ[1 - cur], npw, s));
+        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Z[cur], Z[cur], S, m));
+        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Z[cur], HZ[cur], A, m));
+        LG_TRY(rr(m, m, drop_tol));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Z[cur], C, m, 0.0, nullptr, Z[1 - cur]));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HZ[cur], C, m, 0.0, nullptr, HZ[1 - cur]));
         cur = 1 - cur;
         int nP = 0;
         for (int it = 0; it < c->opt.nline; ++it) {
             z64 *Zc = Z[cur], *HZc = HZ[cur];
             z64 *W = col(Zc, m), *HW = col(HZc, m);
-            // steps 2-3: R = HX - X Upsilon, W = K(R); constraint against earlier blocks
-            LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, c->kp[k].kin64, W, npw, work, s));
-            LG_TRY(constrain(W, m, b * m));
-            if (mixed) {
-                LG_TRY(applyH32_inplace(W, HW, m));
-            } else {
-                LG_TRY(applyH64(W, HW, m));
+            {   // steps 2-3: R = HX - X Upsilon, W = K(R)
+                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 20.0 * npw * m, cbytes64(3.0 * m), true);
+                LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, c->kp[k].kin64, W, npw, work, s));
             }
+            LG_TRY(constrain64(W, m, b * m));
+            LG_TRY(applyH64(W, HW, m));
             // step 4: Rayleigh-Ritz on span[X, W, P]
             const int nz = (2 + nP) * m;
-            LG_TRY(gram(Zc, HZc, nz));
-            LG_TRY(rayleigh_ritz(c->ew, nz, m, S, nz, A, nz, drop_tol, theta, C, nz, ndrop, s));
-            // steps 4-5: P = W Lambda + P Gamma, X = X Delta + P (and H images)
+            LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, nz, nz, Zc, Zc, S, nz));
+            LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, nz, nz, Zc, HZc, A, nz));
+            LG_TRY(rr(nz, m, drop_tol));
+            // steps 4-5: P = W Lambda + P Gamma, X = X Delta + P (and their H images)
             z64 *Zn = Z[1 - cur], *HZn = HZ[1 - cur];
-            LG_TRY(gemm_nn<double>(npw, m, nz - m, 1.0, col(Zc, m), npw, C + m, nz, 0.0, nullptr, npw, col(Zn, 2 * m),
-                                   npw, s));
-            LG_TRY(gemm_nn<double>(npw, m, m, 1.0, Zc, npw, C, nz, 1.0, col(Zn, 2 * m), npw, Zn, npw, s));
-            LG_TRY(gemm_nn<double>(npw, m, nz - m, 1.0, col(HZc, m), npw, C + m, nz, 0.0, nullptr, npw,
-                                   col(HZn, 2 * m), npw, s));
-            LG_TRY(gemm_nn<double>(npw, m, m, 1.0, HZc, npw, C, nz, 1.0, col(HZn, 2 * m), npw, HZn, npw, s));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, nz - m, 1.0, col(Zc, m), C + m, nz, 0.0, nullptr, col(Zn, 2 * m)));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Zc, C, nz, 1.0, col(Zn, 2 * m), Zn));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, nz - m, 1.0, col(HZc, m), C + m, nz, 0.0, nullptr, col(HZn, 2 * m)));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HZc, C, nz, 1.0, col(HZn, 2 * m), HZn));
             cur = 1 - cur;
             nP = 1;
             ++iterations;
         }
-        LG_CUDA_TRY(cudaMemcpyAsync(Xu, Z[cur], sizeof(z64) * (size_t)npw * m, cudaMemcpyDeviceToDevice, s));
-        LG_CUDA_TRY(cudaMemcpyAsync(col(HX, b * m), HZ[cur], sizeof(z64) * (size_t)npw * m, cudaMemcpyDeviceToDevice, s));
+        LG_TRY(copy64(Xu, Z[cur], m));
+        LG_TRY(copy64(col(HX, b * m), HZ[cur], m));
         return LOBPCG_OK;
+    }
+
+    // ---------------------------------------------------------- mixed block visit
+    int block_mixed(int b) {
+        const int j0 = b * m;
+        int cur = 0;
+        z64 *Xb = Z[cur], *HXb = HZ[cur];
+        LG_TRY(copy64(Xb, col(X, j0), m));
+        LG_TRY(copy64(HXb, col(HX, j0), m));
+        if (b > 0) {
+            // X_b <- X_b - Y (Y^H X_b), H X_b likewise: small corrections, FP32 is enough
+            for (int rep = 0; rep < 2; ++rep) {
+                LG_TRY(cast<float, double>(m, Xb, X32));
+                LG_TRY(gemm_cn32(LOBPCG_PH_CONSTRAINT, j0, m, X32all, X32, G32, j0));
+                LG_TRY(gemm_nn32(LOBPCG_PH_CONSTRAINT, m, j0, 1.0f, X32all, G32, j0, 0.0f, nullptr, D32));
+                LG_TRY(cast<double, float>(m, D32, Tmp));
+                LG_TRY(gemm_nn64_axpy(Xb, Tmp, m));
+                LG_TRY(gemm_nn32(LOBPCG_PH_CONSTRAINT, m, j0, 1.0f, HX32all, G32, j0, 0.0f, nullptr, D32));
+                LG_TRY(cast<double, float>(m, D32, Tmp));
+                LG_TRY(gemm_nn64_axpy(HXb, Tmp, m));
+            }
+        }
+        // block Rayleigh-Ritz from FP32 Grams (X_b is near-orthonormal already)
+        LG_TRY(cast<float, double>(m, Xb, X32));
+        LG_TRY(cast<float, double>(m, HXb, HX32));
+        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, X32, S32, m));
+        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, HX32, A32, m));
+        LG_TRY(assemble_block_start(Xb, HXb));
+        LG_TRY(rr(m, m, drop_tol32));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, m, 0.0, nullptr, Z[1 - cur]));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, m, 0.0, nullptr, HZ[1 - cur]));
+        cur = 1 - cur;
+        trace("mixed-start", b, -1, Z[cur], HZ[cur], m);
+        int nP = 0;
+        for (int it = 0; it < c->opt.nline; ++it) {
+            Xb = Z[cur];
+            HXb = HZ[cur];
+            c32 *Q = Q32[cur], *HQ = HQ32[cur];
+            c32 *R32 = Q, *W32 = col(Q, m), *P32 = col(Q, 2 * m);
+            c32 *HW32 = col(HQ, m), *HP32 = col(HQ, 2 * m);
+            LG_TRY(cast<float, double>(m, Xb, X32));
+            LG_TRY(cast<float, double>(m, HXb, HX32));
+            {   // steps 2-3 in FP64: R = HX - X Upsilon; W = K(R), both stored in FP32
+                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 20.0 * npw * m, cbytes64(2.0 * m) + cbytes32(2.0 * m), true);
+                LG_TRY(residual_precond_mixed(npw, m, Xb, npw, HXb, npw, theta, c->kp[k].kin64, R32, W32, npw,
+                                              work, s));
+            }
+            LG_TRY(constrain32(W32, m, X32all, j0, LOBPCG_PH_CONSTRAINT));
+            LG_TRY(constrain32(W32, m, X32, m, LOBPCG_PH_UPDATE));
+            LG_TRY(applyH32(W32, HW32, m));
+            if (nP) {
+                // P <- P - X (X^H P), H P likewise (FP32)
+                LG_TRY(gemm_cn32(LOBPCG_PH_UPDATE, m, m, X32, P32, G32, m));
+                LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, -1.0f, X32, G32, m, 1.0f, P32, P32));
+                LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, -1.0f, HX32, G32, m, 1.0f, HP32, HP32));
+            }
+            const int nz = (2 + nP) * m, nw = nz - m;
+            // Grams in FP32, assembled in FP64: T1 = [R W P]^H [W P], T2 = [W P]^H [HW HP]
+            LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, nz, nw, Q, W32, S32, nz));
+            LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, nw, nw, W32, HW32, A32, nw));
+            LG_TRY(assemble_iteration(nz));
+            LG_TRY(rr(nz, m, drop_tol32));
+            {
+                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * nz * m, false);
+                LG_TRY(copy_cast<float, double>(nz, m, C, nz, C32, nz, s));
+            }
+            // P = W Lambda + P Gamma, H P likewise (FP32)
+            c32 *Qn = Q32[1 - cur], *HQn = HQ32[1 - cur];
+            LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, nw, 1.0f, W32, C32 + m, nz, 0.0f, nullptr, col(Qn, 2 * m)));
+            LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, nw, 1.0f, HW32, C32 + m, nz, 0.0f, nullptr, col(HQn, 2 * m)));
+            // X = X Delta + P, H X = H X Delta + H P (FP64)
+            LG_TRY(cast<double, float>(m, col(Qn, 2 * m), Tmp));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, nz, 1.0, Tmp, Z[1 - cur]));
+            LG_TRY(cast<double, float>(m, col(HQn, 2 * m), Tmp));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, nz, 1.0, Tmp, HZ[1 - cur]));
+            cur = 1 - cur;
+            nP = 1;
+            ++iterations;
+            trace("mixed", b, it, Z[cur], HZ[cur], m);
+        }
+        LG_TRY(copy64(col(X, j0), Z[cur], m));
+        LG_TRY(copy64(col(HX, j0), HZ[cur], m));
+        LG_TRY(cast<float, double>(m, Z[cur], col(X32all, j0)));
+        LG_TRY(cast<float, double>(m, HZ[cur], col(HX32all, j0)));
+        return LOBPCG_OK;
+    }
+    int gemm_nn64_axpy(z64 *V, const z64 *D, int cols) {
+        PhaseScope ps(prof, LOBPCG_PH_CONSTRAINT, 2.0 * npw * cols, 3.0 * cbytes64(cols), true);
+        return axpy_cols(npw, cols, -1.0, D, npw, V, npw, s);
+    }
+    // FP32 Grams of the block, with exact FP64 Rayleigh quotients on the diagonal: the
+    // Ritz values drive R = HX - X Theta, so they must carry FP64 accuracy.
+    int assemble_block_start(const z64 *Xb, const z64 *HXb) {
+        PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * m, cbytes64(2.0 * m), true);
+        LG_TRY(assemble_gram_mixed(m, 0, S32, m, A32, m, nullptr, S, A, s));
+        return diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s);
+    }
+    int assemble_iteration(int nz) {
+        PhaseScope ps(prof, LOBPCG_PH_RR, 0.0, 0.0, false);
+        return assemble_gram_mixed(nz, m, S32, nz, A32, nz - m, theta, S, A, s);
     }
 
     // Rayleigh-Ritz over all M bands closing a sweep (Sec. 3.2), then FP64 residuals.
     int final_rr(double *eig_h, double *res_h) {
-        if (mixed) LG_TRY(applyH64(X, HX, M));  // FP64 refresh of H X for the residual test
-        LG_TRY(gemm_cn<double>(c->gw, M, M, npw, 1.0, X, npw, X, npw, 0.0, S, M, s));
-        LG_TRY(gemm_cn<double>(c->gw, M, M, npw, 1.0, X, npw, HX, npw, 0.0, A, M, s));
-        LG_TRY(rayleigh_ritz(c->ew, M, M, S, M, A, M, drop_tol, theta, C, M, ndrop, s));
-        LG_TRY(gemm_nn<double>(npw, M, M, 1.0, X, npw, C, M, 0.0, nullptr, npw, Tmp, npw, s));
-        LG_CUDA_TRY(cudaMemcpyAsync(X, Tmp, sizeof(z64) * (size_t)npw * M, cudaMemcpyDeviceToDevice, s));
-        LG_TRY(gemm_nn<double>(npw, M, M, 1.0, HX, npw, C, M, 0.0, nullptr, npw, Tmp, npw, s));
-        LG_CUDA_TRY(cudaMemcpyAsync(HX, Tmp, sizeof(z64) * (size_t)npw * M, cudaMemcpyDeviceToDevice, s));
-        LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
+        if (mixed) LG_TRY(applyH64(X, HX, M));  // FP64 H X for the residual test
+        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, X, S, M));
+        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, HX, A, M));
+        LG_TRY(rr(M, M, drop_tol));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, M, M, 1.0, X, C, M, 0.0, nullptr, Tmp));
+        LG_TRY(copy64(X, Tmp, M));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, M, M, 1.0, HX, C, M, 0.0, nullptr, Tmp));
+        LG_TRY(copy64(HX, Tmp, M));
+        {
+            PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * M, cbytes64(2.0 * M), true);
+            LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
+        }
+        if (mixed) {
+            LG_TRY(cast<float, double>(M, X, X32all));
+            LG_TRY(cast<float, double>(M, HX, HX32all));
+        }
         LG_CUDA_TRY(cudaMemcpyAsync(eig_h, theta, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
         LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
         LG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -384,10 +644,11 @@ T *carve(lobpcg_ctx *c, DevBuf &b, size_t count, int &rc) {
     return reinterpret_cast<T *>(b.p);
 }
 
-int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, int &sweeps_done, long long &a64,
-            long long &a32, int &iters) {
+int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, int &sweeps_done, Prof *prof,
+            long long &a64, long long &a32, int &iters) {
     Solver sv;
     sv.c = c;
+    sv.prof = prof;
     sv.k = k;
     sv.npw = c->kp[k].npw;
     sv.M = M;
@@ -396,18 +657,17 @@ int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, i
     sv.mixed = c->opt.precision == LOBPCG_MIXED;
     sv.X = X;
     sv.s = c->stream;
-    sv.drop_tol = sv.mixed ? 1e-10 : 1e-12;
+    sv.drop_tol = 1e-12;
+    sv.drop_tol32 = 1e-3;
+    if (const char *v = std::getenv("LOBPCG_VERBOSE")) sv.verbose = std::atoi(v);
     const int npw = sv.npw, m = sv.m;
     const int nzmax = std::max(3 * m, M);
     int rc = 0;
+    const int zcols = sv.mixed ? m : 3 * m;
     for (int i = 0; i < 2; ++i) {
-        sv.Z[i] = carve<z64>(c, c->Zb[i], (size_t)npw * 3 * m, rc);
-        LG_TRY(rc);
-        sv.HZ[i] = carve<z64>(c, c->HZb[i], (size_t)npw * 3 * m, rc);
-        LG_TRY(rc);
+        sv.Z[i] = carve<z64>(c, c->Zb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
+        sv.HZ[i] = carve<z64>(c, c->HZb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
     }
-    sv.Z32 = carve<c32>(c, c->Z32, (size_t)npw * m, rc); LG_TRY(rc);
-    sv.HZ32 = carve<c32>(c, c->HZ32, (size_t)npw * m, rc); LG_TRY(rc);
     sv.HX = carve<z64>(c, c->HXall, (size_t)npw * M, rc); LG_TRY(rc);
     sv.Tmp = carve<z64>(c, c->Tmp, (size_t)npw * M, rc); LG_TRY(rc);
     sv.S = carve<z64>(c, c->Gram, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
@@ -419,14 +679,36 @@ int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, i
     double *w = carve<double>(c, c->dwork, 4 * (size_t)nzmax + 64, rc); LG_TRY(rc);
     sv.work = w;
     sv.ndrop = reinterpret_cast<int *>(w + 4 * (size_t)nzmax);
+    if (sv.mixed) {
+        sv.X32all = carve<c32>(c, c->X32all, (size_t)npw * M, rc); LG_TRY(rc);
+        sv.HX32all = carve<c32>(c, c->HX32all, (size_t)npw * M, rc); LG_TRY(rc);
+        for (int i = 0; i < 2; ++i) {
+            sv.Q32[i] = carve<c32>(c, c->Q32[i], (size_t)npw * 3 * m, rc); LG_TRY(rc);
+            sv.HQ32[i] = carve<c32>(c, c->HQ32[i], (size_t)npw * 3 * m, rc); LG_TRY(rc);
+        }
+        sv.X32 = carve<c32>(c, c->Z32, (size_t)npw * m, rc); LG_TRY(rc);
+        sv.HX32 = carve<c32>(c, c->HZ32, (size_t)npw * m, rc); LG_TRY(rc);
+        sv.D32 = carve<c32>(c, c->D32, (size_t)npw * m, rc); LG_TRY(rc);
+        c32 *sm = carve<c32>(c, c->Small32, 4 * (size_t)nzmax * nzmax + (size_t)M * m, rc); LG_TRY(rc);
+        sv.S32 = sm;
+        sv.A32 = sm + (size_t)nzmax * nzmax;
+        sv.C32 = sm + 2 * (size_t)nzmax * nzmax;
+        sv.G32 = sm + 4 * (size_t)nzmax * nzmax;
+        // H X of the start vectors, and the FP32 copies the constraint uses
+        LG_TRY(sv.applyH64(X, sv.HX, M));
+        LG_TRY(sv.cast<float, double>(M, X, sv.X32all));
+        LG_TRY(sv.cast<float, double>(M, sv.HX, sv.HX32all));
+    }
     sweeps_done = 0;
     double maxr = 0.0;
     for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
-        for (int b = 0; b < sv.nblk; ++b) LG_TRY(sv.block(b));
+        for (int b = 0; b < sv.nblk; ++b) LG_TRY(sv.mixed ? sv.block_mixed(b) : sv.block64(b));
         LG_TRY(sv.final_rr(eig_h, res_h));
+        if (prof) prof->collect();
         ++sweeps_done;
         maxr = 0.0;
         for (int i = 0; i < M; ++i) maxr = std::max(maxr, res_h[i]);
+        if (sv.verbose >= 1) fprintf(stderr, "[lobpcg] k=%d sweep=%d max_resid=%.3e\n", k, sw, maxr);
         if (!(maxr == maxr)) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite residual");
         if (maxr <= c->opt.tol) break;
     }
@@ -463,6 +745,7 @@ int lobpcg_default_options(lobpcg_options *opt) {
     opt->autotune = 0;
     opt->tol = 1e-8;
     opt->mem_cap = 0;
+    opt->timing = 0;
     return LOBPCG_OK;
 }
 
@@ -631,21 +914,38 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         if (!X[k]) return fail(LOBPCG_ERR_ARG, "X[k] is NULL");
         if (M > c->kp[k].npw) return fail(LOBPCG_ERR_ARG, "nbands exceeds the plane-wave count");
         if (c->nproj > 0 && !c->kp[k].has_beta) return fail(LOBPCG_ERR_ARG, "projectors missing for a k-point");
-        if (!is_device_ptr(X[k])) return fail(LOBPCG_ERR_ARG, "X[k] must be a device pointer");
     }
     const auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = launch_count();
     int worst = LOBPCG_OK, sweeps = 0, iters = 0;
     long long a64 = 0, a32 = 0;
     double maxr = 0.0;
+    Prof prof;
+    prof.on = c->opt.timing != 0;
+    prof.s = c->stream;
     for (int k = 0; k < c->nk; ++k) {
         int sw = 0;
-        int rc = solve_k(c, k, M, static_cast<z64 *>(X[k]), eig + (size_t)k * M, resid + (size_t)k * M, sw, a64, a32,
-                         iters);
+        // host start vectors are staged through a device buffer and copied back
+        const bool host = !is_device_ptr(X[k]);
+        const size_t bytes = sizeof(z64) * (size_t)c->kp[k].npw * M;
+        z64 *Xd = static_cast<z64 *>(X[k]);
+        if (host) {
+            LG_TRY(c->alloc.ensure(c->stageX, bytes));
+            Xd = static_cast<z64 *>(c->stageX.p);
+            LG_CUDA_TRY(cudaMemcpyAsync(Xd, X[k], bytes, cudaMemcpyHostToDevice, c->stream));
+        }
+        int rc = solve_k(c, k, M, Xd, eig + (size_t)k * M, resid + (size_t)k * M, sw, prof.on ? &prof : nullptr,
+                         a64, a32, iters);
         if (rc < 0) return rc;
+        if (host) {
+            LG_CUDA_TRY(cudaMemcpyAsync(X[k], Xd, bytes, cudaMemcpyDeviceToHost, c->stream));
+            LG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        }
         if (rc == LOBPCG_NOT_CONVERGED) worst = rc;
         sweeps = std::max(sweeps, sw);
         for (int i = 0; i < M; ++i) maxr = std::max(maxr, resid[(size_t)k * M + i]);
     }
+    prof.collect();
     if (st) {
         std::memset(st, 0, sizeof(*st));
         st->sweeps = sweeps;
@@ -655,6 +955,14 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         st->band_applies_fp64 = a64;
         st->band_applies_fp32 = a32;
+        st->kernel_launches = launch_count() - l0;
+        for (int p = 0; p < LOBPCG_PH_COUNT; ++p) {
+            st->ph_ms[p] = prof.ms[p];
+            st->ph_flops[p] = prof.flops[p];
+            st->ph_bytes[p] = prof.bytes[p];
+            st->ph_calls[p] = prof.calls[p];
+            st->ph_fp64_flops[p] = prof.fp64_flops[p];
+        }
     }
     return worst;
 }
@@ -663,6 +971,8 @@ int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, doubl
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
     return ret(ctx, solve_impl(ctx, nbands, X, eig, resid, stats));
 }
+
+long long lobpcg_launch_count(void) { return launch_count(); }
 
 const char *lobpcg_last_error(const lobpcg_ctx *ctx) {
     if (!ctx) return global_error();
@@ -676,7 +986,8 @@ void lobpcg_destroy(lobpcg_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->T2, &ctx->nlB, &ctx->stageX, &ctx->stageY, &ctx->Zb[0], &ctx->Zb[1], &ctx->HZb[0],
                       &ctx->HZb[1], &ctx->Z32, &ctx->HZ32, &ctx->HXall, &ctx->Tmp, &ctx->Gram, &ctx->Gram2,
                       &ctx->Cbuf, &ctx->dtheta, &ctx->dres, &ctx->dwork, &ctx->Gc, &ctx->gw.part, &ctx->ew.buf,
-                      &ctx->ew.ibuf, &ctx->ew.gw.part};
+                      &ctx->ew.ibuf, &ctx->ew.gw.part, &ctx->X32all, &ctx->HX32all, &ctx->Q32[0], &ctx->Q32[1],
+                      &ctx->HQ32[0], &ctx->HQ32[1], &ctx->D32, &ctx->Small32};
     for (DevBuf *b : bufs) ctx->alloc.release(*b);
     delete ctx;
 }

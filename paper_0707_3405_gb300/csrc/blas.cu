@@ -5,9 +5,10 @@
 //
 // One tiled kernel serves every operand form: op(A) and op(B) are either the
 // matrix or its conjugate transpose, chosen at compile time so that tile
-// loads stay coalesced.  64 x 64 output tile, K step 16, 256 threads, each
-// thread owning a 4 x 4 register tile (rows tx + 16 i, columns ty + 16 j, so
-// stores to column-major C are coalesced).  A long reduction dimension is
+// loads stay coalesced.  K step 16, 256 threads, each thread owning a T x T
+// register tile (rows tx + 16 i, columns ty + 16 j, so stores to column-major
+// C are coalesced): 64 x 64 output tiles for tall-skinny and large products,
+// 32 x 32 for the small dense ones.  A long reduction dimension is
 // split over grid.z; the partial tiles are summed afterwards in a fixed
 // order, so results are bitwise reproducible.
 #include "common.cuh"
@@ -18,13 +19,20 @@ namespace lg {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TH = 256;
+constexpr int BK = 16, TH = 256;
 
-template <typename R, bool CA, bool CB>
+// T x T register tile per thread, 16 x 16 threads: (16 T) x (16 T) output tile.
+// FP32 products are accumulated in FP32 for at most KFLUSH terms and then added
+// into FP64 accumulators, so that long reductions (the plane-wave count) keep
+// about 1e-6 relative accuracy; split partial sums are FP64.
+constexpr int KFLUSH = 256;
+
+template <typename R, bool CA, bool CB, int T>
 __global__ void __launch_bounds__(TH)
 k_gemm(int m, int n, int K, int kchunk, R alpha, const cx<R> *__restrict__ A, int lda,
        const cx<R> *__restrict__ B, int ldb, R beta, const cx<R> *C, int ldc, cx<R> *D, int ldd,
-       cx<R> *__restrict__ part) {
+       z64 *__restrict__ part) {
+    constexpr int BM = 16 * T, BN = 16 * T;
     __shared__ cx<R> As[BK][BM + 1];
     __shared__ cx<R> Bs[BK][BN + 1];
     const int tid = threadIdx.x;
@@ -33,11 +41,20 @@ k_gemm(int m, int n, int K, int kchunk, R alpha, const cx<R> *__restrict__ A, in
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
     const cx<R> zero = mkc<R>(0, 0);
-    cx<R> acc[4][4];
+    constexpr bool F32 = sizeof(R) == 4;
+    cx<R> acc[T][T];
+    z64 acc64[F32 ? T : 1][F32 ? T : 1];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < T; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = zero;
+        for (int j = 0; j < T; ++j) acc[i][j] = zero;
+    if (F32) {
+#pragma unroll
+        for (int i = 0; i < (F32 ? T : 1); ++i)
+#pragma unroll
+            for (int j = 0; j < (F32 ? T : 1); ++j) acc64[i][j] = mkc(0.0, 0.0);
+    }
+    int since_flush = 0;
 
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
@@ -63,48 +80,63 @@ k_gemm(int m, int n, int K, int kchunk, R alpha, const cx<R> *__restrict__ A, in
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            cx<R> a[4], b[4];
+            cx<R> a[T], b[T];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < T; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+            for (int j = 0; j < T; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < T; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) fma_nn(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < T; ++j) fma_nn(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
+        if (F32) {
+            since_flush += BK;
+            if (since_flush >= KFLUSH) {
+                since_flush = 0;
+#pragma unroll
+                for (int i = 0; i < (F32 ? T : 1); ++i)
+#pragma unroll
+                    for (int j = 0; j < (F32 ? T : 1); ++j) {
+                        acc64[i][j] = acc64[i][j] + cvt<double, R>(acc[i][j]);
+                        acc[i][j] = zero;
+                    }
+            }
+        }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < T; ++j) {
         const int gj = j0 + ty + 16 * j;
         if (gj >= n) continue;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < T; ++i) {
             const int gi = i0 + tx + 16 * i;
             if (gi >= m) continue;
+            z64 t = cvt<double, R>(acc[i][j]);
+            if (F32) t = t + acc64[F32 ? i : 0][F32 ? j : 0];
             if (part) {
-                part[((size_t)blockIdx.z * n + gj) * m + gi] = acc[i][j];
+                part[((size_t)blockIdx.z * n + gj) * m + gi] = t;
             } else {
-                cx<R> v = alpha * acc[i][j];
-                if (beta != (R)0) v = v + beta * C[(size_t)gj * ldc + gi];
-                D[(size_t)gj * ldd + gi] = v;
+                z64 v = (double)alpha * t;
+                if (beta != (R)0) v = v + (double)beta * cvt<double, R>(C[(size_t)gj * ldc + gi]);
+                D[(size_t)gj * ldd + gi] = cvt<R, double>(v);
             }
         }
     }
 }
 
 template <typename R>
-__global__ void k_reduce_parts(int m, int n, int nsplit, R alpha, const cx<R> *__restrict__ part, R beta,
+__global__ void k_reduce_parts(int m, int n, int nsplit, R alpha, const z64 *__restrict__ part, R beta,
                                const cx<R> *C, int ldc, cx<R> *D, int ldd) {
     const size_t tot = (size_t)m * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
         const int gi = (int)(e % m), gj = (int)(e / m);
-        cx<R> s = part[e];
+        z64 s = part[e];
         for (int z = 1; z < nsplit; ++z) s = s + part[(size_t)z * tot + e];
-        cx<R> v = alpha * s;
-        if (beta != (R)0) v = v + beta * C[(size_t)gj * ldc + gi];
-        D[(size_t)gj * ldd + gi] = v;
+        z64 v = (double)alpha * s;
+        if (beta != (R)0) v = v + (double)beta * cvt<double, R>(C[(size_t)gj * ldc + gi]);
+        D[(size_t)gj * ldd + gi] = cvt<R, double>(v);
     }
 }
 
@@ -119,16 +151,19 @@ int num_sms() {
 }
 
 // Launch op(A) op(B) with an optional split of the reduction dimension.
-template <typename R, bool CA, bool CB>
-int launch_gemm(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
-                R beta, const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s, bool allow_split) {
+// Small products use 32 x 32 tiles so that they still spread over the GPU.
+template <typename R, bool CA, bool CB, int T>
+int launch_gemm_t(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
+                  R beta, const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s, bool allow_split,
+                  int min_chunk) {
+    constexpr int BM = 16 * T, BN = 16 * T;
     if (m <= 0 || n <= 0) return LOBPCG_OK;
     const int tm = (m + BM - 1) / BM, tn = (n + BN - 1) / BN;
     const int tiles = tm * tn;
     int nsplit = 1;
-    if (allow_split && w && K > 4 * BK) {
+    if (allow_split && w && K > min_chunk) {
         const int want = (2 * num_sms() + tiles - 1) / tiles;
-        const int maxs = (K + 4 * BK - 1) / (4 * BK);
+        const int maxs = (K + min_chunk - 1) / min_chunk;
         nsplit = std::max(1, std::min(want, maxs));
     }
     if (K <= 0) nsplit = 1;
@@ -137,20 +172,31 @@ int launch_gemm(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int l
     if (kchunk <= 0) kchunk = BK;
     nsplit = K > 0 ? (K + kchunk - 1) / kchunk : 1;
     if (nsplit == 1) {
-        k_gemm<R, CA, CB><<<dim3(tm, tn, 1), TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, D,
-                                                         ldd, nullptr);
+        k_gemm<R, CA, CB, T><<<dim3(tm, tn, 1), TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                            D, ldd, nullptr);
         return check_launch("gemm");
     }
-    const size_t need = sizeof(cx<R>) * (size_t)nsplit * m * n;
+    const size_t need = sizeof(z64) * (size_t)nsplit * m * n;
     LG_TRY(w->alloc->ensure(w->part, need));
-    cx<R> *part = reinterpret_cast<cx<R> *>(w->part.p);
-    k_gemm<R, CA, CB><<<dim3(tm, tn, nsplit), TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, D,
-                                                          ldd, part);
+    z64 *part = reinterpret_cast<z64 *>(w->part.p);
+    k_gemm<R, CA, CB, T><<<dim3(tm, tn, nsplit), TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                             D, ldd, part);
     LG_TRY(check_launch("gemm split"));
     const size_t tot = (size_t)m * n;
     const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
     k_reduce_parts<R><<<blocks, 256, 0, s>>>(m, n, nsplit, alpha, part, beta, C, ldc, D, ldd);
     return check_launch("gemm reduce");
+}
+
+template <typename R, bool CA, bool CB>
+int launch_gemm(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
+                R beta, const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s, bool allow_split) {
+    // tall-skinny and large products: 64 x 64 tiles; small dense ones: 32 x 32 tiles + fine split
+    if ((long long)m * n <= 512LL * 512LL && K <= 8192)
+        return launch_gemm_t<R, CA, CB, 2>(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, allow_split,
+                                           2 * BK);
+    return launch_gemm_t<R, CA, CB, 4>(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, allow_split,
+                                       4 * BK);
 }
 
 }  // namespace
@@ -167,13 +213,14 @@ int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *
     return launch_gemm<R, false, false>(nullptr, M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, false);
 }
 
-int zgemm_small(char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda, const z64 *B,
-                int ldb, double beta, z64 *C, int ldc, cudaStream_t s) {
+int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
+                const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s) {
     const bool ca = (opA == 'C'), cb = (opB == 'C');
-    if (!ca && !cb) return launch_gemm<double, false, false>(nullptr, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, false);
-    if (ca && !cb) return launch_gemm<double, true, false>(nullptr, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, false);
-    if (!ca && cb) return launch_gemm<double, false, true>(nullptr, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, false);
-    return launch_gemm<double, true, true>(nullptr, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, false);
+    const bool sp = w != nullptr;
+    if (!ca && !cb) return launch_gemm<double, false, false>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
+    if (ca && !cb) return launch_gemm<double, true, false>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
+    if (!ca && cb) return launch_gemm<double, false, true>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
+    return launch_gemm<double, true, true>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
 }
 
 template int gemm_cn<double>(GemmWork &, int, int, int, double, const z64 *, int, const z64 *, int, double, z64 *,

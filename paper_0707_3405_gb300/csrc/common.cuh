@@ -89,8 +89,44 @@ int fail(int code, const std::string &m);
 // Message recorded by the last fail() on this host thread.
 const std::string &last_fail();
 
-// Checks a kernel launch (configuration errors are reported at launch time).
+// Checks a kernel launch (configuration errors are reported at launch time) and
+// counts it in the process-wide launch counter.
 int check_launch(const char *what);
+long long launch_count();
+
+// ------------------------------------------------------------------ phase timers
+// CUDA-event timing of solver phases on one stream (no-op when disabled).
+struct Prof {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    struct Rec { int ph; cudaEvent_t a, b; };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    double ms[LOBPCG_PH_COUNT] = {0};
+    double flops[LOBPCG_PH_COUNT] = {0};
+    double fp64_flops[LOBPCG_PH_COUNT] = {0};
+    double bytes[LOBPCG_PH_COUNT] = {0};
+    long long calls[LOBPCG_PH_COUNT] = {0};
+    cudaEvent_t get();
+    // Start timing phase `ph`; returns the start event (nullptr when off).
+    cudaEvent_t begin(int ph);
+    void end(int ph, cudaEvent_t a, double fl, double by, bool fp64);
+    // Wait for the recorded events and add their durations to ms[].
+    void collect();
+    ~Prof();
+};
+
+// RAII scope of one timed phase.
+struct PhaseScope {
+    Prof *p;
+    int ph;
+    double fl, by;
+    bool f64;
+    cudaEvent_t a;
+    PhaseScope(Prof *p_, int ph_, double fl_, double by_, bool f64_)
+        : p(p_), ph(ph_), fl(fl_), by(by_), f64(f64_), a(p_ ? p_->begin(ph_) : nullptr) {}
+    ~PhaseScope() { if (p) p->end(ph, a, fl, by, f64); }
+};
 
 // ------------------------------------------------------------------ device memory
 // A grow-only device buffer owned by the library.
@@ -116,6 +152,7 @@ struct FFTGeom {
     int Px = 0, Py = 0;           // active x planes and y rows of the sphere
     int nx0 = 0, ny0 = 0;         // signed index of plane 0 / row 0
     int npw = 0;
+    long long zlines = 0;         // occupied z-lines summed over planes (FFTs in passes A and C)
     // device tables
     int *plane_begin = nullptr;   // Px+1: sphere range of each x plane
     int2 *plane_yrange = nullptr; // Px: [py_lo, py_hi] rows holding coefficients
@@ -139,6 +176,9 @@ template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy,
                    int nb, const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch,
                    cudaStream_t s);
+// Algorithmic floating-point operations of the three passes for one band
+// (5 n log2 n per length-n complex line FFT, plus the V and T multiplies).
+double fft_flops_per_band(const FFTGeom &g);
 // Shared memory the passes need; 0 when the grid does not fit on one SM.
 template <typename R>
 size_t fft_smem_need(const FFTGeom &g);
@@ -156,7 +196,8 @@ template <typename R>
 int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb, R beta,
             const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s);
 // Small general complex128 product: C = alpha op(A) op(B) + beta C, op in {'N','C'}.
-int zgemm_small(char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
+// w (nullable) enables a split of the reduction dimension.
+int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
                 const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s);
 
 // ------------------------------------------------------------------ dense FP64 eigen-solvers
@@ -178,6 +219,16 @@ int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V
 template <typename R>
 int residual_precond(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
                      const double *kin, cx<R> *W, int ldw, double *work, cudaStream_t s);
+// Mixed schedule: R = HX - X theta (FP64) stored in FP32, and W = K(R) in FP32.
+int residual_precond_mixed(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
+                           const double *kin, c32 *R, c32 *W, int ld, double *work, cudaStream_t s);
+// V += alpha D (FP64 columns).
+int axpy_cols(int rows, int cols, double alpha, const z64 *D, int ldd, z64 *V, int ldv, cudaStream_t s);
+// Assemble the FP64 Rayleigh-Ritz pencil of the mixed schedule (see api.cu).
+int assemble_gram_mixed(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
+                        z64 *S, z64 *A, cudaStream_t s);
+// Overwrite diag(S) = diag(X^H X), diag(A) = diag(X^H HX) in FP64 (m x m, ld m).
+int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, cudaStream_t s);
 int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
                        double *out, cudaStream_t s);
 template <typename Ro, typename Ri>

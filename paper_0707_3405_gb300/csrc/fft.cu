@@ -22,6 +22,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cmath>
 
 namespace lg {
 
@@ -353,6 +354,14 @@ int pick_zc(const FFTGeom &g) {
 }
 
 }  // namespace
+
+double fft_flops_per_band(const FFTGeom &g) {
+    const double N = g.N;
+    const double line = 5.0 * N * std::log2(N);
+    // pass A: occupied z-lines + Px N y-lines; pass B: 2 N^2 x-lines; pass C as A
+    const double lines = 2.0 * (double)g.zlines + 2.0 * g.Px * N + 2.0 * N * N;
+    return lines * line + 2.0 * N * N * N + 8.0 * g.npw;
+}
 
 template <typename R>
 size_t fft_smem_need(const FFTGeom &g) {

@@ -635,7 +635,7 @@ int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A,
             LG_TRY(check_launch("cholesky panel"));
             const z64 *L21 = Ss + (size_t)k0 * n + k0 + kb;
             z64 *S22 = Ss + (size_t)(k0 + kb) * n + k0 + kb;
-            LG_TRY(zgemm_small('N', 'C', rem, rem, kb, -1.0, L21, n, L21, n, 1.0, S22, n, s));
+            LG_TRY(zgemm_small(&w.gw, 'N', 'C', rem, rem, kb, -1.0, L21, n, L21, n, 1.0, S22, n, s));
         }
     }
     k_zero_dropped_rows<<<n, 128, 0, s>>>(n, Ss, dr);
@@ -644,20 +644,20 @@ int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A,
     for (int r0 = NBK; r0 < n; r0 += NBK) {
         const int kb = std::min(NBK, n - r0);
         // Tm(kb x r0) = L[r0:r0+kb, 0:r0] * Li[0:r0, 0:r0]
-        LG_TRY(zgemm_small('N', 'N', kb, r0, r0, 1.0, Ss + r0, n, Li, n, 0.0, Tm, n, s));
+        LG_TRY(zgemm_small(&w.gw, 'N', 'N', kb, r0, r0, 1.0, Ss + r0, n, Li, n, 0.0, Tm, n, s));
         // Li[r0:r0+kb, 0:r0] = -Li_rr * Tm
-        LG_TRY(zgemm_small('N', 'N', kb, r0, kb, -1.0, Li + (size_t)r0 * n + r0, n, Tm, n, 0.0, Li + r0, n, s));
+        LG_TRY(zgemm_small(&w.gw, 'N', 'N', kb, r0, kb, -1.0, Li + (size_t)r0 * n + r0, n, Tm, n, 0.0, Li + r0, n, s));
     }
     // Ahat = Li As Li^H
-    LG_TRY(zgemm_small('N', 'N', n, n, n, 1.0, Li, n, As, n, 0.0, Tm, n, s));
-    LG_TRY(zgemm_small('N', 'C', n, n, n, 1.0, Tm, n, Li, n, 0.0, As, n, s));
+    LG_TRY(zgemm_small(&w.gw, 'N', 'N', n, n, n, 1.0, Li, n, As, n, 0.0, Tm, n, s));
+    LG_TRY(zgemm_small(&w.gw, 'N', 'C', n, n, n, 1.0, Tm, n, Li, n, 0.0, As, n, s));
     k_hermitize_rowsum<<<n, 128, 0, s>>>(n, As, dr, rs);
     LG_TRY(check_launch("hermitize"));
     k_set_dropped_diag<<<1, 1024, 0, s>>>(n, As, dr, nd, rs);
     LG_TRY(check_launch("dropped diag"));
     LG_TRY(heev_lowest(w, n, m, As, n, theta, Q, n, s));
     // C = D Li^H Q
-    LG_TRY(zgemm_small('C', 'N', n, m, n, 1.0, Li, n, Q, n, 0.0, Tm, n, s));
+    LG_TRY(zgemm_small(&w.gw, 'C', 'N', n, m, n, 1.0, Li, n, Q, n, 0.0, Tm, n, s));
     k_scale_rows_copy<<<dim3((n + 127) / 128, m), 128, 0, s>>>(n, m, d, Tm, n, C, ldc);
     LG_TRY(check_launch("scale C"));
     if (ndropped) {

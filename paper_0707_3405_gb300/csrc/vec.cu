@@ -67,6 +67,93 @@ __global__ void k_resid_precond(int npw, int m, const z64 *__restrict__ X, int l
     }
 }
 
+// Mixed schedule: R = HX - theta X in FP64, stored in FP32 together with W = K(R).
+__global__ void k_resid_precond_mixed(int npw, int m, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX,
+                                      int ldhx, const double *__restrict__ theta, const double *__restrict__ kin,
+                                      const double *__restrict__ ekin, c32 *__restrict__ R, c32 *__restrict__ W,
+                                      int ld) {
+    const int j = blockIdx.y;
+    const double th = theta[j];
+    const double ie = 1.0 / ekin[j];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+        const z64 x = X[(size_t)j * ldx + g], hx = HX[(size_t)j * ldhx + g];
+        const double t = kin[g] * ie;
+        const double p = 27.0 + t * (18.0 + t * (12.0 + 8.0 * t));
+        const double t2 = t * t;
+        const double k = p / (p + 16.0 * t2 * t2);
+        const double rx = hx.x - th * x.x, ry = hx.y - th * x.y;
+        R[(size_t)j * ld + g] = mkc<float>((float)rx, (float)ry);
+        W[(size_t)j * ld + g] = mkc<float>((float)(k * rx), (float)(k * ry));
+    }
+}
+
+__global__ void k_axpy_cols(int rows, int cols, double alpha, const z64 *__restrict__ D, int ldd, z64 *__restrict__ V,
+                            int ldv) {
+    const size_t tot = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        const z64 d = D[(size_t)j * ldd + i];
+        z64 &v = V[(size_t)j * ldv + i];
+        v = mkc(v.x + alpha * d.x, v.y + alpha * d.y);
+    }
+}
+
+// nz x nz pencil of the mixed schedule.
+//   mx = 0: S = S32 (ld lds32), A = A32 (ld lda32), both full FP32 Grams.
+//   mx > 0: the basis is [X W P] with X the orthonormal Ritz block (mx columns)
+//     and [W P] projected out of span(X).  T1 = S32 = [R W P]^H [W P] (nz x nw,
+//     ld lds32) and T2 = A32 = [W P]^H [HW HP] (nw x nw, ld lda32), nw = nz - mx:
+//     S = [[I, 0], [0, T1[mx:, :]]],  A = [[diag(theta), T1[:mx, :]], [T1[:mx, :]^H, T2]].
+__global__ void k_assemble(int nz, int mx, const c32 *__restrict__ S32, int lds32, const c32 *__restrict__ A32,
+                           int lda32, const double *__restrict__ theta, z64 *__restrict__ S, z64 *__restrict__ A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nz) return;
+    z64 s, a;
+    if (mx == 0) {
+        s = cvt<double, float>(S32[(size_t)j * lds32 + i]);
+        a = cvt<double, float>(A32[(size_t)j * lda32 + i]);
+    } else if (i < mx && j < mx) {
+        s = mkc(i == j ? 1.0 : 0.0, 0.0);
+        a = mkc(i == j ? theta[i] : 0.0, 0.0);
+    } else if (i >= mx && j >= mx) {
+        if (i >= j) {
+            s = cvt<double, float>(S32[(size_t)(j - mx) * lds32 + i]);
+            a = cvt<double, float>(A32[(size_t)(j - mx) * lda32 + (i - mx)]);
+        } else {
+            s = conjc(cvt<double, float>(S32[(size_t)(i - mx) * lds32 + j]));
+            a = conjc(cvt<double, float>(A32[(size_t)(i - mx) * lda32 + (j - mx)]));
+        }
+    } else if (j < mx) {  // i >= mx > j: conj(R_j^H Q_i)
+        s = mkc(0.0, 0.0);
+        a = conjc(cvt<double, float>(S32[(size_t)(i - mx) * lds32 + j]));
+    } else {              // i < mx <= j: R_i^H Q_j
+        s = mkc(0.0, 0.0);
+        a = cvt<double, float>(S32[(size_t)(j - mx) * lds32 + i]);
+    }
+    S[(size_t)j * nz + i] = s;
+    A[(size_t)j * nz + i] = a;
+}
+
+// FP64 diagonals of X^H X and X^H HX (one block per column) written onto the
+// diagonals of the FP64 pencil S, A (ld n): exact Rayleigh quotients for the
+// block-start Rayleigh-Ritz of the mixed schedule.
+__global__ void __launch_bounds__(256)
+k_diag_pencil(int npw, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX, int ldhx, z64 *__restrict__ S,
+              z64 *__restrict__ A, int n) {
+    const int j = blockIdx.x;
+    double xx = 0.0, xh = 0.0;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+        const z64 x = X[(size_t)j * ldx + g], h = HX[(size_t)j * ldhx + g];
+        xx += abs2(x);
+        xh += x.x * h.x + x.y * h.y;
+    }
+    block_sum2(xx, xh);
+    if (threadIdx.x == 0) {
+        S[(size_t)j * n + j] = mkc(xx, 0.0);
+        A[(size_t)j * n + j] = mkc(xh, 0.0);
+    }
+}
+
 // ||HX_j - theta_j X_j|| / ||X_j|| (one block per column, FP64).
 __global__ void __launch_bounds__(256)
 k_resid_norm(int npw, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX, int ldhx,
@@ -118,6 +205,34 @@ int residual_precond(int npw, int m, const z64 *X, int ldx, const z64 *HX, int l
     const int gx = std::max(1, std::min((npw + 255) / 256, 64));
     k_resid_precond<R><<<dim3(gx, m), 256, 0, s>>>(npw, m, X, ldx, HX, ldhx, theta, kin, work, W, ldw);
     return check_launch("residual/preconditioner");
+}
+
+int residual_precond_mixed(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
+                           const double *kin, c32 *R, c32 *W, int ld, double *work, cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, work);
+    LG_TRY(check_launch("ekin"));
+    const int gx = std::max(1, std::min((npw + 255) / 256, 64));
+    k_resid_precond_mixed<<<dim3(gx, m), 256, 0, s>>>(npw, m, X, ldx, HX, ldhx, theta, kin, work, R, W, ld);
+    return check_launch("residual/preconditioner (mixed)");
+}
+
+int axpy_cols(int rows, int cols, double alpha, const z64 *D, int ldd, z64 *V, int ldv, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_axpy_cols<<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, alpha, D, ldd, V, ldv);
+    return check_launch("axpy");
+}
+
+int assemble_gram_mixed(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
+                        z64 *S, z64 *A, cudaStream_t s) {
+    k_assemble<<<dim3((nz + 127) / 128, nz), 128, 0, s>>>(nz, mx, S32, lds32, A32, lda32, theta, S, A);
+    return check_launch("assemble gram");
+}
+
+int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    k_diag_pencil<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, S, A, m);
+    return check_launch("diagonal of the pencil");
 }
 
 int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,

@@ -99,11 +99,22 @@ def test_solve_argument_errors():
         with pytest.raises(lg.LobpcgError) as e:
             s.solve([X], nbands=10)                     # not a multiple of the block
         assert e.value.code == lg.ERR_ARG
-        with pytest.raises(lg.LobpcgError):
-            s.solve([X.cpu()])                          # host pointer
         with pytest.raises(lg.LobpcgError) as e:
             s.set_options(block_size=0)
         assert e.value.code == lg.ERR_ARG
+
+
+def test_solve_host_start_vectors_match_device():
+    """Host (numpy) start vectors are staged by the library: same result as device ones."""
+    import torch
+    w = synth.make_workload("gamma24")
+    with make_solver(w, block_size=16, nline=4, max_sweeps=3, tol=1e-30) as s:
+        Xd = _start(w, s)
+        Xh = Xd.cpu().numpy().copy()
+        rd = s.solve([Xd])
+        rh = s.solve([Xh])
+        assert np.array_equal(rd.eig, rh.eig)
+        assert np.array_equal(Xd.cpu().numpy(), Xh)
 
 
 def test_memory_cap_returns_oom():
