@@ -182,6 +182,27 @@ int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller);
 int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int precision);
 
 /*
+ * Allocation-free Y = (T + V_loc) X for nb bands of k-point k.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run (code inside another framework's memory pool
+ * or under a fixed device-memory budget, loops that must not touch the
+ * allocator because allocation can synchronise the device).  It runs the same
+ * FFT passes as lobpcg_apply_H, without the KB projector part, and allocates
+ * nothing: the FFT half-box lives in a 32 MiB file-scope device array that
+ * every GPU loading the library holds until the process exits.
+ *   X, Y       device pointers only, npw_k x nb column-major, complex128
+ *              (precision = LOBPCG_C128) or complex64 (LOBPCG_C64); must not overlap.
+ *   limit      one band's half-box, Px * N^2 complex numbers (Px = x-planes the
+ *              sphere occupies, about N/2 + 1), must fit in 32 MiB, else
+ *              LOBPCG_ERR_ARG; bands are processed in batches that fit.
+ * The first call on each device looks up the array's device address (host code
+ * cannot use the array's name as an address), so make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU
+ * race on it.  Errors: ERR_ARG, ERR_CUDA; the message is lobpcg_last_error(NULL).
+ */
+int lobpcg_apply_local_noalloc(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int precision);
+
+/*
  * Lowest nbands eigenpairs of every k-point by block LOBPCG (Algorithm 1),
  * block by block with the orthogonality constraint, each sweep closed by an
  * all-band Rayleigh-Ritz step (Sec. 3.2).

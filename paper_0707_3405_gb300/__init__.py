@@ -31,7 +31,7 @@ FP64, MIXED = 0, 1
 EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
-    "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count",
+    "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
     "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_heev", "lobpcg_k_last_error",
 )
 
@@ -103,6 +103,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_last_error": (ctypes.c_char_p, [vp]),
         "lobpcg_destroy": (None, [vp]),
         "lobpcg_launch_count": (ctypes.c_longlong, []),
+        "lobpcg_apply_local_noalloc": (i, [vp, i, vp, vp, i, i]),
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
         "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
@@ -251,6 +252,17 @@ class Solver:
         if nb and X.shape[-1] != self.npw(k):
             raise ValueError("X must have shape (nb, npw_k)")
         _check(self._lib.lobpcg_apply_H(self.handle, k, _ptr(X), _ptr(Y), nb, prec), self.handle)
+        return Y
+
+    def apply_local_noalloc(self, k: int, X, Y):
+        """Y = (T + V_loc) X without any device allocation (the library's fixed
+        32 MiB scratch array holds the FFT half-box).  X and Y are (nb, npw)
+        CUDA tensors, complex128 or complex64."""
+        import torch
+        prec = C128 if X.dtype == torch.complex128 else C64
+        rc = self._lib.lobpcg_apply_local_noalloc(self.handle, k, _ptr(X), _ptr(Y), int(X.shape[0]), prec)
+        if rc < 0:
+            raise LobpcgError(rc, (self._lib.lobpcg_last_error(None) or b"").decode(errors="replace"))
         return Y
 
     def solve(self, X, nbands: int | None = None) -> SolveResult:

@@ -867,6 +867,30 @@ int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller) {
     return LOBPCG_OK;
 }
 
+}  // extern "C"
+
+namespace lg {
+int ctx_local_view(const lobpcg_ctx *c, int k, LocalView *v) {
+    if (!c || !v) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
+    if (k < 0 || k >= c->nk) return fail(LOBPCG_ERR_ARG, "k out of range");
+    const KPoint &K = c->kp[k];
+    v->geom = &K.geom;
+    v->plan = &c->plan;
+    v->npw = K.npw;
+    v->kin64 = K.kin64;
+    v->kin32 = K.kin32;
+    v->vt64 = c->vt64;
+    v->vt32 = c->vt32;
+    v->tw64 = c->tw64;
+    v->tw32 = c->tw32;
+    v->stream = c->stream;
+    return LOBPCG_OK;
+}
+bool is_device_pointer(const void *p) { return is_device_ptr(p); }
+}  // namespace lg
+
+extern "C" {
+
 static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int precision) {
     if (k < 0 || k >= c->nk) return fail(LOBPCG_ERR_ARG, "k out of range");
     if (nb < 0) return fail(LOBPCG_ERR_ARG, "nb must be >= 0");

@@ -183,6 +183,24 @@ double fft_flops_per_band(const FFTGeom &g);
 template <typename R>
 size_t fft_smem_need(const FFTGeom &g);
 
+// Read-only view of one k-point's FFT tables inside a handle (for entry points
+// that run the FFT passes on scratch they own).
+struct LocalView {
+    const FFTGeom *geom = nullptr;
+    const FFTPlan *plan = nullptr;
+    int npw = 0;
+    const double *kin64 = nullptr, *vt64 = nullptr;
+    const float *kin32 = nullptr, *vt32 = nullptr;
+    const z64 *tw64 = nullptr;
+    const c32 *tw32 = nullptr;
+    cudaStream_t stream = nullptr;
+};
+}  // namespace lg
+struct lobpcg_ctx;
+namespace lg {
+int ctx_local_view(const lobpcg_ctx *c, int k, LocalView *v);
+bool is_device_pointer(const void *p);
+
 // ------------------------------------------------------------------ BLAS-like kernels
 // Scratch for split-K partial sums (grown on demand).
 struct GemmWork {
