@@ -51,7 +51,38 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ttt-max-sweeps", type=int, default=120)
+    ap.add_argument("--ncu", action="store_true",
+                    help="profiling run: only the warm-up and timed steps of --mode, no other legs")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "apply"],
+                    help="with --ncu: time LOBPCG sweeps or standalone apply_H on all bands")
     return ap.parse_args()
+
+
+def ncu_run(args):
+    """Minimal launch sequence for ncu captures: build the handle, then
+    warm-up + timed steps of one kind (prints a short JSON line, not a bench value)."""
+    import torch
+    import paper_0707_3405_gb300 as lg
+    import __graft_entry__
+    __graft_entry__.build()
+    w = make(args.workload)
+    s = solver_for(w, args.precision, timing=False, max_sweeps=1, tol=1e-30)
+    X = start_block(w, s)
+    if args.mode == "apply" and args.precision == "mixed":
+        X = X.to(torch.complex64)
+    Y = torch.empty_like(X)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.warmup + args.steps):
+        if args.mode == "sweep":
+            s.solve([X])
+        else:
+            s.apply_H(0, X, Y)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_run": True, "mode": args.mode, "precision": args.precision, "workload": w.name,
+                      "launches": lg.launch_count(), "s": time.perf_counter() - t0}))
+    s.close()
+    return 0
 
 
 def peaks():
@@ -236,6 +267,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu:
+        return ncu_run(args)
     import torch
     import paper_0707_3405_gb300 as lg
     import __graft_entry__

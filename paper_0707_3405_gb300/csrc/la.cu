@@ -386,27 +386,37 @@ __device__ void tri_bounds(const double *__restrict__ d, const double *__restric
     hi += pad;
 }
 
-// One warp per eigenvalue index k < m: 32 Sturm counts per round narrow the bracket 33-fold.
+// Four lanes per eigenvalue index k < m (eight eigenvalues per warp): each round
+// the group evaluates 4 Sturm counts inside the bracket and keeps the fifth of it
+// that holds eigenvalue k.  FP64 divisions are scarce on this GPU, so few lanes per
+// eigenvalue (less total work) beat wide multisection (fewer rounds).
+constexpr int kMsG = 4;
 __global__ void k_multisect(int n, int m, const double *__restrict__ d, const double *__restrict__ e,
                             double *__restrict__ theta) {
-    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int gid = (int)((blockIdx.x * blockDim.x + threadIdx.x) / kMsG);
+    const int sub = threadIdx.x & (kMsG - 1);
     const int lane = threadIdx.x & 31;
-    if (k >= m) return;
+    const int base = lane & ~(kMsG - 1);
+    const bool active = gid < m;
+    const int k = active ? gid : m - 1;
     double lo, hi, tnorm, pivmin;
     tri_bounds(d, e, n, lo, hi, tnorm, pivmin);
-    for (int it = 0; it < 16; ++it) {
+    for (int it = 0; it < 48; ++it) {
         const double w = hi - lo;
-        if (w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
-        const double x = lo + w * (double)(lane + 1) / 33.0;
-        const int c = sturm_count(d, e, n, x, pivmin);
+        const bool done = w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin;
+        if (__all_sync(0xffffffffu, done)) break;
+        const double x = lo + w * (double)(sub + 1) / (double)(kMsG + 1);
+        const int c = done ? 0 : sturm_count(d, e, n, x, pivmin);
         const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
-        const int T = __popc(mask) - 1;  // counts are monotone: lanes 0..T have c <= k
-        const double xlo = __shfl_sync(0xffffffffu, x, T < 0 ? 0 : T);
-        const double xhi = __shfl_sync(0xffffffffu, x, T < 31 ? T + 1 : 31);
-        if (T >= 0) lo = xlo;
-        if (T < 31) hi = xhi;
+        const int T = __popc((mask >> base) & ((1u << kMsG) - 1u)) - 1;  // counts are monotone in sub
+        const double xlo = __shfl_sync(0xffffffffu, x, base + (T < 0 ? 0 : T));
+        const double xhi = __shfl_sync(0xffffffffu, x, base + (T < kMsG - 1 ? T + 1 : kMsG - 1));
+        if (!done) {
+            if (T >= 0) lo = xlo;
+            if (T < kMsG - 1) hi = xhi;
+        }
     }
-    if (lane == 0) theta[k] = 0.5 * (lo + hi);
+    if (active && sub == 0) theta[k] = 0.5 * (lo + hi);
 }
 
 // ------------------------------------------------------------------ eigenvectors (inverse iteration)
@@ -573,7 +583,7 @@ int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V
     }
     k_tri_last<<<1, 32, 0, s>>>(n, A, lda, dg);
     LG_TRY(check_launch("tridiag last"));
-    k_multisect<<<(m + 7) / 8, 256, 0, s>>>(n, m, dg, eg, theta);
+    k_multisect<<<(m * kMsG + 255) / 256, 256, 0, s>>>(n, m, dg, eg, theta);
     LG_TRY(check_launch("multisection"));
     k_inviter<<<(m + 63) / 64, 64, 0, s>>>(n, m, dg, eg, theta, Z, sc, pv);
     LG_TRY(check_launch("inverse iteration"));
