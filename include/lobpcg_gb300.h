@@ -99,6 +99,11 @@ typedef struct {
     double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */
     long long mem_cap;   /* 0: no cap; else maximum bytes the handle may allocate (ERR_OOM above it) */
     int    timing;       /* 1: time each phase of lobpcg_solve with CUDA events on the handle's stream */
+    int    nbuf;         /* extra buffer bands iterated above the M requested ones but not required to
+                            converge (rounded up to whole blocks; 0 = none).  They give the top wanted
+                            bands a gap to the unresolved spectrum. */
+    double mixed_switch; /* MIXED only: a block whose smallest residual after the previous sweep is
+                            below this (Ha) runs its iterations in FP64 (default 1e-6; 0 = never) */
 } lobpcg_options;
 
 /* Phases of a solve, for the per-phase timers of lobpcg_stats. */
@@ -126,6 +131,8 @@ typedef struct {
     double    ph_bytes[LOBPCG_PH_COUNT];   /* algorithmic DRAM bytes */
     long long ph_calls[LOBPCG_PH_COUNT];   /* timed calls */
     double    ph_fp64_flops[LOBPCG_PH_COUNT];  /* part of ph_flops done in FP64 arithmetic */
+    long long block_visits_fp32;  /* block visits run with the mixed FP32/FP64 schedule */
+    long long block_visits_fp64;  /* block visits run entirely in FP64 */
 } lobpcg_stats;
 
 /* Fill *opt with defaults: m = 64, nline = 4, max_sweeps = 100, FP64, tol = 1e-8. */

@@ -70,6 +70,15 @@ int lobpcg_k_rayleigh_ritz(int n, int m, const void *S, const void *A, double dr
                            double *theta, void *C, int *ndropped, void *stream);
 
 /*
+ * The same Rayleigh-Ritz step in FP32 arithmetic: S, A and C are complex64
+ * (n x n and n x m, column-major), theta is float.  The mixed-precision
+ * schedule uses it inside the block iterations, where only the search
+ * subspace, not the final eigenvalues, depends on it.
+ */
+int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double drop_tol,
+                             float *theta, void *C, int *ndropped, void *stream);
+
+/*
  * Hermitian eigen-decomposition in FP64: A = V diag(w) V^H, eigenvalues ascending.
  *   A   (device, n x n complex128, ld n; lower triangle used, not modified),
  *   w   (device, n doubles), V (device, n x n complex128, ld n).

@@ -32,7 +32,7 @@ EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
-    "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_heev", "lobpcg_k_last_error",
+    "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev", "lobpcg_k_last_error",
 )
 
 
@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("nline", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gemm_split", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("nbuf", ctypes.c_int), ("mixed_switch", ctypes.c_double)]
 
 
 PHASES = ("fft", "nonlocal", "gram", "constraint", "rr", "update")
@@ -58,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong),
                 ("ph_ms", ctypes.c_double * NPH), ("ph_flops", ctypes.c_double * NPH),
                 ("ph_bytes", ctypes.c_double * NPH), ("ph_calls", ctypes.c_longlong * NPH),
-                ("ph_fp64_flops", ctypes.c_double * NPH)]
+                ("ph_fp64_flops", ctypes.c_double * NPH),
+                ("block_visits_fp32", ctypes.c_longlong), ("block_visits_fp64", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -107,6 +108,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
         "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
+        "lobpcg_k_rayleigh_ritz32": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_heev": (i, [i, vp, vp, vp, vp]),
         "lobpcg_k_last_error": (ctypes.c_char_p, []),
     }
@@ -169,7 +171,8 @@ class Solver:
 
     def __init__(self, a: float, N: int, ecut: float, kpts, vloc, proj_E=None, beta=None,
                  block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
-                 tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, stream=None):
+                 tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, nbuf: int = 0,
+                 mixed_switch: float | None = None, stream=None):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -180,7 +183,7 @@ class Solver:
         E = np.ascontiguousarray(np.zeros(0) if proj_E is None else np.asarray(proj_E, dtype=np.float64))
         self.nproj = int(E.shape[0])
         self.nk = int(kp.shape[0])
-        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing)
+        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch)
         cell = Cell(a, N, ecut)
         self._stream = stream
         rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
@@ -195,18 +198,22 @@ class Solver:
                 self.set_projectors(k, beta(self.gvectors(k), k))
 
     @staticmethod
-    def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False) -> Options:
+    def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False, nbuf=0,
+                 mixed_switch=None) -> Options:
         o = default_options()
         o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         o.tol = tol
         o.mem_cap = mem_cap
         o.timing = 1 if timing else 0
+        o.nbuf = nbuf
+        if mixed_switch is not None:
+            o.mixed_switch = mixed_switch
         return o
 
     def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0,
-                    timing=False):
-        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing)
+                    timing=False, nbuf=0, mixed_switch=None):
+        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch)
         _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
 
     def set_stream(self, stream):
@@ -349,6 +356,19 @@ def rayleigh_ritz(S, A, m, drop_tol=1e-12, stream=None):
     nd = torch.zeros(1, dtype=torch.int32, device=S.device)
     _check(lib.lobpcg_k_rayleigh_ritz(n, m, _ptr(S), _ptr(A), drop_tol, _ptr(theta), _ptr(C), _ptr(nd),
                                       _stream_handle(stream)), None, kernels=True)
+    return theta, C, nd
+
+
+def rayleigh_ritz32(S, A, m, drop_tol=1e-3, stream=None):
+    """FP32 version of rayleigh_ritz on complex64 CUDA tensors (column-major)."""
+    import torch
+    lib = load()
+    n = S.shape[0]
+    theta = torch.empty(m, dtype=torch.float32, device=S.device)
+    C = torch.empty((m, n), dtype=torch.complex64, device=S.device)
+    nd = torch.zeros(1, dtype=torch.int32, device=S.device)
+    _check(lib.lobpcg_k_rayleigh_ritz32(n, m, _ptr(S), _ptr(A), drop_tol, _ptr(theta), _ptr(C), _ptr(nd),
+                                        _stream_handle(stream)), None, kernels=True)
     return theta, C, nd
 
 

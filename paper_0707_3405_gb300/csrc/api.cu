@@ -169,7 +169,7 @@ struct lobpcg_ctx {
     EigWork ew;
     // solver buffers
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
-    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32;
+    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext;
     std::string err;
 };
 
@@ -377,6 +377,8 @@ struct Solver {
     c32 *Q32[2], *HQ32[2];   // [R W P] and [. HW HP], npw x 3m
     c32 *X32, *HX32;         // FP32 copies of X_b, H X_b
     c32 *S32, *A32, *C32, *G32, *D32;
+    c32 *S32p, *A32p;        // FP32 Rayleigh-Ritz pencil (nz x nz)
+    float *theta32;          // FP32 Ritz values (only the FP64 Rayleigh quotients are used)
     long long applies64 = 0, applies32 = 0;
     int iterations = 0;
     int verbose = 0;          // LOBPCG_VERBOSE: 1 per sweep, 2 per iteration (synchronising diagnostics)
@@ -514,6 +516,18 @@ struct Solver {
     }
 
     // ---------------------------------------------------------- mixed block visit
+    // Rayleigh-Ritz of the mixed schedule: FP32 Gram blocks assembled into an FP64 pencil,
+    // solved in FP64; the coefficients also come back in FP32 for the FP32 updates.
+    int rr_mixed(int nz, int mm) {
+        LG_TRY(rr(nz, mm, drop_tol32));
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * nz * mm, false);
+        return copy_cast<float, double>(nz, mm, C, nz, C32, nz, s);
+    }
+    int ritz_values(const z64 *Xb, const z64 *HXb) {
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * m, cbytes64(2.0 * m), true);
+        return rayleigh_quotients(npw, m, Xb, npw, HXb, npw, theta, s);
+    }
+
     int block_mixed(int b) {
         const int j0 = b * m;
         int cur = 0;
@@ -533,12 +547,16 @@ struct Solver {
                 LG_TRY(gemm_nn64_axpy(HXb, Tmp, m));
             }
         }
-        // block Rayleigh-Ritz from FP32 Grams (X_b is near-orthonormal already)
+        // block Rayleigh-Ritz from FP32 Grams, solved in FP32; rotation in FP64
         LG_TRY(cast<float, double>(m, Xb, X32));
         LG_TRY(cast<float, double>(m, HXb, HX32));
         LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, X32, S32, m));
         LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, HX32, A32, m));
-        LG_TRY(assemble_block_start(Xb, HXb));
+        {
+            PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * m, cbytes64(2.0 * m), true);
+            LG_TRY(assemble_gram_mixed(m, 0, S32, m, A32, m, nullptr, S, A, s));
+            LG_TRY(diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s));
+        }
         LG_TRY(rr(m, m, drop_tol32));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, m, 0.0, nullptr, Z[1 - cur]));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, m, 0.0, nullptr, HZ[1 - cur]));
@@ -553,10 +571,16 @@ struct Solver {
             c32 *HW32 = col(HQ, m), *HP32 = col(HQ, 2 * m);
             LG_TRY(cast<float, double>(m, Xb, X32));
             LG_TRY(cast<float, double>(m, HXb, HX32));
-            {   // steps 2-3 in FP64: R = HX - X Upsilon; W = K(R), both stored in FP32
-                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 20.0 * npw * m, cbytes64(2.0 * m) + cbytes32(2.0 * m), true);
-                LG_TRY(residual_precond_mixed(npw, m, Xb, npw, HXb, npw, theta, c->kp[k].kin64, R32, W32, npw,
-                                              work, s));
+            // step 1: exact FP64 Rayleigh quotients of the current block
+            LG_TRY(ritz_values(Xb, HXb));
+            {   // step 2: R = HX - X Upsilon in FP64, stored FP32, then projected out of span(X) in FP32
+                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 4.0 * npw * m, cbytes64(2.0 * m) + cbytes32(m), true);
+                LG_TRY(residual32(npw, m, Xb, npw, HXb, npw, theta, R32, npw, s));
+            }
+            LG_TRY(constrain32(R32, m, X32, m, LOBPCG_PH_UPDATE));
+            {   // step 3: W = K(R)
+                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 10.0 * npw * m, cbytes64(m) + 2.0 * cbytes32(m), false);
+                LG_TRY(precond32(npw, m, Xb, npw, c->kp[k].kin64, R32, npw, W32, npw, work, s));
             }
             LG_TRY(constrain32(W32, m, X32all, j0, LOBPCG_PH_CONSTRAINT));
             LG_TRY(constrain32(W32, m, X32, m, LOBPCG_PH_UPDATE));
@@ -568,16 +592,15 @@ struct Solver {
                 LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, -1.0f, HX32, G32, m, 1.0f, HP32, HP32));
             }
             const int nz = (2 + nP) * m, nw = nz - m;
-            // Grams in FP32, assembled in FP64: T1 = [R W P]^H [W P], T2 = [W P]^H [HW HP]
+            // step 4: Grams in FP32: T1 = [R W P]^H [W P], T2 = [W P]^H [HW HP]; FP32 pencil; FP32 RR
             LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, nz, nw, Q, W32, S32, nz));
             LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, nw, nw, W32, HW32, A32, nw));
-            LG_TRY(assemble_iteration(nz));
-            LG_TRY(rr(nz, m, drop_tol32));
             {
-                PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * nz * m, false);
-                LG_TRY(copy_cast<float, double>(nz, m, C, nz, C32, nz, s));
+                PhaseScope ps(prof, LOBPCG_PH_RR, 0.0, 0.0, false);
+                LG_TRY(assemble_gram_mixed(nz, m, S32, nz, A32, nw, theta, S, A, s));
             }
-            // P = W Lambda + P Gamma, H P likewise (FP32)
+            LG_TRY(rr_mixed(nz, m));
+            // step 5: P = W Lambda + P Gamma, H P likewise (FP32)
             c32 *Qn = Q32[1 - cur], *HQn = HQ32[1 - cur];
             LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, nw, 1.0f, W32, C32 + m, nz, 0.0f, nullptr, col(Qn, 2 * m)));
             LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, nw, 1.0f, HW32, C32 + m, nz, 0.0f, nullptr, col(HQn, 2 * m)));
@@ -589,7 +612,10 @@ struct Solver {
             cur = 1 - cur;
             nP = 1;
             ++iterations;
-            trace("mixed", b, it, Z[cur], HZ[cur], m);
+            if (verbose >= 2) {
+                LG_TRY(ritz_values(Z[cur], HZ[cur]));
+                trace("mixed", b, it, Z[cur], HZ[cur], m);
+            }
         }
         LG_TRY(copy64(col(X, j0), Z[cur], m));
         LG_TRY(copy64(col(HX, j0), HZ[cur], m));
@@ -597,22 +623,15 @@ struct Solver {
         LG_TRY(cast<float, double>(m, HZ[cur], col(HX32all, j0)));
         return LOBPCG_OK;
     }
+    // FP32 copies of block b (read by the constraint of later mixed blocks) after an FP64 visit
+    int refresh32(int b) {
+        LG_TRY(cast<float, double>(m, col(X, b * m), col(X32all, b * m)));
+        return cast<float, double>(m, col(HX, b * m), col(HX32all, b * m));
+    }
     int gemm_nn64_axpy(z64 *V, const z64 *D, int cols) {
         PhaseScope ps(prof, LOBPCG_PH_CONSTRAINT, 2.0 * npw * cols, 3.0 * cbytes64(cols), true);
         return axpy_cols(npw, cols, -1.0, D, npw, V, npw, s);
     }
-    // FP32 Grams of the block, with exact FP64 Rayleigh quotients on the diagonal: the
-    // Ritz values drive R = HX - X Theta, so they must carry FP64 accuracy.
-    int assemble_block_start(const z64 *Xb, const z64 *HXb) {
-        PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * m, cbytes64(2.0 * m), true);
-        LG_TRY(assemble_gram_mixed(m, 0, S32, m, A32, m, nullptr, S, A, s));
-        return diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s);
-    }
-    int assemble_iteration(int nz) {
-        PhaseScope ps(prof, LOBPCG_PH_RR, 0.0, 0.0, false);
-        return assemble_gram_mixed(nz, m, S32, nz, A32, nz - m, theta, S, A, s);
-    }
-
     // Rayleigh-Ritz over all M bands closing a sweep (Sec. 3.2), then FP64 residuals.
     int final_rr(double *eig_h, double *res_h) {
         if (mixed) LG_TRY(applyH64(X, HX, M));  // FP64 H X for the residual test
@@ -644,8 +663,15 @@ T *carve(lobpcg_ctx *c, DevBuf &b, size_t count, int &rc) {
     return reinterpret_cast<T *>(b.p);
 }
 
-int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, int &sweeps_done, Prof *prof,
-            long long &a64, long long &a32, int &iters) {
+struct SolveCounters {
+    long long a64 = 0, a32 = 0;          // single-band H applications (FP64, FP32)
+    long long visits32 = 0, visits64 = 0;  // block visits per precision
+    int iters = 0;                       // Algorithm 1 iterations
+};
+
+// Solve one k-point for M bands of which the first Mreq must converge (the rest are buffer bands).
+int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h, int &sweeps_done,
+            Prof *prof, SolveCounters &cnt) {
     Solver sv;
     sv.c = c;
     sv.prof = prof;
@@ -663,7 +689,7 @@ int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, i
     const int npw = sv.npw, m = sv.m;
     const int nzmax = std::max(3 * m, M);
     int rc = 0;
-    const int zcols = sv.mixed ? m : 3 * m;
+    const int zcols = 3 * m;   // a mixed solve visits converged blocks in FP64
     for (int i = 0; i < 2; ++i) {
         sv.Z[i] = carve<z64>(c, c->Zb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
         sv.HZ[i] = carve<z64>(c, c->HZb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
@@ -689,11 +715,14 @@ int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, i
         sv.X32 = carve<c32>(c, c->Z32, (size_t)npw * m, rc); LG_TRY(rc);
         sv.HX32 = carve<c32>(c, c->HZ32, (size_t)npw * m, rc); LG_TRY(rc);
         sv.D32 = carve<c32>(c, c->D32, (size_t)npw * m, rc); LG_TRY(rc);
-        c32 *sm = carve<c32>(c, c->Small32, 4 * (size_t)nzmax * nzmax + (size_t)M * m, rc); LG_TRY(rc);
+        c32 *sm = carve<c32>(c, c->Small32, 6 * (size_t)nzmax * nzmax + (size_t)M * m + nzmax, rc); LG_TRY(rc);
         sv.S32 = sm;
         sv.A32 = sm + (size_t)nzmax * nzmax;
         sv.C32 = sm + 2 * (size_t)nzmax * nzmax;
-        sv.G32 = sm + 4 * (size_t)nzmax * nzmax;
+        sv.S32p = sm + 3 * (size_t)nzmax * nzmax;
+        sv.A32p = sm + 4 * (size_t)nzmax * nzmax;
+        sv.G32 = sm + 5 * (size_t)nzmax * nzmax;
+        sv.theta32 = reinterpret_cast<float *>(sm + 5 * (size_t)nzmax * nzmax + (size_t)M * m);
         // H X of the start vectors, and the FP32 copies the constraint uses
         LG_TRY(sv.applyH64(X, sv.HX, M));
         LG_TRY(sv.cast<float, double>(M, X, sv.X32all));
@@ -701,20 +730,38 @@ int solve_k(lobpcg_ctx *c, int k, int M, z64 *X, double *eig_h, double *res_h, i
     }
     sweeps_done = 0;
     double maxr = 0.0;
+    // residuals of the previous sweep choose each block's precision in a mixed solve
+    std::vector<double> res_prev(M, HUGE_VAL);
     for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
-        for (int b = 0; b < sv.nblk; ++b) LG_TRY(sv.mixed ? sv.block_mixed(b) : sv.block64(b));
+        for (int b = 0; b < sv.nblk; ++b) {
+            double rmin = HUGE_VAL;
+            for (int i = b * m; i < (b + 1) * m; ++i) rmin = std::min(rmin, res_prev[i]);
+            if (sv.mixed && !(rmin < c->opt.mixed_switch)) {
+                LG_TRY(sv.block_mixed(b));
+                ++cnt.visits32;
+            } else {
+                LG_TRY(sv.block64(b));
+                if (sv.mixed) LG_TRY(sv.refresh32(b));
+                ++cnt.visits64;
+            }
+        }
         LG_TRY(sv.final_rr(eig_h, res_h));
         if (prof) prof->collect();
         ++sweeps_done;
         maxr = 0.0;
-        for (int i = 0; i < M; ++i) maxr = std::max(maxr, res_h[i]);
+        bool finite = true;
+        for (int i = 0; i < Mreq; ++i) {
+            finite = finite && std::isfinite(res_h[i]) && std::isfinite(eig_h[i]);
+            maxr = std::max(maxr, res_h[i]);
+        }
         if (sv.verbose >= 1) fprintf(stderr, "[lobpcg] k=%d sweep=%d max_resid=%.3e\n", k, sw, maxr);
-        if (!(maxr == maxr)) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite residual");
+        if (!finite) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite Ritz value or residual");
+        std::copy(res_h, res_h + M, res_prev.begin());
         if (maxr <= c->opt.tol) break;
     }
-    a64 += sv.applies64;
-    a32 += sv.applies32;
-    iters += sv.iterations;
+    cnt.a64 += sv.applies64;
+    cnt.a32 += sv.applies32;
+    cnt.iters += sv.iterations;
     return maxr <= c->opt.tol ? LOBPCG_OK : LOBPCG_NOT_CONVERGED;
 }
 
@@ -725,6 +772,8 @@ int validate_options(const lobpcg_options &o) {
     if (o.precision != LOBPCG_FP64 && o.precision != LOBPCG_MIXED) return fail(LOBPCG_ERR_ARG, "unknown precision");
     if (!(o.tol > 0.0)) return fail(LOBPCG_ERR_ARG, "tol must be > 0");
     if (3 * o.block_size > 4096) return fail(LOBPCG_ERR_ARG, "block_size too large (3 m must be <= 4096)");
+    if (o.nbuf < 0) return fail(LOBPCG_ERR_ARG, "nbuf must be >= 0");
+    if (!(o.mixed_switch >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_switch must be >= 0");
     return LOBPCG_OK;
 }
 
@@ -746,6 +795,8 @@ int lobpcg_default_options(lobpcg_options *opt) {
     opt->tol = 1e-8;
     opt->mem_cap = 0;
     opt->timing = 0;
+    opt->nbuf = 0;
+    opt->mixed_switch = 1e-6;
     return LOBPCG_OK;
 }
 
@@ -936,16 +987,20 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
     if (M < 1 || M % m) return fail(LOBPCG_ERR_ARG, "nbands must be a positive multiple of block_size");
     for (int k = 0; k < c->nk; ++k) {
         if (!X[k]) return fail(LOBPCG_ERR_ARG, "X[k] is NULL");
-        if (M > c->kp[k].npw) return fail(LOBPCG_ERR_ARG, "nbands exceeds the plane-wave count");
+        const int nb_extra = c->opt.nbuf > 0 ? ((c->opt.nbuf + m - 1) / m) * m : 0;
+        if (M + nb_extra > c->kp[k].npw)
+            return fail(LOBPCG_ERR_ARG, "nbands (plus buffer bands) exceeds the plane-wave count");
         if (c->nproj > 0 && !c->kp[k].has_beta) return fail(LOBPCG_ERR_ARG, "projectors missing for a k-point");
     }
     const auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launch_count();
-    int worst = LOBPCG_OK, sweeps = 0, iters = 0;
-    long long a64 = 0, a32 = 0;
+    int worst = LOBPCG_OK, sweeps = 0;
+    SolveCounters cnt;
     double maxr = 0.0;
     Prof prof;
     prof.on = c->opt.timing != 0;
+    const int nbuf = c->opt.nbuf > 0 ? ((c->opt.nbuf + m - 1) / m) * m : 0;
+    std::vector<double> ebuf;
     prof.s = c->stream;
     for (int k = 0; k < c->nk; ++k) {
         int sw = 0;
@@ -958,9 +1013,27 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
             Xd = static_cast<z64 *>(c->stageX.p);
             LG_CUDA_TRY(cudaMemcpyAsync(Xd, X[k], bytes, cudaMemcpyHostToDevice, c->stream));
         }
-        int rc = solve_k(c, k, M, Xd, eig + (size_t)k * M, resid + (size_t)k * M, sw, prof.on ? &prof : nullptr,
-                         a64, a32, iters);
-        if (rc < 0) return rc;
+        // buffer bands: an internal block of M + nbuf columns, the extra ones pseudo-random
+        int rc;
+        if (nbuf > 0) {
+            const int npw = c->kp[k].npw;
+            LG_TRY(c->alloc.ensure(c->Xext, sizeof(z64) * (size_t)npw * (M + nbuf)));
+            z64 *Xe = static_cast<z64 *>(c->Xext.p);
+            LG_CUDA_TRY(cudaMemcpyAsync(Xe, Xd, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            LG_TRY(fill_random(npw, nbuf, Xe + (size_t)npw * M, npw, 0x51ED270Bu + 977u * (unsigned)k, c->stream));
+            ebuf.resize(2 * (size_t)(M + nbuf));
+            rc = solve_k(c, k, M + nbuf, M, Xe, ebuf.data(), ebuf.data() + (M + nbuf), sw, prof.on ? &prof : nullptr,
+                         cnt);
+            if (rc < 0) return rc;
+            LG_CUDA_TRY(cudaMemcpyAsync(Xd, Xe, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            LG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            std::memcpy(eig + (size_t)k * M, ebuf.data(), sizeof(double) * M);
+            std::memcpy(resid + (size_t)k * M, ebuf.data() + (M + nbuf), sizeof(double) * M);
+        } else {
+            rc = solve_k(c, k, M, M, Xd, eig + (size_t)k * M, resid + (size_t)k * M, sw, prof.on ? &prof : nullptr,
+                         cnt);
+            if (rc < 0) return rc;
+        }
         if (host) {
             LG_CUDA_TRY(cudaMemcpyAsync(X[k], Xd, bytes, cudaMemcpyDeviceToHost, c->stream));
             LG_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -973,12 +1046,14 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
     if (st) {
         std::memset(st, 0, sizeof(*st));
         st->sweeps = sweeps;
-        st->iterations = iters;
+        st->iterations = cnt.iters;
         st->converged = worst == LOBPCG_OK;
         st->max_resid = maxr;
         st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        st->band_applies_fp64 = a64;
-        st->band_applies_fp32 = a32;
+        st->band_applies_fp64 = cnt.a64;
+        st->band_applies_fp32 = cnt.a32;
+        st->block_visits_fp32 = cnt.visits32;
+        st->block_visits_fp64 = cnt.visits64;
         st->kernel_launches = launch_count() - l0;
         for (int p = 0; p < LOBPCG_PH_COUNT; ++p) {
             st->ph_ms[p] = prof.ms[p];
@@ -1011,7 +1086,7 @@ void lobpcg_destroy(lobpcg_ctx *ctx) {
                       &ctx->HZb[1], &ctx->Z32, &ctx->HZ32, &ctx->HXall, &ctx->Tmp, &ctx->Gram, &ctx->Gram2,
                       &ctx->Cbuf, &ctx->dtheta, &ctx->dres, &ctx->dwork, &ctx->Gc, &ctx->gw.part, &ctx->ew.buf,
                       &ctx->ew.ibuf, &ctx->ew.gw.part, &ctx->X32all, &ctx->HX32all, &ctx->Q32[0], &ctx->Q32[1],
-                      &ctx->HQ32[0], &ctx->HQ32[1], &ctx->D32, &ctx->Small32};
+                      &ctx->HQ32[0], &ctx->HQ32[1], &ctx->D32, &ctx->Small32, &ctx->Xext};
     for (DevBuf *b : bufs) ctx->alloc.release(*b);
     delete ctx;
 }

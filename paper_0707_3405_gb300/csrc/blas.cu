@@ -213,14 +213,25 @@ int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *
     return launch_gemm<R, false, false>(nullptr, M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, false);
 }
 
-int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
-                const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s) {
+template <typename R>
+int gemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const cx<R> *A, int lda,
+               const cx<R> *B, int ldb, double beta, cx<R> *C, int ldc, cudaStream_t s) {
     const bool ca = (opA == 'C'), cb = (opB == 'C');
     const bool sp = w != nullptr;
-    if (!ca && !cb) return launch_gemm<double, false, false>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
-    if (ca && !cb) return launch_gemm<double, true, false>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
-    if (!ca && cb) return launch_gemm<double, false, true>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
-    return launch_gemm<double, true, true>(w, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, sp);
+    const R al = (R)alpha, be = (R)beta;
+    if (!ca && !cb) return launch_gemm<R, false, false>(w, m, n, k, al, A, lda, B, ldb, be, C, ldc, C, ldc, s, sp);
+    if (ca && !cb) return launch_gemm<R, true, false>(w, m, n, k, al, A, lda, B, ldb, be, C, ldc, C, ldc, s, sp);
+    if (!ca && cb) return launch_gemm<R, false, true>(w, m, n, k, al, A, lda, B, ldb, be, C, ldc, C, ldc, s, sp);
+    return launch_gemm<R, true, true>(w, m, n, k, al, A, lda, B, ldb, be, C, ldc, C, ldc, s, sp);
+}
+template int gemm_small<double>(GemmWork *, char, char, int, int, int, double, const z64 *, int, const z64 *, int,
+                                double, z64 *, int, cudaStream_t);
+template int gemm_small<float>(GemmWork *, char, char, int, int, int, double, const c32 *, int, const c32 *, int,
+                               double, c32 *, int, cudaStream_t);
+
+int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
+                const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s) {
+    return gemm_small<double>(w, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
 }
 
 template int gemm_cn<double>(GemmWork &, int, int, int, double, const z64 *, int, const z64 *, int, double, z64 *,

@@ -214,6 +214,10 @@ template <typename R>
 int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb, R beta,
             const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s);
 // Small general complex128 product: C = alpha op(A) op(B) + beta C, op in {'N','C'}.
+// Small general complex product in precision R; w (nullable) enables a split of the reduction dimension.
+template <typename R>
+int gemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const cx<R> *A, int lda,
+               const cx<R> *B, int ldb, double beta, cx<R> *C, int ldc, cudaStream_t s);
 // w (nullable) enables a split of the reduction dimension.
 int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
                 const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s);
@@ -228,6 +232,9 @@ struct EigWork {
 // Rayleigh-Ritz: lowest m pairs of A c = theta S c (n x n, ld n). See lobpcg_k_rayleigh_ritz.
 int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,
                   double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s);
+// The same Rayleigh-Ritz in FP32 arithmetic (complex64 pencil, float Ritz values).
+int rayleigh_ritz32(EigWork &w, int n, int m, const c32 *S, int lds, const c32 *A, int lda, double drop_tol,
+                    float *theta, c32 *C, int ldc, int *ndropped, cudaStream_t s);
 // Copy the lower triangle of A (n x n, ld n) onto the upper one (imaginary diagonal cleared).
 int hermitize_lower(EigWork &w, int n, z64 *A, cudaStream_t s);
 // Lowest m eigenpairs of a Hermitian matrix (n x n, ld lda, lower triangle; overwritten).
@@ -247,8 +254,18 @@ int assemble_gram_mixed(int nz, int mx, const c32 *S32, int lds32, const c32 *A3
                         z64 *S, z64 *A, cudaStream_t s);
 // Overwrite diag(S) = diag(X^H X), diag(A) = diag(X^H HX) in FP64 (m x m, ld m).
 int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, cudaStream_t s);
+// Deterministic pseudo-random complex entries in [-1, 1) (buffer-band start vectors).
+int fill_random(int rows, int cols, z64 *X, int ldx, unsigned seed, cudaStream_t s);
 int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
                        double *out, cudaStream_t s);
+// FP32-output pencil assembly, FP64 Rayleigh quotients, FP32 residual and preconditioner (mixed schedule).
+int assemble_gram_mixed32(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
+                          c32 *S, c32 *A, cudaStream_t s);
+int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, cudaStream_t s);
+int residual32(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta, c32 *R, int ldr,
+               cudaStream_t s);
+int precond32(int npw, int m, const z64 *X, int ldx, const double *kin, const c32 *R, int ldr, c32 *W, int ldw,
+              double *work, cudaStream_t s);
 template <typename Ro, typename Ri>
 int copy_cast(int rows, int cols, const cx<Ri> *A, int lda, cx<Ro> *B, int ldb, cudaStream_t s);
 int scale_rows_real(int rows, int cols, const double *d, z64 *A, int lda, cudaStream_t s);

@@ -74,6 +74,15 @@ int lobpcg_k_rayleigh_ritz(int n, int m, const void *S, const void *A, double dr
                          theta, static_cast<z64 *>(C), n, ndropped, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double drop_tol, float *theta, void *C,
+                             int *ndropped, void *stream) {
+    if (n < 1 || m < 1 || m > n || n > 4096) return fail(LOBPCG_ERR_ARG, "need 1 <= m <= n <= 4096");
+    if (!S || !A || !theta || !C) return fail(LOBPCG_ERR_ARG, "NULL pointer");
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    return rayleigh_ritz32(pool().ew, n, m, static_cast<const c32 *>(S), n, static_cast<const c32 *>(A), n, drop_tol,
+                           theta, static_cast<c32 *>(C), n, ndropped, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream) {
     if (n < 1 || n > 4096) return fail(LOBPCG_ERR_ARG, "need 1 <= n <= 4096");
     if (!A || !w || !V) return fail(LOBPCG_ERR_ARG, "NULL pointer");

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 
 namespace lg {
 
@@ -29,35 +30,59 @@ namespace {
 
 constexpr int NBK = 32;  // Cholesky / inverse block size
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename RT> struct Lim;
+template <> struct Lim<double> {
+    static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
+    static __device__ __forceinline__ double tiny() { return DBL_MIN; }
+    static __device__ __forceinline__ double big() { return DBL_MAX; }
+};
+template <> struct Lim<float> {
+    static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
+    static __device__ __forceinline__ float tiny() { return FLT_MIN; }
+    static __device__ __forceinline__ float big() { return FLT_MAX; }
+};
+__device__ __forceinline__ z64 ldcg_cx(const z64 *p) {
+    const double2 t = __ldcg(reinterpret_cast<const double2 *>(p));
+    return mkc(t.x, t.y);
+}
+__device__ __forceinline__ c32 ldcg_cx(const c32 *p) {
+    const float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
+    return mkc(t.x, t.y);
+}
+
+
+template <typename RT>
+__device__ __forceinline__ RT warp_sum(RT v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
 // Deterministic block sum (blockDim.x multiple of 32, <= 1024). Result on all threads.
-__device__ double block_sum(double v, double *sh) {
+template <typename RT>
+__device__ RT block_sum(RT v, RT *sh) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = v;
     __syncthreads();
-    double t = 0.0;
+    RT t = 0.0;
     for (int i = 0; i < nw; ++i) t += sh[i];
     return t;
 }
 
 // ------------------------------------------------------------------ scaling
-__global__ void k_scale_gram(int n, const z64 *__restrict__ S, int lds, const z64 *__restrict__ A, int lda,
-                             z64 *__restrict__ Ss, z64 *__restrict__ As, double *__restrict__ d) {
+template <typename RT>
+__global__ void k_scale_gram(int n, const cx<RT> *__restrict__ S, int lds, const cx<RT> *__restrict__ A, int lda,
+                             cx<RT> *__restrict__ Ss, cx<RT> *__restrict__ As, RT *__restrict__ d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= n) return;
-    const double si = S[(size_t)i * lds + i].x, sj = S[(size_t)j * lds + j].x;
-    const double di = si > 0.0 ? 1.0 / sqrt(si) : 0.0;
-    const double dj = sj > 0.0 ? 1.0 / sqrt(sj) : 0.0;
+    const RT si = S[(size_t)i * lds + i].x, sj = S[(size_t)j * lds + j].x;
+    const RT di = si > 0.0 ? 1.0 / sqrt(si) : 0.0;
+    const RT dj = sj > 0.0 ? 1.0 / sqrt(sj) : 0.0;
     if (j == 0) d[i] = di;
-    z64 s, a;
+    cx<RT> s, a;
     if (i >= j) {
         s = S[(size_t)j * lds + i];
         a = A[(size_t)j * lda + i];
@@ -73,32 +98,33 @@ __global__ void k_scale_gram(int n, const z64 *__restrict__ S, int lds, const z6
 // ------------------------------------------------------------------ Cholesky with dropping
 // Factor the kb x kb diagonal block at k0 (already updated by earlier panels),
 // write L_kk over it and its inverse into Linv.
+template <typename RT>
 __global__ void __launch_bounds__(256)
-k_chol_diag(int n, int k0, int kb, z64 *__restrict__ L, z64 *__restrict__ Linv, double drop_tol,
+k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ Linv, RT drop_tol,
             int *__restrict__ dropped, int *__restrict__ ndrop) {
-    __shared__ z64 T[NBK][NBK + 1];
-    __shared__ z64 I[NBK][NBK + 1];
+    __shared__ cx<RT> T[NBK][NBK + 1];
+    __shared__ cx<RT> I[NBK][NBK + 1];
     __shared__ int dflag[NBK];
     const int tid = threadIdx.x;
     for (int e = tid; e < NBK * NBK; e += blockDim.x) {
         const int r = e % NBK, c = e / NBK;
-        z64 v = mkc(0.0, 0.0);
+        cx<RT> v = mkc<RT>(0.0, 0.0);
         if (r < kb && c < kb && r >= c) v = L[(size_t)(k0 + c) * n + k0 + r];
         T[r][c] = v;
-        I[r][c] = mkc(0.0, 0.0);
+        I[r][c] = mkc<RT>(0.0, 0.0);
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
-        const double p = T[j][j].x;
+        const RT p = T[j][j].x;
         const bool drop = !(p > drop_tol);
         __syncthreads();
         if (drop) {
-            for (int r = j + 1 + tid; r < kb; r += blockDim.x) T[r][j] = mkc(0.0, 0.0);
-            if (tid == 0) { T[j][j] = mkc(1.0, 0.0); dflag[j] = 1; }
+            for (int r = j + 1 + tid; r < kb; r += blockDim.x) T[r][j] = mkc<RT>(0.0, 0.0);
+            if (tid == 0) { T[j][j] = mkc<RT>(1.0, 0.0); dflag[j] = 1; }
         } else {
-            const double rt = sqrt(p), inv = 1.0 / rt;
+            const RT rt = sqrt(p), inv = 1.0 / rt;
             for (int r = j + 1 + tid; r < kb; r += blockDim.x) T[r][j] = inv * T[r][j];
-            if (tid == 0) { T[j][j] = mkc(rt, 0.0); dflag[j] = 0; }
+            if (tid == 0) { T[j][j] = mkc<RT>(rt, 0.0); dflag[j] = 0; }
         }
         __syncthreads();
         if (!drop) {
@@ -113,24 +139,24 @@ k_chol_diag(int n, int k0, int kb, z64 *__restrict__ L, z64 *__restrict__ Linv, 
     // clear the rows of dropped columns inside the block
     for (int e = tid; e < kb * kb; e += blockDim.x) {
         const int r = e % kb, c = e / kb;
-        if (c < r && dflag[r]) T[r][c] = mkc(0.0, 0.0);
+        if (c < r && dflag[r]) T[r][c] = mkc<RT>(0.0, 0.0);
     }
     __syncthreads();
     // inverse of the lower-triangular block, one column per thread
     if (tid < kb) {
         const int c = tid;
-        I[c][c] = mkc(1.0 / T[c][c].x, 0.0);  // real positive diagonal
+        I[c][c] = mkc<RT>(1.0 / T[c][c].x, 0.0);  // real positive diagonal
         for (int r = c + 1; r < kb; ++r) {
-            z64 s = mkc(0.0, 0.0);
+            cx<RT> s = mkc<RT>(0.0, 0.0);
             for (int l = c; l < r; ++l) s = s + T[r][l] * I[l][c];
-            I[r][c] = (-1.0 / T[r][r].x) * s;
+            I[r][c] = (RT)(-1.0 / T[r][r].x) * s;
         }
     }
     __syncthreads();
     for (int e = tid; e < kb * kb; e += blockDim.x) {
         const int r = e % kb, c = e / kb;
-        L[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? T[r][c] : mkc(0.0, 0.0);
-        Linv[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? I[r][c] : mkc(0.0, 0.0);
+        L[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? T[r][c] : mkc<RT>(0.0, 0.0);
+        Linv[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? I[r][c] : mkc<RT>(0.0, 0.0);
     }
     if (tid < kb) {
         dropped[k0 + tid] = dflag[tid];
@@ -139,44 +165,47 @@ k_chol_diag(int n, int k0, int kb, z64 *__restrict__ L, z64 *__restrict__ Linv, 
 }
 
 // Panel: L21 = S21 Linv_kk^H for rows k0+kb..n-1 (8 rows per block, 32 columns).
+template <typename RT>
 __global__ void __launch_bounds__(256)
-k_chol_panel(int n, int k0, int kb, z64 *__restrict__ L, const z64 *__restrict__ Linv,
+k_chol_panel(int n, int k0, int kb, cx<RT> *__restrict__ L, const cx<RT> *__restrict__ Linv,
              const int *__restrict__ dropped) {
-    __shared__ z64 Di[NBK][NBK + 1];
-    __shared__ z64 Srow[8][NBK + 1];
+    __shared__ cx<RT> Di[NBK][NBK + 1];
+    __shared__ cx<RT> Srow[8][NBK + 1];
     const int tid = threadIdx.x;
     for (int e = tid; e < NBK * NBK; e += blockDim.x) {
         const int r = e % NBK, c = e / NBK;
-        Di[r][c] = (r < kb && c < kb) ? Linv[(size_t)(k0 + c) * n + k0 + r] : mkc(0.0, 0.0);
+        Di[r][c] = (r < kb && c < kb) ? Linv[(size_t)(k0 + c) * n + k0 + r] : mkc<RT>(0.0, 0.0);
     }
     const int rl = tid / NBK, c = tid % NBK;
     const int row = k0 + kb + blockIdx.x * 8 + rl;
     if (row < n && c < kb) Srow[rl][c] = L[(size_t)(k0 + c) * n + row];
     __syncthreads();
     if (row < n && c < kb) {
-        z64 s = mkc(0.0, 0.0);
+        cx<RT> s = mkc<RT>(0.0, 0.0);
         for (int l = 0; l <= c; ++l) s = s + mul_conj(Srow[rl][l], Di[c][l]);
-        if (dropped[k0 + c]) s = mkc(0.0, 0.0);
+        if (dropped[k0 + c]) s = mkc<RT>(0.0, 0.0);
         L[(size_t)(k0 + c) * n + row] = s;
     }
 }
 
-__global__ void k_zero_dropped_rows(int n, z64 *__restrict__ L, const int *__restrict__ dropped) {
+template <typename RT>
+__global__ void k_zero_dropped_rows(int n, cx<RT> *__restrict__ L, const int *__restrict__ dropped) {
     const int j = blockIdx.x;
     if (!dropped[j]) return;
-    for (int c = threadIdx.x; c < j; c += blockDim.x) L[(size_t)c * n + j] = mkc(0.0, 0.0);
+    for (int c = threadIdx.x; c < j; c += blockDim.x) L[(size_t)c * n + j] = mkc<RT>(0.0, 0.0);
 }
 
 // ------------------------------------------------------------------ hermitize / dropped rows
-__global__ void k_hermitize_rowsum(int n, z64 *__restrict__ A, const int *__restrict__ dropped,
-                                   double *__restrict__ rowsum) {
+template <typename RT>
+__global__ void k_hermitize_rowsum(int n, cx<RT> *__restrict__ A, const int *__restrict__ dropped,
+                                   RT *__restrict__ rowsum) {
     const int i = blockIdx.x;
-    __shared__ double sh[32];
-    double s = 0.0;
+    __shared__ RT sh[32];
+    RT s = 0.0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        z64 v = (i >= j) ? A[(size_t)j * n + i] : conjc(A[(size_t)i * n + j]);
+        cx<RT> v = (i >= j) ? A[(size_t)j * n + i] : conjc(A[(size_t)i * n + j]);
         if (i == j) v.y = 0.0;
-        if (dropped && (dropped[i] || dropped[j])) v = mkc(0.0, 0.0);
+        if (dropped && (dropped[i] || dropped[j])) v = mkc<RT>(0.0, 0.0);
         s += sqrt(abs2(v));
         if (i >= j) {
             A[(size_t)j * n + i] = v;
@@ -187,71 +216,75 @@ __global__ void k_hermitize_rowsum(int n, z64 *__restrict__ A, const int *__rest
     if (threadIdx.x == 0) rowsum[i] = s;
 }
 
-__global__ void k_set_dropped_diag(int n, z64 *__restrict__ A, const int *__restrict__ dropped,
-                                   const int *__restrict__ ndrop, const double *__restrict__ rowsum) {
+template <typename RT>
+__global__ void k_set_dropped_diag(int n, cx<RT> *__restrict__ A, const int *__restrict__ dropped,
+                                   const int *__restrict__ ndrop, const RT *__restrict__ rowsum) {
     if (*ndrop == 0) return;
-    __shared__ double sh[32];
-    double mx = 0.0;
+    __shared__ RT sh[32];
+    RT mx = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, rowsum[i]);
     // deterministic max via shuffles
 #pragma unroll
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
     __syncthreads();
-    double m2 = 0.0;
+    RT m2 = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, sh[w]);
-    const double sigma = 2.0 * m2 + 1.0;
+    const RT sigma = 2.0 * m2 + 1.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-        if (dropped[i]) A[(size_t)i * n + i] = mkc(sigma, 0.0);
+        if (dropped[i]) A[(size_t)i * n + i] = mkc<RT>(sigma, 0.0);
 }
 
 // ------------------------------------------------------------------ tridiagonalisation
 // Reflector of x = A[i+1:n, i] in the LAPACK larfg convention:
 //   H = I - tau v v^H, v[0] = 1, H^H x = beta e_1 with beta real.
+template <typename RT>
 struct Refl {
-    z64 tau;
-    double beta;
-    z64 scal;  // v[r] = x[r] * scal for r >= 1
+    cx<RT> tau;
+    RT beta;
+    cx<RT> scal;  // v[r] = x[r] * scal for r >= 1
 };
 
-__device__ Refl make_reflector(const z64 *__restrict__ col, int L, double *sh) {
-    double s = 0.0;
+template <typename RT>
+__device__ Refl<RT> make_reflector(const cx<RT> *__restrict__ col, int L, RT *sh) {
+    RT s = 0.0;
     for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(col[r]);
     s = block_sum(s, sh);
-    const z64 alpha = col[0];
-    Refl R;
+    const cx<RT> alpha = col[0];
+    Refl<RT> R;
     if (s == 0.0 && alpha.y == 0.0) {
-        R.tau = mkc(0.0, 0.0);
+        R.tau = mkc<RT>(0.0, 0.0);
         R.beta = alpha.x;
-        R.scal = mkc(0.0, 0.0);
+        R.scal = mkc<RT>(0.0, 0.0);
         return R;
     }
-    const double beta = -copysign(sqrt(abs2(alpha) + s), alpha.x);
+    const RT beta = -copysign(sqrt(abs2(alpha) + s), alpha.x);
     R.beta = beta;
-    R.tau = mkc((beta - alpha.x) / beta, -alpha.y / beta);
-    const z64 den = mkc(alpha.x - beta, alpha.y);
-    const double dd = abs2(den);
-    R.scal = mkc(den.x / dd, -den.y / dd);
+    R.tau = mkc<RT>((beta - alpha.x) / beta, -alpha.y / beta);
+    const cx<RT> den = mkc<RT>(alpha.x - beta, alpha.y);
+    const RT dd = abs2(den);
+    R.scal = mkc<RT>(den.x / dd, -den.y / dd);
     return R;
 }
 
 // Step i, part 1: reflector (every block, redundantly) and y = A22 v by 32x32 tiles;
 // the last block to finish forms w = tau y - |tau|^2/2 (v^H y) v.
+template <typename RT>
 __global__ void __launch_bounds__(256)
-k_tri_step1(int n, int i, z64 *__restrict__ A, int lda, z64 *__restrict__ Hv, z64 *__restrict__ taus,
-            double *__restrict__ dg, double *__restrict__ eg, z64 *__restrict__ ypart, z64 *__restrict__ wv,
+k_tri_step1(int n, int i, cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<RT> *__restrict__ taus,
+            RT *__restrict__ dg, RT *__restrict__ eg, cx<RT> *__restrict__ ypart, cx<RT> *__restrict__ wv,
             unsigned int *__restrict__ counter) {
-    __shared__ double sh[32];
-    __shared__ z64 vs[32];
-    __shared__ z64 acc[8][33];
+    __shared__ RT sh[32];
+    __shared__ cx<RT> vs[32];
+    __shared__ cx<RT> acc[8][33];
     __shared__ bool last;
     const int L = n - i - 1;
-    const z64 *col = A + (size_t)i * lda + i + 1;
-    const Refl R = make_reflector(col, L, sh);
+    const cx<RT> *col = A + (size_t)i * lda + i + 1;
+    const Refl<RT> R = make_reflector<RT>(col, L, sh);
     const int tr = blockIdx.x, tc = blockIdx.y;
     const int tid = threadIdx.x;
     if (tr == 0 && tc == 0) {
-        for (int r = tid; r < L; r += blockDim.x) Hv[(size_t)i * n + i + 1 + r] = (r == 0) ? mkc(1.0, 0.0) : col[r] * R.scal;
+        for (int r = tid; r < L; r += blockDim.x) Hv[(size_t)i * n + i + 1 + r] = (r == 0) ? mkc<RT>(1.0, 0.0) : col[r] * R.scal;
         if (tid == 0) {
             taus[i] = R.tau;
             dg[i] = A[(size_t)i * lda + i].x;
@@ -261,14 +294,14 @@ k_tri_step1(int n, int i, z64 *__restrict__ A, int lda, z64 *__restrict__ Hv, z6
     // v entries of this column tile
     if (tid < 32) {
         const int c = tc * 32 + tid;
-        vs[tid] = (c < L) ? ((c == 0) ? mkc(1.0, 0.0) : col[c] * R.scal) : mkc(0.0, 0.0);
+        vs[tid] = (c < L) ? ((c == 0) ? mkc<RT>(1.0, 0.0) : col[c] * R.scal) : mkc<RT>(0.0, 0.0);
     }
     __syncthreads();
     const int rl = tid & 31, cg = tid >> 5;  // 32 rows x 8 column groups of 4
     const int r = tr * 32 + rl;
-    z64 s = mkc(0.0, 0.0);
+    cx<RT> s = mkc<RT>(0.0, 0.0);
     if (r < L) {
-        const z64 *A22 = A + (size_t)(i + 1) * lda + i + 1;
+        const cx<RT> *A22 = A + (size_t)(i + 1) * lda + i + 1;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int cl = cg * 4 + q, c = tc * 32 + cl;
@@ -278,7 +311,7 @@ k_tri_step1(int n, int i, z64 *__restrict__ A, int lda, z64 *__restrict__ Hv, z6
     acc[cg][rl] = s;
     __syncthreads();
     if (tid < 32) {
-        z64 t = acc[0][tid];
+        cx<RT> t = acc[0][tid];
         for (int g = 1; g < 8; ++g) t = t + acc[g][tid];
         const int rr = tr * 32 + tid;
         if (rr < L) ypart[(size_t)tc * n + rr] = t;
@@ -296,14 +329,13 @@ k_tri_step1(int n, int i, z64 *__restrict__ A, int lda, z64 *__restrict__ Hv, z6
     __threadfence();
     const int ncb = gridDim.y;
     // y = sum of partials (fixed order), dot = v^H y
-    double dre = 0.0, dim = 0.0;
+    RT dre = 0.0, dim = 0.0;
     for (int rr = tid; rr < L; rr += blockDim.x) {
-        z64 y = mkc(0.0, 0.0);
+        cx<RT> y = mkc<RT>(0.0, 0.0);
         for (int c = 0; c < ncb; ++c) {
-            const double2 t = __ldcg(reinterpret_cast<const double2 *>(ypart + (size_t)c * n + rr));
-            y = y + mkc(t.x, t.y);
+            y = y + ldcg_cx(ypart + (size_t)c * n + rr);
         }
-        const z64 v = (rr == 0) ? mkc(1.0, 0.0) : col[rr] * R.scal;
+        const cx<RT> v = (rr == 0) ? mkc<RT>(1.0, 0.0) : col[rr] * R.scal;
         // conj(v) * y
         dre += v.x * y.x + v.y * y.y;
         dim += v.x * y.y - v.y * y.x;
@@ -311,55 +343,58 @@ k_tri_step1(int n, int i, z64 *__restrict__ A, int lda, z64 *__restrict__ Hv, z6
     }
     dre = block_sum(dre, sh);
     (void)dim;  // v^H A v is real for Hermitian A
-    const double t2 = 0.5 * abs2(R.tau) * dre;
+    const RT t2 = 0.5 * abs2(R.tau) * dre;
     __syncthreads();
     for (int rr = tid; rr < L; rr += blockDim.x) {
-        const z64 v = (rr == 0) ? mkc(1.0, 0.0) : col[rr] * R.scal;
-        const z64 y = wv[rr];
+        const cx<RT> v = (rr == 0) ? mkc<RT>(1.0, 0.0) : col[rr] * R.scal;
+        const cx<RT> y = wv[rr];
         wv[rr] = R.tau * y - t2 * v;
     }
 }
 
 // Step i, part 2: A22 -= w v^H + v w^H on 32x32 tiles.
+template <typename RT>
 __global__ void __launch_bounds__(256)
-k_tri_step2(int n, int i, z64 *__restrict__ A, int lda, const z64 *__restrict__ Hv, const z64 *__restrict__ wv) {
-    __shared__ z64 vr[32], wr[32], vc[32], wc[32];
+k_tri_step2(int n, int i, cx<RT> *__restrict__ A, int lda, const cx<RT> *__restrict__ Hv, const cx<RT> *__restrict__ wv) {
+    __shared__ cx<RT> vr[32], wr[32], vc[32], wc[32];
     const int L = n - i - 1;
     const int tr = blockIdx.x, tc = blockIdx.y, tid = threadIdx.x;
-    const z64 *v = Hv + (size_t)i * n + i + 1;
+    const cx<RT> *v = Hv + (size_t)i * n + i + 1;
     if (tid < 32) {
         const int r = tr * 32 + tid, c = tc * 32 + tid;
-        vr[tid] = r < L ? v[r] : mkc(0.0, 0.0);
-        wr[tid] = r < L ? wv[r] : mkc(0.0, 0.0);
-        vc[tid] = c < L ? v[c] : mkc(0.0, 0.0);
-        wc[tid] = c < L ? wv[c] : mkc(0.0, 0.0);
+        vr[tid] = r < L ? v[r] : mkc<RT>(0.0, 0.0);
+        wr[tid] = r < L ? wv[r] : mkc<RT>(0.0, 0.0);
+        vc[tid] = c < L ? v[c] : mkc<RT>(0.0, 0.0);
+        wc[tid] = c < L ? wv[c] : mkc<RT>(0.0, 0.0);
     }
     __syncthreads();
-    z64 *A22 = A + (size_t)(i + 1) * lda + i + 1;
+    cx<RT> *A22 = A + (size_t)(i + 1) * lda + i + 1;
     for (int e = tid; e < 32 * 32; e += blockDim.x) {
         const int rl = e & 31, cl = e >> 5;
         const int r = tr * 32 + rl, c = tc * 32 + cl;
         if (r < L && c < L) {
-            z64 a = A22[(size_t)c * lda + r];
+            cx<RT> a = A22[(size_t)c * lda + r];
             a = a - mul_conj(wr[rl], vc[cl]) - mul_conj(vr[rl], wc[cl]);
             A22[(size_t)c * lda + r] = a;
         }
     }
 }
 
-__global__ void k_tri_last(int n, const z64 *__restrict__ A, int lda, double *__restrict__ dg) {
+template <typename RT>
+__global__ void k_tri_last(int n, const cx<RT> *__restrict__ A, int lda, RT *__restrict__ dg) {
     if (threadIdx.x == 0) dg[n - 1] = A[(size_t)(n - 1) * lda + n - 1].x;
 }
 
 // ------------------------------------------------------------------ eigenvalues (multisection)
-__device__ __forceinline__ int sturm_count(const double *__restrict__ d, const double *__restrict__ e, int n,
-                                           double x, double pivmin) {
+template <typename RT>
+__device__ __forceinline__ int sturm_count(const RT *__restrict__ d, const RT *__restrict__ e, int n,
+                                           RT x, RT pivmin) {
     int c = 0;
-    double q = d[0] - x;
+    RT q = d[0] - x;
     if (fabs(q) < pivmin) q = -pivmin;
     c += (q < 0.0);
     for (int i = 1; i < n; ++i) {
-        const double ei = e[i - 1];
+        const RT ei = e[i - 1];
         q = d[i] - x - (ei * ei) / q;
         if (fabs(q) < pivmin) q = -pivmin;
         c += (q < 0.0);
@@ -367,21 +402,22 @@ __device__ __forceinline__ int sturm_count(const double *__restrict__ d, const d
     return c;
 }
 
-__device__ void tri_bounds(const double *__restrict__ d, const double *__restrict__ e, int n, double &lo,
-                           double &hi, double &tnorm, double &pivmin) {
-    lo = DBL_MAX;
-    hi = -DBL_MAX;
-    double emax2 = 0.0;
+template <typename RT>
+__device__ void tri_bounds(const RT *__restrict__ d, const RT *__restrict__ e, int n, RT &lo,
+                           RT &hi, RT &tnorm, RT &pivmin) {
+    lo = Lim<RT>::big();
+    hi = -Lim<RT>::big();
+    RT emax2 = 0.0;
     for (int i = 0; i < n; ++i) {
-        double r = 0.0;
+        RT r = 0.0;
         if (i > 0) r += fabs(e[i - 1]);
         if (i < n - 1) { r += fabs(e[i]); emax2 = fmax(emax2, e[i] * e[i]); }
         lo = fmin(lo, d[i] - r);
         hi = fmax(hi, d[i] + r);
     }
     tnorm = fmax(fabs(lo), fabs(hi));
-    pivmin = DBL_MIN * fmax(1.0, emax2);
-    const double pad = 2.0 * DBL_EPSILON * tnorm * n + 2.0 * pivmin;
+    pivmin = Lim<RT>::tiny() * fmax(1.0, emax2);
+    const RT pad = 2.0 * Lim<RT>::eps() * tnorm * n + 2.0 * pivmin;
     lo -= pad;
     hi += pad;
 }
@@ -391,26 +427,27 @@ __device__ void tri_bounds(const double *__restrict__ d, const double *__restric
 // that holds eigenvalue k.  FP64 divisions are scarce on this GPU, so few lanes per
 // eigenvalue (less total work) beat wide multisection (fewer rounds).
 constexpr int kMsG = 4;
-__global__ void k_multisect(int n, int m, const double *__restrict__ d, const double *__restrict__ e,
-                            double *__restrict__ theta) {
+template <typename RT>
+__global__ void k_multisect(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e,
+                            RT *__restrict__ theta) {
     const int gid = (int)((blockIdx.x * blockDim.x + threadIdx.x) / kMsG);
     const int sub = threadIdx.x & (kMsG - 1);
     const int lane = threadIdx.x & 31;
     const int base = lane & ~(kMsG - 1);
     const bool active = gid < m;
     const int k = active ? gid : m - 1;
-    double lo, hi, tnorm, pivmin;
+    RT lo, hi, tnorm, pivmin;
     tri_bounds(d, e, n, lo, hi, tnorm, pivmin);
     for (int it = 0; it < 48; ++it) {
-        const double w = hi - lo;
-        const bool done = w <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin;
+        const RT w = hi - lo;
+        const bool done = w <= 2.0 * Lim<RT>::eps() * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin;
         if (__all_sync(0xffffffffu, done)) break;
-        const double x = lo + w * (double)(sub + 1) / (double)(kMsG + 1);
+        const RT x = lo + w * (RT)(sub + 1) / (RT)(kMsG + 1);
         const int c = done ? 0 : sturm_count(d, e, n, x, pivmin);
         const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
         const int T = __popc((mask >> base) & ((1u << kMsG) - 1u)) - 1;  // counts are monotone in sub
-        const double xlo = __shfl_sync(0xffffffffu, x, base + (T < 0 ? 0 : T));
-        const double xhi = __shfl_sync(0xffffffffu, x, base + (T < kMsG - 1 ? T + 1 : kMsG - 1));
+        const RT xlo = __shfl_sync(0xffffffffu, x, base + (T < 0 ? 0 : T));
+        const RT xhi = __shfl_sync(0xffffffffu, x, base + (T < kMsG - 1 ? T + 1 : kMsG - 1));
         if (!done) {
             if (T >= 0) lo = xlo;
             if (T < kMsG - 1) hi = xhi;
@@ -420,10 +457,11 @@ __global__ void k_multisect(int n, int m, const double *__restrict__ d, const do
 }
 
 // ------------------------------------------------------------------ eigenvectors (inverse iteration)
-__device__ __forceinline__ double hash_uniform(unsigned int a, unsigned int b) {
+template <typename RT>
+__device__ __forceinline__ RT hash_uniform(unsigned int a, unsigned int b) {
     unsigned int h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
     h ^= h >> 16; h *= 0x7FEB352Du; h ^= h >> 15; h *= 0x846CA68Bu; h ^= h >> 16;
-    return (double)h * (2.0 / 4294967296.0) - 1.0;
+    return (RT)h * (2.0 / 4294967296.0) - 1.0;
 }
 
 // One thread per eigenvalue index; the thread whose eigenvalue starts a cluster
@@ -431,24 +469,27 @@ __device__ __forceinline__ double hash_uniform(unsigned int a, unsigned int b) {
 // (LU of T - lambda I with partial pivoting, three solves from a pseudo-random
 // start, each followed by modified Gram-Schmidt against the cluster's earlier
 // vectors and a normalisation).
-__global__ void k_inviter(int n, int m, const double *__restrict__ d, const double *__restrict__ e,
-                          const double *__restrict__ theta, double *Z, double *scratch, signed char *pivs) {
+template <typename RT>
+__global__ void k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e,
+                          const RT *__restrict__ theta, RT *Z, RT *scratch, signed char *pivs) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
-    double lo, hi, tnorm, pivmin;
+    RT lo, hi, tnorm, pivmin;
     tri_bounds(d, e, n, lo, hi, tnorm, pivmin);
-    const double gaptol = 1e-5 * fmax(tnorm, DBL_MIN);
-    const double pert = 10.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    // vectors of eigenvalues closer than gaptol are orthogonalised against each other;
+    // elsewhere orthogonality is ~ eps |T| / gap (LAPACK uses 1e-3 |T| for single precision)
+    const RT gaptol = (sizeof(RT) == 4 ? (RT)1e-3 : (RT)1e-5) * fmax(tnorm, Lim<RT>::tiny());
+    const RT pert = 10.0 * Lim<RT>::eps() * fmax(tnorm, Lim<RT>::tiny());
     if (k > 0 && theta[k] - theta[k - 1] <= gaptol) return;  // not a cluster start
-    double lam_prev = -DBL_MAX;
+    RT lam_prev = -Lim<RT>::big();
     for (int j = k; j < m; ++j) {
         if (j > k && theta[j] - theta[j - 1] > gaptol) break;
-        double lam = theta[j];
+        RT lam = theta[j];
         if (j > k && lam < lam_prev + pert) lam = lam_prev + pert;
         lam_prev = lam;
-        double *dd = scratch + (size_t)j * 5 * n;
-        double *du = dd + n, *du2 = du + n, *dl = du2 + n;
-        double *z = Z + (size_t)j * n;
+        RT *dd = scratch + (size_t)j * 5 * n;
+        RT *du = dd + n, *du2 = du + n, *dl = du2 + n;
+        RT *z = Z + (size_t)j * n;
         signed char *pv = pivs + (size_t)j * n;
         for (int i = 0; i < n; ++i) dd[i] = d[i] - lam;
         for (int i = 0; i + 1 < n; ++i) { du[i] = e[i]; dl[i] = e[i]; du2[i] = 0.0; }
@@ -456,28 +497,28 @@ __global__ void k_inviter(int n, int m, const double *__restrict__ d, const doub
             if (fabs(dd[i]) >= fabs(dl[i])) {
                 pv[i] = 0;
                 if (dd[i] == 0.0) dd[i] = pert;
-                const double f = dl[i] / dd[i];
+                const RT f = dl[i] / dd[i];
                 dl[i] = f;
                 dd[i + 1] -= f * du[i];
             } else {
                 pv[i] = 1;
-                const double f = dd[i] / dl[i];
+                const RT f = dd[i] / dl[i];
                 dd[i] = dl[i];
                 dl[i] = f;
-                const double t = du[i];
+                const RT t = du[i];
                 du[i] = dd[i + 1];
                 dd[i + 1] = t - f * dd[i + 1];
                 if (i + 2 < n) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
             }
         }
         if (dd[n - 1] == 0.0) dd[n - 1] = pert;
-        for (int i = 0; i < n; ++i) z[i] = hash_uniform((unsigned)j, (unsigned)i);
+        for (int i = 0; i < n; ++i) z[i] = hash_uniform<RT>((unsigned)j, (unsigned)i);
         for (int it = 0; it < 3; ++it) {
             for (int i = 0; i + 1 < n; ++i) {
                 if (pv[i] == 0) {
                     z[i + 1] -= dl[i] * z[i];
                 } else {
-                    const double t = z[i];
+                    const RT t = z[i];
                     z[i] = z[i + 1];
                     z[i + 1] = t - dl[i] * z[i];
                 }
@@ -486,14 +527,14 @@ __global__ void k_inviter(int n, int m, const double *__restrict__ d, const doub
             if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / dd[n - 2];
             for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
             for (int p = k; p < j; ++p) {
-                const double *zp = Z + (size_t)p * n;
-                double s = 0.0;
+                const RT *zp = Z + (size_t)p * n;
+                RT s = 0.0;
                 for (int i = 0; i < n; ++i) s += z[i] * zp[i];
                 for (int i = 0; i < n; ++i) z[i] -= s * zp[i];
             }
-            double nr = 0.0;
+            RT nr = 0.0;
             for (int i = 0; i < n; ++i) nr += z[i] * z[i];
-            const double inv = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+            const RT inv = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
             for (int i = 0; i < n; ++i) z[i] *= inv;
         }
     }
@@ -501,37 +542,39 @@ __global__ void k_inviter(int n, int m, const double *__restrict__ d, const doub
 
 // ------------------------------------------------------------------ back-transformation
 // V[:, j] = H_0 H_1 ... H_{n-2} z_j (complex), one block per eigenvector.
+template <typename RT>
 __global__ void __launch_bounds__(256)
-k_backtransform(int n, int m, const z64 *__restrict__ Hv, const z64 *__restrict__ taus, const double *__restrict__ Z,
-                z64 *__restrict__ V, int ldv) {
+k_backtransform(int n, int m, const cx<RT> *__restrict__ Hv, const cx<RT> *__restrict__ taus, const RT *__restrict__ Z,
+                cx<RT> *__restrict__ V, int ldv) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    z64 *z = reinterpret_cast<z64 *>(smraw);
-    __shared__ double sh[32], sh2[32];
+    cx<RT> *z = reinterpret_cast<cx<RT> *>(smraw);
+    __shared__ RT sh[32], sh2[32];
     const int j = blockIdx.x;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) z[r] = mkc(Z[(size_t)j * n + r], 0.0);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) z[r] = mkc<RT>(Z[(size_t)j * n + r], 0.0);
     __syncthreads();
     for (int i = n - 2; i >= 0; --i) {
-        const z64 tau = taus[i];
+        const cx<RT> tau = taus[i];
         if (tau.x == 0.0 && tau.y == 0.0) continue;
         const int L = n - i - 1;
-        const z64 *v = Hv + (size_t)i * n + i + 1;
-        double sre = 0.0, sim = 0.0;
+        const cx<RT> *v = Hv + (size_t)i * n + i + 1;
+        RT sre = 0.0, sim = 0.0;
         for (int r = threadIdx.x; r < L; r += blockDim.x) {
-            const z64 a = v[r], b = z[i + 1 + r];
+            const cx<RT> a = v[r], b = z[i + 1 + r];
             sre += a.x * b.x + a.y * b.y;
             sim += a.x * b.y - a.y * b.x;
         }
         sre = block_sum(sre, sh);
         sim = block_sum(sim, sh2);
-        const z64 ts = tau * mkc(sre, sim);
+        const cx<RT> ts = tau * mkc<RT>(sre, sim);
         for (int r = threadIdx.x; r < L; r += blockDim.x) z[i + 1 + r] = z[i + 1 + r] - ts * v[r];
         __syncthreads();
     }
     for (int r = threadIdx.x; r < n; r += blockDim.x) V[(size_t)j * ldv + r] = z[r];
 }
 
-__global__ void k_scale_rows_copy(int n, int m, const double *__restrict__ d, const z64 *__restrict__ T, int ldt,
-                                  z64 *__restrict__ C, int ldc) {
+template <typename RT>
+__global__ void k_scale_rows_copy(int n, int m, const RT *__restrict__ d, const cx<RT> *__restrict__ T, int ldt,
+                                  cx<RT> *__restrict__ C, int ldc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i < n) C[(size_t)j * ldc + i] = d[i] * T[(size_t)j * ldt + i];
 }
@@ -542,139 +585,155 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V, int ldv, cudaStream_t s) {
+template <typename RT>
+int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT> *V, int ldv, cudaStream_t s) {
     if (n <= 0 || m <= 0) return LOBPCG_OK;
     if (m > n) return fail(LOBPCG_ERR_ARG, "heev: m > n");
     const int nt = (n + 31) / 32;
     // workspace carve-up
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-    const size_t o_hv = take(sizeof(z64) * (size_t)n * n);
-    const size_t o_tau = take(sizeof(z64) * n);
-    const size_t o_d = take(sizeof(double) * n);
-    const size_t o_e = take(sizeof(double) * n);
-    const size_t o_yp = take(sizeof(z64) * (size_t)nt * n);
-    const size_t o_wv = take(sizeof(z64) * n);
-    const size_t o_z = take(sizeof(double) * (size_t)n * m);
-    const size_t o_sc = take(sizeof(double) * 5 * (size_t)n * m);
+    const size_t o_hv = take(sizeof(cx<RT>) * (size_t)n * n);
+    const size_t o_tau = take(sizeof(cx<RT>) * n);
+    const size_t o_d = take(sizeof(RT) * n);
+    const size_t o_e = take(sizeof(RT) * n);
+    const size_t o_yp = take(sizeof(cx<RT>) * (size_t)nt * n);
+    const size_t o_wv = take(sizeof(cx<RT>) * n);
+    const size_t o_z = take(sizeof(RT) * (size_t)n * m);
+    const size_t o_sc = take(sizeof(RT) * 5 * (size_t)n * m);
     const size_t o_pv = take((size_t)n * m);
     const size_t o_cnt = take(sizeof(unsigned int) * n);
     LG_TRY(w.alloc->ensure(w.buf, off));
     char *base = reinterpret_cast<char *>(w.buf.p);
-    z64 *Hv = reinterpret_cast<z64 *>(base + o_hv);
-    z64 *taus = reinterpret_cast<z64 *>(base + o_tau);
-    double *dg = reinterpret_cast<double *>(base + o_d);
-    double *eg = reinterpret_cast<double *>(base + o_e);
-    z64 *yp = reinterpret_cast<z64 *>(base + o_yp);
-    z64 *wv = reinterpret_cast<z64 *>(base + o_wv);
-    double *Z = reinterpret_cast<double *>(base + o_z);
-    double *sc = reinterpret_cast<double *>(base + o_sc);
+    cx<RT> *Hv = reinterpret_cast<cx<RT> *>(base + o_hv);
+    cx<RT> *taus = reinterpret_cast<cx<RT> *>(base + o_tau);
+    RT *dg = reinterpret_cast<RT *>(base + o_d);
+    RT *eg = reinterpret_cast<RT *>(base + o_e);
+    cx<RT> *yp = reinterpret_cast<cx<RT> *>(base + o_yp);
+    cx<RT> *wv = reinterpret_cast<cx<RT> *>(base + o_wv);
+    RT *Z = reinterpret_cast<RT *>(base + o_z);
+    RT *sc = reinterpret_cast<RT *>(base + o_sc);
     signed char *pv = reinterpret_cast<signed char *>(base + o_pv);
     unsigned int *cnt = reinterpret_cast<unsigned int *>(base + o_cnt);
     LG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n, s));
-    LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(z64) * n, s));
+    LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(cx<RT>) * n, s));
     for (int i = 0; i + 1 < n; ++i) {
         const int L = n - i - 1;
         const int tl = (L + 31) / 32;
-        k_tri_step1<<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, taus, dg, eg, yp, wv, cnt);
+        k_tri_step1<RT><<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, taus, dg, eg, yp, wv, cnt);
         LG_TRY(check_launch("tridiag step 1"));
-        k_tri_step2<<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, wv);
+        k_tri_step2<RT><<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, wv);
         LG_TRY(check_launch("tridiag step 2"));
     }
-    k_tri_last<<<1, 32, 0, s>>>(n, A, lda, dg);
+    k_tri_last<RT><<<1, 32, 0, s>>>(n, A, lda, dg);
     LG_TRY(check_launch("tridiag last"));
-    k_multisect<<<(m * kMsG + 255) / 256, 256, 0, s>>>(n, m, dg, eg, theta);
+    k_multisect<RT><<<(m * kMsG + 255) / 256, 256, 0, s>>>(n, m, dg, eg, theta);
     LG_TRY(check_launch("multisection"));
-    k_inviter<<<(m + 63) / 64, 64, 0, s>>>(n, m, dg, eg, theta, Z, sc, pv);
+    k_inviter<RT><<<(m + 63) / 64, 64, 0, s>>>(n, m, dg, eg, theta, Z, sc, pv);
     LG_TRY(check_launch("inverse iteration"));
-    const size_t smem = sizeof(z64) * (size_t)n;
+    const size_t smem = sizeof(cx<RT>) * (size_t)n;
     if (smem > 48 * 1024) {
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_backtransform<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    k_backtransform<<<m, 256, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
+    k_backtransform<RT><<<m, 256, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
     return check_launch("back-transform");
 }
 
-int hermitize_lower(EigWork &w, int n, z64 *A, cudaStream_t s) {
-    LG_TRY(w.alloc->ensure(w.ibuf, sizeof(double) * (size_t)n + 256));
-    k_hermitize_rowsum<<<n, 128, 0, s>>>(n, A, nullptr, reinterpret_cast<double *>(w.ibuf.p));
+template <typename RT>
+int hermitize_lower_t(EigWork &w, int n, cx<RT> *A, cudaStream_t s) {
+    LG_TRY(w.alloc->ensure(w.ibuf, sizeof(RT) * (size_t)n + 256));
+    k_hermitize_rowsum<RT><<<n, 128, 0, s>>>(n, A, nullptr, reinterpret_cast<RT *>(w.ibuf.p));
     return check_launch("hermitize");
 }
 
-int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,
-                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s) {
+template <typename RT>
+int rayleigh_ritz_t(EigWork &w, int n, int m, const cx<RT> *S, int lds, const cx<RT> *A, int lda, double drop_tol,
+                    RT *theta, cx<RT> *C, int ldc, int *ndropped, cudaStream_t s) {
     if (n <= 0 || m <= 0) return LOBPCG_OK;
     if (m > n) return fail(LOBPCG_ERR_ARG, "rayleigh_ritz: m > n");
     if (n > 4096) return fail(LOBPCG_ERR_ARG, "rayleigh_ritz: n > 4096");
     // own workspace (separate from heev's)
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-    const size_t o_ss = take(sizeof(z64) * (size_t)n * n);
-    const size_t o_as = take(sizeof(z64) * (size_t)n * n);
-    const size_t o_li = take(sizeof(z64) * (size_t)n * n);
-    const size_t o_tm = take(sizeof(z64) * (size_t)n * n);
-    const size_t o_q = take(sizeof(z64) * (size_t)n * m);
-    const size_t o_d = take(sizeof(double) * n);
-    const size_t o_rs = take(sizeof(double) * n);
+    const size_t o_ss = take(sizeof(cx<RT>) * (size_t)n * n);
+    const size_t o_as = take(sizeof(cx<RT>) * (size_t)n * n);
+    const size_t o_li = take(sizeof(cx<RT>) * (size_t)n * n);
+    const size_t o_tm = take(sizeof(cx<RT>) * (size_t)n * n);
+    const size_t o_q = take(sizeof(cx<RT>) * (size_t)n * m);
+    const size_t o_d = take(sizeof(RT) * n);
+    const size_t o_rs = take(sizeof(RT) * n);
     const size_t o_dr = take(sizeof(int) * n);
     const size_t o_nd = take(sizeof(int));
     LG_TRY(w.alloc->ensure(w.ibuf, off));
     char *base = reinterpret_cast<char *>(w.ibuf.p);
-    z64 *Ss = reinterpret_cast<z64 *>(base + o_ss);
-    z64 *As = reinterpret_cast<z64 *>(base + o_as);
-    z64 *Li = reinterpret_cast<z64 *>(base + o_li);
-    z64 *Tm = reinterpret_cast<z64 *>(base + o_tm);
-    z64 *Q = reinterpret_cast<z64 *>(base + o_q);
-    double *d = reinterpret_cast<double *>(base + o_d);
-    double *rs = reinterpret_cast<double *>(base + o_rs);
+    cx<RT> *Ss = reinterpret_cast<cx<RT> *>(base + o_ss);
+    cx<RT> *As = reinterpret_cast<cx<RT> *>(base + o_as);
+    cx<RT> *Li = reinterpret_cast<cx<RT> *>(base + o_li);
+    cx<RT> *Tm = reinterpret_cast<cx<RT> *>(base + o_tm);
+    cx<RT> *Q = reinterpret_cast<cx<RT> *>(base + o_q);
+    RT *d = reinterpret_cast<RT *>(base + o_d);
+    RT *rs = reinterpret_cast<RT *>(base + o_rs);
     int *dr = reinterpret_cast<int *>(base + o_dr);
     int *nd = reinterpret_cast<int *>(base + o_nd);
 
     LG_CUDA_TRY(cudaMemsetAsync(nd, 0, sizeof(int), s));
-    LG_CUDA_TRY(cudaMemsetAsync(Li, 0, sizeof(z64) * (size_t)n * n, s));
-    k_scale_gram<<<dim3((n + 127) / 128, n), 128, 0, s>>>(n, S, lds, A, lda, Ss, As, d);
+    LG_CUDA_TRY(cudaMemsetAsync(Li, 0, sizeof(cx<RT>) * (size_t)n * n, s));
+    k_scale_gram<RT><<<dim3((n + 127) / 128, n), 128, 0, s>>>(n, S, lds, A, lda, Ss, As, d);
     LG_TRY(check_launch("scale gram"));
     // blocked Cholesky with dropping (L overwrites Ss)
     for (int k0 = 0; k0 < n; k0 += NBK) {
         const int kb = std::min(NBK, n - k0);
-        k_chol_diag<<<1, 256, 0, s>>>(n, k0, kb, Ss, Li, drop_tol, dr, nd);
+        k_chol_diag<RT><<<1, 256, 0, s>>>(n, k0, kb, Ss, Li, (RT)drop_tol, dr, nd);
         LG_TRY(check_launch("cholesky diag"));
         const int rem = n - k0 - kb;
         if (rem > 0) {
-            k_chol_panel<<<(rem + 7) / 8, 256, 0, s>>>(n, k0, kb, Ss, Li, dr);
+            k_chol_panel<RT><<<(rem + 7) / 8, 256, 0, s>>>(n, k0, kb, Ss, Li, dr);
             LG_TRY(check_launch("cholesky panel"));
-            const z64 *L21 = Ss + (size_t)k0 * n + k0 + kb;
-            z64 *S22 = Ss + (size_t)(k0 + kb) * n + k0 + kb;
-            LG_TRY(zgemm_small(&w.gw, 'N', 'C', rem, rem, kb, -1.0, L21, n, L21, n, 1.0, S22, n, s));
+            const cx<RT> *L21 = Ss + (size_t)k0 * n + k0 + kb;
+            cx<RT> *S22 = Ss + (size_t)(k0 + kb) * n + k0 + kb;
+            LG_TRY(gemm_small<RT>(&w.gw, 'N', 'C', rem, rem, kb, -1.0, L21, n, L21, n, 1.0, S22, n, s));
         }
     }
-    k_zero_dropped_rows<<<n, 128, 0, s>>>(n, Ss, dr);
+    k_zero_dropped_rows<RT><<<n, 128, 0, s>>>(n, Ss, dr);
     LG_TRY(check_launch("zero dropped rows"));
     // off-diagonal blocks of L^-1, block row by block row
     for (int r0 = NBK; r0 < n; r0 += NBK) {
         const int kb = std::min(NBK, n - r0);
         // Tm(kb x r0) = L[r0:r0+kb, 0:r0] * Li[0:r0, 0:r0]
-        LG_TRY(zgemm_small(&w.gw, 'N', 'N', kb, r0, r0, 1.0, Ss + r0, n, Li, n, 0.0, Tm, n, s));
+        LG_TRY(gemm_small<RT>(&w.gw, 'N', 'N', kb, r0, r0, 1.0, Ss + r0, n, Li, n, 0.0, Tm, n, s));
         // Li[r0:r0+kb, 0:r0] = -Li_rr * Tm
-        LG_TRY(zgemm_small(&w.gw, 'N', 'N', kb, r0, kb, -1.0, Li + (size_t)r0 * n + r0, n, Tm, n, 0.0, Li + r0, n, s));
+        LG_TRY(gemm_small<RT>(&w.gw, 'N', 'N', kb, r0, kb, -1.0, Li + (size_t)r0 * n + r0, n, Tm, n, 0.0, Li + r0, n, s));
     }
     // Ahat = Li As Li^H
-    LG_TRY(zgemm_small(&w.gw, 'N', 'N', n, n, n, 1.0, Li, n, As, n, 0.0, Tm, n, s));
-    LG_TRY(zgemm_small(&w.gw, 'N', 'C', n, n, n, 1.0, Tm, n, Li, n, 0.0, As, n, s));
-    k_hermitize_rowsum<<<n, 128, 0, s>>>(n, As, dr, rs);
+    LG_TRY(gemm_small<RT>(&w.gw, 'N', 'N', n, n, n, 1.0, Li, n, As, n, 0.0, Tm, n, s));
+    LG_TRY(gemm_small<RT>(&w.gw, 'N', 'C', n, n, n, 1.0, Tm, n, Li, n, 0.0, As, n, s));
+    k_hermitize_rowsum<RT><<<n, 128, 0, s>>>(n, As, dr, rs);
     LG_TRY(check_launch("hermitize"));
-    k_set_dropped_diag<<<1, 1024, 0, s>>>(n, As, dr, nd, rs);
+    k_set_dropped_diag<RT><<<1, 1024, 0, s>>>(n, As, dr, nd, rs);
     LG_TRY(check_launch("dropped diag"));
-    LG_TRY(heev_lowest(w, n, m, As, n, theta, Q, n, s));
+    LG_TRY(heev_lowest_t<RT>(w, n, m, As, n, theta, Q, n, s));
     // C = D Li^H Q
-    LG_TRY(zgemm_small(&w.gw, 'C', 'N', n, m, n, 1.0, Li, n, Q, n, 0.0, Tm, n, s));
-    k_scale_rows_copy<<<dim3((n + 127) / 128, m), 128, 0, s>>>(n, m, d, Tm, n, C, ldc);
+    LG_TRY(gemm_small<RT>(&w.gw, 'C', 'N', n, m, n, 1.0, Li, n, Q, n, 0.0, Tm, n, s));
+    k_scale_rows_copy<RT><<<dim3((n + 127) / 128, m), 128, 0, s>>>(n, m, d, Tm, n, C, ldc);
     LG_TRY(check_launch("scale C"));
     if (ndropped) {
         k_copy_int<<<1, 1, 0, s>>>(nd, ndropped);
         LG_TRY(check_launch("copy ndropped"));
     }
     return LOBPCG_OK;
+}
+
+int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V, int ldv, cudaStream_t s) {
+    return heev_lowest_t<double>(w, n, m, A, lda, theta, V, ldv, s);
+}
+int hermitize_lower(EigWork &w, int n, z64 *A, cudaStream_t s) { return hermitize_lower_t<double>(w, n, A, s); }
+int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,
+                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s) {
+    return rayleigh_ritz_t<double>(w, n, m, S, lds, A, lda, drop_tol, theta, C, ldc, ndropped, s);
+}
+int rayleigh_ritz32(EigWork &w, int n, int m, const c32 *S, int lds, const c32 *A, int lda, double drop_tol,
+                    float *theta, c32 *C, int ldc, int *ndropped, cudaStream_t s) {
+    return rayleigh_ritz_t<float>(w, n, m, S, lds, A, lda, drop_tol, theta, C, ldc, ndropped, s);
 }
 
 }  // namespace lg

@@ -98,14 +98,57 @@ __global__ void k_axpy_cols(int rows, int cols, double alpha, const z64 *__restr
     }
 }
 
+// Rayleigh quotients theta_j = Re(x_j^H (Hx)_j) / x_j^H x_j in FP64 (one block per column).
+__global__ void __launch_bounds__(256)
+k_rayleigh_quotients(int npw, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX, int ldhx,
+                     double *__restrict__ theta) {
+    const int j = blockIdx.x;
+    double xx = 0.0, xh = 0.0;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+        const z64 x = X[(size_t)j * ldx + g], h = HX[(size_t)j * ldhx + g];
+        xx += abs2(x);
+        xh += x.x * h.x + x.y * h.y;
+    }
+    block_sum2(xx, xh);
+    if (threadIdx.x == 0) theta[j] = xx > 0.0 ? xh / xx : 0.0;
+}
+
+// R = HX - X theta in FP64, stored in FP32.
+__global__ void k_residual32(int npw, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX, int ldhx,
+                             const double *__restrict__ theta, c32 *__restrict__ R, int ldr) {
+    const int j = blockIdx.y;
+    const double th = theta[j];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+        const z64 x = X[(size_t)j * ldx + g], hx = HX[(size_t)j * ldhx + g];
+        R[(size_t)j * ldr + g] = mkc<float>((float)(hx.x - th * x.x), (float)(hx.y - th * x.y));
+    }
+}
+
+// W = K(R) (Teter-Payne-Allan, x = T(q)/Ekin_j) on FP32 columns.
+__global__ void k_precond32(int npw, const c32 *__restrict__ R, int ldr, const double *__restrict__ kin,
+                            const double *__restrict__ ekin, c32 *__restrict__ W, int ldw) {
+    const int j = blockIdx.y;
+    const double ie = 1.0 / ekin[j];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+        const double t = kin[g] * ie;
+        const double p = 27.0 + t * (18.0 + t * (12.0 + 8.0 * t));
+        const double t2 = t * t;
+        const float k = (float)(p / (p + 16.0 * t2 * t2));
+        const c32 r = R[(size_t)j * ldr + g];
+        W[(size_t)j * ldw + g] = mkc<float>(k * r.x, k * r.y);
+    }
+}
+
 // nz x nz pencil of the mixed schedule.
 //   mx = 0: S = S32 (ld lds32), A = A32 (ld lda32), both full FP32 Grams.
 //   mx > 0: the basis is [X W P] with X the orthonormal Ritz block (mx columns)
 //     and [W P] projected out of span(X).  T1 = S32 = [R W P]^H [W P] (nz x nw,
 //     ld lds32) and T2 = A32 = [W P]^H [HW HP] (nw x nw, ld lda32), nw = nz - mx:
 //     S = [[I, 0], [0, T1[mx:, :]]],  A = [[diag(theta), T1[:mx, :]], [T1[:mx, :]^H, T2]].
+template <typename Ro>
 __global__ void k_assemble(int nz, int mx, const c32 *__restrict__ S32, int lds32, const c32 *__restrict__ A32,
-                           int lda32, const double *__restrict__ theta, z64 *__restrict__ S, z64 *__restrict__ A) {
+                           int lda32, const double *__restrict__ theta, cx<Ro> *__restrict__ S,
+                           cx<Ro> *__restrict__ A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= nz) return;
     z64 s, a;
@@ -130,8 +173,8 @@ __global__ void k_assemble(int nz, int mx, const c32 *__restrict__ S32, int lds3
         s = mkc(0.0, 0.0);
         a = cvt<double, float>(S32[(size_t)(j - mx) * lds32 + i]);
     }
-    S[(size_t)j * nz + i] = s;
-    A[(size_t)j * nz + i] = a;
+    S[(size_t)j * nz + i] = cvt<Ro, double>(s);
+    A[(size_t)j * nz + i] = cvt<Ro, double>(a);
 }
 
 // FP64 diagonals of X^H X and X^H HX (one block per column) written onto the
@@ -225,14 +268,62 @@ int axpy_cols(int rows, int cols, double alpha, const z64 *D, int ldd, z64 *V, i
 
 int assemble_gram_mixed(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
                         z64 *S, z64 *A, cudaStream_t s) {
-    k_assemble<<<dim3((nz + 127) / 128, nz), 128, 0, s>>>(nz, mx, S32, lds32, A32, lda32, theta, S, A);
+    k_assemble<double><<<dim3((nz + 127) / 128, nz), 128, 0, s>>>(nz, mx, S32, lds32, A32, lda32, theta, S, A);
     return check_launch("assemble gram");
+}
+
+int assemble_gram_mixed32(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
+                          c32 *S, c32 *A, cudaStream_t s) {
+    k_assemble<float><<<dim3((nz + 127) / 128, nz), 128, 0, s>>>(nz, mx, S32, lds32, A32, lda32, theta, S, A);
+    return check_launch("assemble gram (fp32)");
+}
+
+int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    k_rayleigh_quotients<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, theta);
+    return check_launch("rayleigh quotients");
+}
+
+int residual32(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta, c32 *R, int ldr,
+               cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    const int gx = std::max(1, std::min((npw + 255) / 256, 64));
+    k_residual32<<<dim3(gx, m), 256, 0, s>>>(npw, X, ldx, HX, ldhx, theta, R, ldr);
+    return check_launch("residual (fp32 out)");
+}
+
+int precond32(int npw, int m, const z64 *X, int ldx, const double *kin, const c32 *R, int ldr, c32 *W, int ldw,
+              double *work, cudaStream_t s) {
+    if (m <= 0) return LOBPCG_OK;
+    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, work);
+    LG_TRY(check_launch("ekin"));
+    const int gx = std::max(1, std::min((npw + 255) / 256, 64));
+    k_precond32<<<dim3(gx, m), 256, 0, s>>>(npw, R, ldr, kin, work, W, ldw);
+    return check_launch("preconditioner (fp32)");
 }
 
 int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
     k_diag_pencil<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, S, A, m);
     return check_launch("diagonal of the pencil");
+}
+
+__global__ void k_fill_random(int rows, int cols, z64 *__restrict__ X, int ldx, unsigned seed) {
+    const size_t tot = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)j + seed) * 0x85EBCA77u;
+        h ^= h >> 16; h *= 0x7FEB352Du; h ^= h >> 15; h *= 0x846CA68Bu; h ^= h >> 16;
+        unsigned g = h * 0x27D4EB2Fu + 0x165667B1u;
+        g ^= g >> 15; g *= 0x2C1B3C6Du; g ^= g >> 12;
+        X[(size_t)j * ldx + i] = mkc((double)h * (2.0 / 4294967296.0) - 1.0, (double)g * (2.0 / 4294967296.0) - 1.0);
+    }
+}
+
+int fill_random(int rows, int cols, z64 *X, int ldx, unsigned seed, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_fill_random<<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, seed);
+    return check_launch("fill random");
 }
 
 int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,

@@ -138,3 +138,25 @@ def test_rayleigh_ritz_drops_dependent_columns():
     assert np.abs(theta.cpu().numpy() - ref).max() < 1e-8 * np.abs(ref).max()
     C = C.cpu().numpy().T
     assert np.abs(C[[6, 7]]).max() < 1e-12 * np.abs(C).max()
+
+
+@pytest.mark.parametrize("n,m", [(3, 1), (48, 16), (128, 64), (192, 64)])
+def test_rayleigh_ritz_fp32(n, m):
+    """The FP32 Rayleigh-Ritz used inside the mixed-precision block iterations:
+    Ritz values to ~1e-5 relative, C^H S C = I to ~1e-4."""
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(100 + n + m)
+    Z = _c(rng, 4 * n, n)
+    H = _herm(rng, 4 * n)
+    S = Z.conj().T @ Z
+    A = Z.conj().T @ H @ Z
+    theta, C, nd = lg.rayleigh_ritz32(torch.tensor(S.T.copy(), dtype=torch.complex64, device="cuda"),
+                                      torch.tensor(A.T.copy(), dtype=torch.complex64, device="cuda"), m)
+    theta = theta.cpu().numpy().astype(float)
+    C = C.cpu().numpy().T.astype(complex)
+    ref = scipy.linalg.eigh(A, S, eigvals_only=True)[:m]
+    sc = np.abs(ref).max()
+    assert int(nd.item()) == 0
+    assert np.abs(theta - ref).max() < 2e-5 * sc
+    assert np.abs(C.conj().T @ S @ C - np.eye(m)).max() < 1e-3

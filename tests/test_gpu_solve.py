@@ -147,3 +147,16 @@ def test_solve_k96_one_block_vs_oracle_hamiltonian():
         rq = np.real(np.einsum("gi,gi->i", Xn.conj(), H.apply(Xn)))
         assert np.abs(rq - res.eig[0]).max() < 1e-10
         assert np.all(np.diff(res.eig[0]) >= -1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_with_buffer_bands(precision):
+    """nbuf extra bands are iterated but only the requested ones must converge;
+    the returned pairs are the lowest ones (golden values)."""
+    w = synth.tiny_workload(a=6.0, N=12, natoms=2, kpt=(0.25, 0.125, -0.375))
+    ref = np.loadtxt(os.path.join(GOLDEN, "tiny_kb_eig.txt"))
+    with make_solver(w, block_size=8, nline=4, max_sweeps=100, precision=precision, tol=1e-8, nbuf=5) as s:
+        X = _start(w, s, M=16)
+        res = s.solve([X])
+        assert res.status == 0
+        _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
