@@ -2,17 +2,17 @@
 
 Workload (default): the 96^3 cell -- a = 20 bohr, 57925 plane waves at
 k = (1/4, 1/4, 1/4), 64 Gaussian atoms on a jittered rock-salt lattice with
-256 Kleinman-Bylander projectors, 256 bands in blocks of 64, nline = 4,
-complex128 (seeded synthetic inputs, no pseudopotential data).
+256 Kleinman-Bylander projectors, 256 bands in blocks of 64 plus 64 buffer
+bands, nline = 4 (seeded synthetic inputs, no pseudopotential data).
 
-One step = one LOBPCG sweep (every block visited for nline iterations of
-Algorithm 1 with the block constraint, closed by the all-band Rayleigh-Ritz
-step and FP64 residuals), through ``lobpcg_solve`` with max_sweeps = 1.
-``value`` is H psi band-applies per second over the timed sweeps.  The JSON
-line also carries the time to a 1e-8 Ha residual of the FP64 and the mixed
-schedules (full solves from the same start), the standalone ``apply_H``
-throughput, the roofline of the dominant phase, the CPU-oracle baseline and
-the SM clocks seen during the timed region.
+One step = one full ``lobpcg_solve`` from the same seeded start block until
+every one of the 256 bands has an FP64 residual <= 1e-8 Ha (mixed FP32/FP64
+schedule by default).  ``ms_per_step`` is therefore the time to 1e-8 Ha and
+``value`` the H psi band-applies per second done on the way (FP32 and FP64
+applies counted alike).  The same line carries the FP64-only solve of the
+same problem from the same start (time, sweeps, eigenvalue difference), the
+standalone ``apply_H`` throughput, the roofline of the dominant phase, the
+CPU-oracle baseline and the SM clocks seen during the timed region.
 
 ``--impl reference`` times the CPU FP64 oracle on the same workload and metric
 (bounded samples on the host cores).
@@ -37,6 +37,7 @@ METRIC = "LOBPCG s to 1e-8 Ha residual, mixed vs FP64 on GB300; H·psi band-appl
 UNIT = "band-applies/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25          # GB300 FP64 (CUDA cores), nominal per GPU
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock = 80.5
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -47,10 +48,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="k96")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--nbuf", type=int, default=64, help="buffer bands above the wanted ones")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-sweeps", type=int, default=60)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-only comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--ttt-max-sweeps", type=int, default=120)
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the warm-up and timed steps of --mode, no other legs")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "apply"],
@@ -66,7 +69,7 @@ def ncu_run(args):
     import __graft_entry__
     __graft_entry__.build()
     w = make(args.workload)
-    s = solver_for(w, args.precision, timing=False, max_sweeps=1, tol=1e-30)
+    s = solver_for(w, args.precision, timing=False, max_sweeps=1, tol=1e-30, nbuf=args.nbuf)
     X = start_block(w, s)
     if args.mode == "apply" and args.precision == "mixed":
         X = X.to(torch.complex64)
@@ -153,11 +156,12 @@ def make(workload: str):
     return synth.make_workload(workload)
 
 
-def solver_for(w, precision, timing=False, max_sweeps=1, tol=1e-8):
+def solver_for(w, precision, timing=False, max_sweeps=1, tol=1e-8, nbuf=0):
     import paper_0707_3405_gb300 as lg
     return lg.Solver(w.a, w.N, w.ecut, w.kpts, w.vloc(), w.proj_E if w.nproj else None,
                      beta=(lambda mil, k: w.beta(mil, k)) if w.nproj else None, block_size=w.block,
-                     nline=w.nline, max_sweeps=max_sweeps, precision=precision, tol=tol, timing=timing)
+                     nline=w.nline, max_sweeps=max_sweeps, precision=precision, tol=tol, timing=timing,
+                     nbuf=nbuf)
 
 
 def start_block(w, s, k=0, device=True, pinned=False):
@@ -263,6 +267,34 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def roofline_of(ph_ms, ph_ms64, ph_fl, ph_fl64, ph_by, ph_by64, ph_calls, steps, pk, pk_kind):
+    """Roofline of the (phase, arithmetic precision) segment that took the most device time."""
+    segs = []
+    for p in ph_ms:
+        t64, t32 = ph_ms64[p], ph_ms[p] - ph_ms64[p]
+        segs.append((t64, p, "fp64", ph_fl64[p], ph_by64[p]))
+        segs.append((t32, p, "fp32", ph_fl[p] - ph_fl64[p], ph_by[p] - ph_by64[p]))
+    segs = [x for x in segs if x[0] > 0 and (x[3] > 0 or x[4] > 0)]
+    t_ms, p, prec, fl, by = max(segs)
+    t = t_ms / 1e3
+    if p in ("fft",) or fl == 0:
+        roof = {"bound": "hbm", "achieved": by / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"}
+    elif prec == "fp64":
+        roof = {"bound": "alu", "alu": "fp64", "achieved": fl / t / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (a probe measured 1.185)"}
+    else:
+        roof = {"bound": "alu", "alu": "fp32", "achieved": fl / t / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["phase"] = p
+    roof["precision"] = prec
+    roof["phase_share"] = t_ms / max(1e-9, sum(ph_ms.values()))
+    roof["calls_per_step"] = ph_calls[p] / max(1, steps)
+    return roof
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -281,16 +313,18 @@ def main():
     w = make(args.workload)
     pk, pk_kind = peaks()
 
-    s = solver_for(w, args.precision, timing=True, max_sweeps=1, tol=1e-30)
+    s = solver_for(w, args.precision, timing=True, max_sweeps=args.max_sweeps, tol=args.tol, nbuf=args.nbuf)
     npw = s.npw(0)
-    X = start_block(w, s)
+    X0 = start_block(w, s)
+    X = torch.empty_like(X0)
     stream = torch.cuda.current_stream()
 
-    def step(Xbuf):
+    def step(Xbuf, start):
+        Xbuf.copy_(start)
         return s.solve([Xbuf])
 
     for _ in range(max(args.warmup, 3)):
-        step(X)
+        step(X, X0)
     torch.cuda.synchronize()
     barrier(ws)
     clocks = ClockSampler(torch.cuda.current_device())
@@ -299,22 +333,22 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    applies = 0
-    ph_ms = {p: 0.0 for p in lg.PHASES}
-    ph_fl = {p: 0.0 for p in lg.PHASES}
-    ph_by = {p: 0.0 for p in lg.PHASES}
-    ph_calls = {p: 0 for p in lg.PHASES}
-    ph_f64 = {p: 0.0 for p in lg.PHASES}
+    applies, sweeps, converged, maxres = 0, [], True, 0.0
+    keys = ("ph_ms", "ph_ms_fp64", "ph_flops", "ph_fp64_flops", "ph_bytes", "ph_bytes_fp64", "ph_calls")
+    acc = {k: {p: 0.0 for p in lg.PHASES} for k in keys}
+    visits = [0, 0]
     for _ in range(args.steps):
-        r = step(X)
+        r = step(X, X0)
         st = r.stats
         applies += st["band_applies_fp64"] + st["band_applies_fp32"]
-        for p in lg.PHASES:
-            ph_ms[p] += st["ph_ms"][p]
-            ph_fl[p] += st["ph_flops"][p]
-            ph_by[p] += st["ph_bytes"][p]
-            ph_calls[p] += st["ph_calls"][p]
-            ph_f64[p] += st["ph_fp64_flops"][p]
+        sweeps.append(st["sweeps"])
+        converged = converged and r.status == 0
+        maxres = max(maxres, float(r.resid.max()))
+        visits[0] += st["block_visits_fp32"]
+        visits[1] += st["block_visits_fp64"]
+        for k in keys:
+            for p in lg.PHASES:
+                acc[k][p] += st[k][p]
     e1.record(stream)
     torch.cuda.synchronize()
     launches = lg.launch_count() - l0
@@ -324,43 +358,30 @@ def main():
     t_max = max_over_ranks(t, ws)
     total_applies = sum_over_ranks(applies, ws)
     value = total_applies / t_max
+    eig_main = r.eig.copy()
+    roof = roofline_of(acc["ph_ms"], acc["ph_ms_fp64"], acc["ph_flops"], acc["ph_fp64_flops"], acc["ph_bytes"],
+                       acc["ph_bytes_fp64"], acc["ph_calls"], args.steps, pk, pk_kind)
 
-    # roofline of the dominant phase (device time from the library's CUDA events)
-    dom = max(ph_ms, key=lambda p: ph_ms[p])
-    dom_s = ph_ms[dom] / 1e3
-    if dom == "fft" and args.precision == "mixed":
-        roof = {"bound": "hbm", "achieved": ph_by[dom] / dom_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
-    elif ph_f64[dom] >= 0.5 * ph_fl[dom]:
-        roof = {"bound": "alu", "achieved": ph_fl[dom] / dom_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "alu": "fp64"}
-    else:
-        roof = {"bound": "alu", "achieved": ph_fl[dom] / dom_s / 1e12, "peak": 74.0, "unit": "TFLOP/s",
-                "alu": "fp32"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["phase"] = dom
-    roof["phase_share"] = ph_ms[dom] / max(1e-9, sum(ph_ms.values()))
-    roof["launches_per_step"] = ph_calls[dom] / max(1, args.steps)
-    roof["peak_source"] = ("GB300 FP64 nominal 1.25 TFLOP/s (probe measured 1.185)" if roof.get("alu") == "fp64"
-                           else ("GB300 FP32 FMA probe 74 TFLOP/s" if roof.get("alu") == "fp32"
-                                 else f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"))
-
-    # end to end through the same public call with pinned host buffers
-    Xh = X.cpu().pin_memory()
+    # end to end through the same public call, start vectors in pinned host memory
+    Xh0 = X0.cpu().pin_memory()
+    Xh = torch.empty_like(Xh0).pin_memory()
+    n_e2e = max(1, min(2, args.steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r = step(Xh)
-    t_e2e = time.perf_counter() - t0
-    e2e_applies = args.steps * (r.stats["band_applies_fp64"] + r.stats["band_applies_fp32"])
-    t_e2e = max_over_ranks(t_e2e, ws)
-    e2e = {"value": sum_over_ranks(e2e_applies, ws) / t_e2e, "unit": UNIT,
-           "h2d_bytes_per_step": 16 * npw * w.nbands, "d2h_bytes_per_step": 16 * npw * w.nbands + 16 * w.nbands}
+    e2e_applies = 0
+    for _ in range(n_e2e):
+        Xh.copy_(Xh0)
+        r = s.solve([Xh])
+        e2e_applies += r.stats["band_applies_fp64"] + r.stats["band_applies_fp32"]
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": sum_over_ranks(e2e_applies, ws) / t_e2e, "unit": UNIT, "s_per_solve": t_e2e / n_e2e,
+           "h2d_bytes_per_step": 16 * npw * w.nbands,
+           "d2h_bytes_per_step": 16 * npw * w.nbands + 16 * w.nbands}
 
     # standalone apply_H throughput on all bands
     applyh = {}
     for dt, name in ((torch.complex128, "c128"), (torch.complex64, "c64")):
-        Xa = X.to(dt)
+        Xa = X0.to(dt)
         Ya = torch.empty_like(Xa)
         for _ in range(2):
             s.apply_H(0, Xa, Ya)
@@ -374,28 +395,24 @@ def main():
         applyh[f"{name}_band_applies_per_s"] = reps * w.nbands / (a0.elapsed_time(a1) / 1e3)
     s.close()
 
-    # time to tolerance, FP64 vs mixed, from the same start
-    ttt = None
-    if not args.no_ttt:
-        ttt = {"tol": 1e-8}
-        for prec in ("mixed", "fp64"):
-            s2 = solver_for(w, prec, timing=False, max_sweeps=args.ttt_max_sweeps, tol=1e-8)
-            X2 = start_block(w, s2)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r2 = s2.solve([X2])
-            el = time.perf_counter() - t0
-            ttt[f"{prec}_s"] = el
-            ttt[f"{prec}_sweeps"] = r2.stats["sweeps"]
-            ttt[f"{prec}_converged"] = bool(r2.status == 0)
-            ttt[f"{prec}_max_resid"] = float(r2.resid.max())
-            ttt[f"{prec}_band_applies"] = {"fp64": r2.stats["band_applies_fp64"], "fp32": r2.stats["band_applies_fp32"]}
-            if prec == "mixed":
-                eig_mixed = r2.eig.copy()
-            else:
-                ttt["max_eig_diff_mixed_vs_fp64_Ha"] = float(np.abs(r2.eig - eig_mixed).max())
-            s2.close()
-        ttt["speedup_mixed_vs_fp64"] = ttt["fp64_s"] / ttt["mixed_s"]
+    # the FP64-only path on the same problem from the same start
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        s2 = solver_for(w, "fp64", timing=False, max_sweeps=args.max_sweeps, tol=args.tol, nbuf=args.nbuf)
+        X2 = X0.clone()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        r2 = s2.solve([X2])
+        f1.record(stream)
+        torch.cuda.synchronize()
+        el = f0.elapsed_time(f1) / 1e3
+        fp64 = {"s_to_tol": el, "sweeps": r2.stats["sweeps"], "converged": bool(r2.status == 0),
+                "max_resid": float(r2.resid.max()),
+                "band_applies": r2.stats["band_applies_fp64"] + r2.stats["band_applies_fp32"],
+                "max_eig_diff_vs_main_Ha": float(np.abs(r2.eig - eig_main).max()),
+                "speedup_main_vs_fp64": el / (t_max / args.steps)}
+        s2.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -409,21 +426,25 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "c128/f64" if args.precision == "fp64" else "mixed c64/f32 + c128/f64",
+            "dtype": "c128/f64" if args.precision == "fp64" else "c64/f32 + c128/f64",
             "data": "synthetic",
             "config": {"workload": w.name, "a_bohr": w.a, "N": w.N, "npw": npw, "kpt": list(map(float, w.kpts[0])),
                        "natoms": len(w.pos), "nproj": w.nproj, "nbands": w.nbands, "block": w.block,
-                       "nline": w.nline, "precision": args.precision, "step": "one LOBPCG sweep",
+                       "nbuf": args.nbuf, "nline": w.nline, "precision": args.precision, "tol_Ha": args.tol,
+                       "step": f"one lobpcg_solve to max residual <= {args.tol:g} Ha from the same start",
                        "l2": f"inputs larger than L2 (X is {16 * npw * w.nbands / 1e6:.0f} MB)",
                        "parallelism": f"replicas x{ws}"},
+            "s_to_tol": t_max / args.steps,
+            "sweeps": sweeps, "converged": converged, "max_resid": maxres,
+            "block_visits": {"fp32": visits[0], "fp64": visits[1]},
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": roof,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "apply_H": applyh,
-            "time_to_tol": ttt,
-            "phases_ms_per_step": {p: ph_ms[p] / args.steps for p in lg.PHASES},
+            "fp64_path": fp64,
+            "phases_ms_per_step": {p: acc["ph_ms"][p] / args.steps for p in lg.PHASES},
         }
         print(json.dumps(line))
     if ws > 1:

@@ -133,6 +133,8 @@ typedef struct {
     double    ph_fp64_flops[LOBPCG_PH_COUNT];  /* part of ph_flops done in FP64 arithmetic */
     long long block_visits_fp32;  /* block visits run with the mixed FP32/FP64 schedule */
     long long block_visits_fp64;  /* block visits run entirely in FP64 */
+    double    ph_ms_fp64[LOBPCG_PH_COUNT];     /* part of ph_ms spent in calls doing FP64 arithmetic */
+    double    ph_bytes_fp64[LOBPCG_PH_COUNT];  /* part of ph_bytes moved by those calls */
 } lobpcg_stats;
 
 /* Fill *opt with defaults: m = 64, nline = 4, max_sweeps = 100, FP64, tol = 1e-8. */

@@ -62,12 +62,15 @@ void Prof::end(int ph, cudaEvent_t a, double fl, double by, bool fp64) {
     if (!on) return;
     flops[ph] += fl;
     bytes[ph] += by;
-    if (fp64) fp64_flops[ph] += fl;
+    if (fp64) {
+        fp64_flops[ph] += fl;
+        bytes64[ph] += by;
+    }
     calls[ph] += 1;
     cudaEvent_t b = get();
     if (!a || !b) return;
     cudaEventRecord(b, s);
-    recs.push_back({ph, a, b});
+    recs.push_back({ph, fp64, a, b});
     if (recs.size() > 4096) collect();
 }
 
@@ -76,8 +79,12 @@ void Prof::collect() {
     cudaEventSynchronize(recs.back().b);
     for (auto &r : recs) {
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.ph] += t;
-        else cudaGetLastError();
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            ms[r.ph] += t;
+            if (r.f64) ms64[r.ph] += t;
+        } else {
+            cudaGetLastError();
+        }
         pool.push_back(r.a);
         pool.push_back(r.b);
     }
@@ -1061,6 +1068,8 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
             st->ph_bytes[p] = prof.bytes[p];
             st->ph_calls[p] = prof.calls[p];
             st->ph_fp64_flops[p] = prof.fp64_flops[p];
+            st->ph_ms_fp64[p] = prof.ms64[p];
+            st->ph_bytes_fp64[p] = prof.bytes64[p];
         }
     }
     return worst;

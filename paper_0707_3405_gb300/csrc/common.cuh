@@ -99,13 +99,15 @@ long long launch_count();
 struct Prof {
     bool on = false;
     cudaStream_t s = nullptr;
-    struct Rec { int ph; cudaEvent_t a, b; };
+    struct Rec { int ph; bool f64; cudaEvent_t a, b; };
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> recs;
     double ms[LOBPCG_PH_COUNT] = {0};
+    double ms64[LOBPCG_PH_COUNT] = {0};   // part of ms[] spent in scopes doing FP64 arithmetic
     double flops[LOBPCG_PH_COUNT] = {0};
     double fp64_flops[LOBPCG_PH_COUNT] = {0};
     double bytes[LOBPCG_PH_COUNT] = {0};
+    double bytes64[LOBPCG_PH_COUNT] = {0};
     long long calls[LOBPCG_PH_COUNT] = {0};
     cudaEvent_t get();
     // Start timing phase `ph`; returns the start event (nullptr when off).
