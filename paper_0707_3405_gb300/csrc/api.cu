@@ -819,18 +819,21 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
     c->nk = nk;
     c->nproj = nproj;
     const int N = cell->N;
-    // potential: [x][y][z] -> [z][x][y], scaled by 1/N^3 (the forward FFT's normalisation)
+    // potential: [x][y][z] -> [z][x][y] (FP32 register FFT: [y][x][z]), scaled by 1/N^3
+    // (the forward FFT's normalisation)
     const size_t N3 = (size_t)N * N * N;
     std::vector<double> vt(N3);
     std::vector<float> vt32(N3);
     const double inv = 1.0 / (double)N3;
+    const bool reg32 = fft_reg_supported(N);
+    if (reg32) LG_TRY(fft_reg_prepare());
     for (int x = 0; x < N; ++x)
         for (int y = 0; y < N; ++y)
             for (int z = 0; z < N; ++z) {
                 const double v = vloc_r[((size_t)x * N + y) * N + z] * inv;
                 if (!std::isfinite(v)) return fail(LOBPCG_ERR_ARG, "vloc_r has non-finite values");
                 vt[((size_t)z * N + x) * N + y] = v;
-                vt32[((size_t)z * N + x) * N + y] = (float)v;
+                vt32[reg32 ? ((size_t)y * N + x) * N + z : ((size_t)z * N + x) * N + y] = (float)v;
             }
     LG_TRY(upload(c, &c->vt64, vt.data(), N3));
     LG_TRY(upload(c, &c->vt32, vt32.data(), N3));

@@ -171,13 +171,23 @@ bool make_fft_plan(int N, FFTPlan &plan);
 
 // Local-potential application Y = V_loc X (+ T X) for a block of bands on one k-point.
 //   X, Y: npw x nb column-major (ld = ldx / ldy) of cx<R>; T: npw kinetic (nullable)
-//   vt:   device potential pre-scaled by 1/N^3, layout [z][x][y]
+//   vt:   device potential pre-scaled by 1/N^3, layout [z][x][y] ([y][x][z] for the
+//         FP32 register variant)
 //   tw:   device twiddles e^{-2 pi i t / N}, t < N
 //   T2:   scratch of at least nbatch * Px * N * N cx<R>
 template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy,
                    int nb, const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch,
                    cudaStream_t s);
+// FP32 register-resident variant of the three passes for the grid edges it is
+// compiled for (8, 12, 16, 20, 24, 36, 48, 64, 72, 96, 120, 128, 160).  Its scratch is laid out T2[b][px][y][z]
+// and its potential table vt as [y][x][z] (pre-scaled by 1/N^3);
+// fft_vloc_apply<float> routes to it whenever fft_reg_supported(N).
+bool fft_reg_supported(int N);
+int fft_reg_prepare();                        // twiddle constants on the current device (once)
+size_t fft_reg_smem_need(const FFTGeom &g);
+int fft_reg_apply(const FFTGeom &g, const c32 *X, int ldx, c32 *Y, int ldy, int nb, const float *kin,
+                  const float *vt, c32 *T2, int nbatch, cudaStream_t s);
 // Algorithmic floating-point operations of the three passes for one band
 // (5 n log2 n per length-n complex line FFT, plus the V and T multiplies).
 double fft_flops_per_band(const FFTGeom &g);

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 namespace lg {
 
@@ -365,6 +366,10 @@ double fft_flops_per_band(const FFTGeom &g) {
 
 template <typename R>
 size_t fft_smem_need(const FFTGeom &g) {
+    if (std::is_same<R, float>::value && fft_reg_supported(g.N)) {
+        const size_t need = fft_reg_smem_need(g);
+        return need <= (size_t)max_dyn_smem() ? need : 0;
+    }
     const int zc = pick_zc<R>(g);
     return zc ? smem_ac<R>(g, zc) : 0;
 }
@@ -373,6 +378,9 @@ template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
                    const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch, cudaStream_t s) {
     if (nb <= 0) return LOBPCG_OK;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fft_reg_supported(g.N)) return fft_reg_apply(g, X, ldx, Y, ldy, nb, kin, vt, T2, nbatch, s);
+    }
     const int N = g.N;
     const int zc = pick_zc<R>(g);
     if (zc == 0) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT grid too large for shared memory");
