@@ -93,7 +93,9 @@ typedef struct {
     int    nline;        /* Algorithm 1 iterations per block visit (paper: 4) */
     int    max_sweeps;   /* sweeps over all blocks before giving up */
     int    precision;    /* LOBPCG_FP64 or LOBPCG_MIXED */
-    int    gemm_split;   /* mixed path GEMM mode: 0 = auto, 1 = BF16x3, 2 = TF32x3, 3 = FP32 SIMT */
+    int    gemm_split;   /* complex64 GEMM engine: 0 = auto (= 2), 2 = tensor cores with 3xTF32 split
+                            operands for long reductions and tall products, 3 = CUDA cores only;
+                            1 (BF16x3) is not built: ERR_UNSUPPORTED */
     int    use_graph;    /* 1: replay block iterations as CUDA graphs */
     int    autotune;     /* 1: time kernel variants once per shape and keep the fastest */
     double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */

@@ -87,6 +87,25 @@ int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double 
  */
 int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream);
 
+/*
+ * Engine of the complex64 (LOBPCG_C64) GEMMs, process-wide; lobpcg_solve and
+ * lobpcg_apply_H set it from lobpcg_options.gemm_split on entry.
+ *   0 (auto) or 2: 5th-generation tensor cores (tcgen05, accumulators in TMEM)
+ *      with 3xTF32 split operands and FP32 accumulation (relative error about
+ *      1e-6 of sum |a||b|) for long reductions (A^H B with K >= 1024) and tall
+ *      products (A B with M >= 1024); CUDA cores for the other shapes.
+ *   3: CUDA cores only (FP32 products, FP64 accumulation every 256 terms).
+ * Returns ERR_ARG for other values (1, BF16x3, is not built).
+ */
+int lobpcg_k_set_gemm_mode(int mode);
+
+/*
+ * Synchronises the device, then returns LOBPCG_ERR_TIMEOUT if a tensor-core
+ * GEMM launched so far stopped because an mbarrier wait ran out (its output is
+ * then not valid), else LOBPCG_OK.  Clears the condition.
+ */
+int lobpcg_k_check_timeouts(void);
+
 /* Message of the last failure of a lobpcg_k_* call on this host thread. */
 const char *lobpcg_k_last_error(void);
 

@@ -32,7 +32,8 @@ EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
-    "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev", "lobpcg_k_last_error",
+    "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
+    "lobpcg_k_set_gemm_mode", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
 
 
@@ -111,6 +112,8 @@ def load() -> ctypes.CDLL:
         "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_rayleigh_ritz32": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_heev": (i, [i, vp, vp, vp, vp]),
+        "lobpcg_k_set_gemm_mode": (i, [i]),
+        "lobpcg_k_check_timeouts": (i, []),
         "lobpcg_k_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -314,6 +317,17 @@ def launch_count() -> int:
 
 
 # ---------------------------------------------------------------- dense building blocks
+def set_gemm_mode(mode: int):
+    """Complex64 GEMM engine, process-wide: 0 or 2 = tensor cores (3xTF32) for long
+    reductions and tall products, 3 = CUDA cores only."""
+    _check(load().lobpcg_k_set_gemm_mode(int(mode)), None, kernels=True)
+
+
+def check_timeouts():
+    """Synchronise; raise LobpcgError(ERR_TIMEOUT) if a tensor-core GEMM gave up waiting."""
+    _check(load().lobpcg_k_check_timeouts(), None, kernels=True)
+
+
 def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None):
     """C = alpha A^H B + beta C for torch CUDA tensors given as (cols, rows) row-major
     (i.e. column-major matrices): A is (m, K), B is (n, K), C is (n, m)."""

@@ -762,6 +762,7 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
             maxr = std::max(maxr, res_h[i]);
         }
         if (sv.verbose >= 1) fprintf(stderr, "[lobpcg] k=%d sweep=%d max_resid=%.3e\n", k, sw, maxr);
+        if (sv.mixed) LG_TRY(tc_check_error());
         if (!finite) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite Ritz value or residual");
         std::copy(res_h, res_h + M, res_prev.begin());
         if (maxr <= c->opt.tol) break;
@@ -780,6 +781,9 @@ int validate_options(const lobpcg_options &o) {
     if (!(o.tol > 0.0)) return fail(LOBPCG_ERR_ARG, "tol must be > 0");
     if (3 * o.block_size > 4096) return fail(LOBPCG_ERR_ARG, "block_size too large (3 m must be <= 4096)");
     if (o.nbuf < 0) return fail(LOBPCG_ERR_ARG, "nbuf must be >= 0");
+    if (o.gemm_split == 1) return fail(LOBPCG_ERR_UNSUPPORTED, "gemm_split 1 (BF16x3) is not built; use 2 (TF32x3)");
+    if (o.gemm_split != 0 && o.gemm_split != 2 && o.gemm_split != 3)
+        return fail(LOBPCG_ERR_ARG, "gemm_split must be 0, 2 or 3");
     if (!(o.mixed_switch >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_switch must be >= 0");
     return LOBPCG_OK;
 }
@@ -988,6 +992,7 @@ static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int 
 
 int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int precision) {
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
+    set_gemm_mode(ctx->opt.gemm_split);
     return ret(ctx, apply_impl(ctx, k, X, Y, nb, precision));
 }
 
@@ -1080,6 +1085,7 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
 
 int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid, lobpcg_stats *stats) {
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
+    set_gemm_mode(ctx->opt.gemm_split);
     return ret(ctx, solve_impl(ctx, nbands, X, eig, resid, stats));
 }
 

@@ -14,6 +14,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace lg {
 
@@ -201,15 +202,31 @@ int launch_gemm(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int l
 
 }  // namespace
 
+namespace {
+int g_gemm_mode = 0;
+// tensor-core thresholds: a long reduction (A^H B) or a tall product (A B)
+constexpr int kTcMinK = 1024, kTcMinM = 1024;
+}  // namespace
+
+void set_gemm_mode(int mode) { g_gemm_mode = mode; }
+int gemm_mode() { return g_gemm_mode; }
+
 template <typename R>
 int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb, R beta,
             cx<R> *C, int ldc, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (g_gemm_mode != 3 && K >= kTcMinK) return tc_gemm_cn(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    }
     return launch_gemm<R, true, false>(&w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s, true);
 }
 
 template <typename R>
 int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb, R beta,
             const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (g_gemm_mode != 3 && M >= kTcMinM && k > 0)
+            return tc_gemm_nn(M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s);
+    }
     return launch_gemm<R, false, false>(nullptr, M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, false);
 }
 

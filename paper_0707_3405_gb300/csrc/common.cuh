@@ -222,6 +222,19 @@ struct GemmWork {
 template <typename R>
 int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
             R beta, cx<R> *C, int ldc, cudaStream_t s);
+// Complex64 products on the tensor cores (3xTF32 split operands, FP32 accumulation):
+// C = alpha A^H B + beta C (K split over the GPU, FP64 partial sums) and
+// D = alpha A B + beta C.  gemm_cn<float> / gemm_nn<float> route here for long
+// reductions / tall products unless the GEMM mode says otherwise.
+int tc_gemm_cn(GemmWork &w, int m, int n, int K, float alpha, const c32 *A, int lda, const c32 *B, int ldb,
+               float beta, c32 *C, int ldc, cudaStream_t s);
+int tc_gemm_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c32 *B, int ldb, float beta,
+               const c32 *C, int ldc, c32 *D, int ldd, cudaStream_t s);
+int tc_check_error();   // LOBPCG_ERR_TIMEOUT if a tensor-core GEMM gave up waiting (clears the flag)
+// FP32 GEMM engine, process-wide: 0 = auto / 2 = tensor cores (TF32x3) where the shape suits them,
+// 3 = CUDA cores only.
+void set_gemm_mode(int mode);
+int gemm_mode();
 template <typename R>
 int gemm_nn(int M, int n, int k, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb, R beta,
             const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s);

@@ -104,6 +104,17 @@ int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream) {
     return rc;
 }
 
+int lobpcg_k_set_gemm_mode(int mode) {
+    if (mode != 0 && mode != 2 && mode != 3) return fail(LOBPCG_ERR_ARG, "gemm mode must be 0, 2 or 3");
+    set_gemm_mode(mode);
+    return LOBPCG_OK;
+}
+
+int lobpcg_k_check_timeouts(void) {
+    LG_CUDA_TRY(cudaDeviceSynchronize());
+    return tc_check_error();
+}
+
 const char *lobpcg_k_last_error(void) { return global_error(); }
 
 }  // extern "C"

@@ -62,6 +62,72 @@ def test_gemm_nn(M, n, k, prec):
     assert (np.abs(got - ref) / scale).max() < tol
 
 
+@pytest.fixture
+def gemm_mode():
+    import paper_0707_3405_gb300 as lg
+    yield lg.set_gemm_mode
+    lg.set_gemm_mode(0)
+
+
+# complex64 on the tensor cores (3xTF32): shapes of the projector, Gram, constraint and update
+# products, plus ragged edges (partial M / N tiles, K tails, N above one tile)
+@pytest.mark.parametrize("m,n,K", [(256, 256, 57925), (192, 128, 57925), (64, 64, 5000), (130, 7, 3001),
+                                   (17, 300, 2000), (1, 1, 1024), (129, 65, 1031)])
+@pytest.mark.parametrize("mode", [0, 3])
+def test_gemm_cn_c64_engines(m, n, K, mode, gemm_mode):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    gemm_mode(mode)
+    rng = np.random.default_rng(m * 13 + n + K)
+    A, B, C0 = _c(rng, K, m), _c(rng, K, n), _c(rng, m, n)
+    At = torch.tensor(A.T.copy(), dtype=torch.complex64, device="cuda")
+    Bt = torch.tensor(B.T.copy(), dtype=torch.complex64, device="cuda")
+    Ct = torch.tensor(C0.T.copy(), dtype=torch.complex64, device="cuda")
+    lg.gemm_cn(At, Bt, alpha=0.75, beta=0.5, C=Ct)
+    lg.check_timeouts()
+    A32 = At.cpu().numpy().T.astype(np.complex128)   # the inputs as the GPU sees them (rounded to FP32)
+    B32 = Bt.cpu().numpy().T.astype(np.complex128)
+    C32 = C0.astype(np.complex64).astype(np.complex128)
+    ref = 0.75 * A32.conj().T @ B32 + 0.5 * C32
+    scale = 0.75 * np.abs(A32).T @ np.abs(B32) + 0.5 * np.abs(C32)
+    got = Ct.cpu().numpy().T
+    assert (np.abs(got - ref) / scale).max() < 2e-6
+
+
+@pytest.mark.parametrize("M,n,k", [(57925, 256, 256), (57925, 64, 192), (3001, 7, 432), (1500, 300, 17),
+                                   (1024, 1, 1), (2049, 129, 65)])
+@pytest.mark.parametrize("mode", [0, 3])
+def test_gemm_nn_c64_engines(M, n, k, mode, gemm_mode):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    gemm_mode(mode)
+    rng = np.random.default_rng(M + 3 * n + k)
+    A, B, C0 = _c(rng, M, k), _c(rng, k, n), _c(rng, M, n)
+    At = torch.tensor(A.T.copy(), dtype=torch.complex64, device="cuda")
+    Bt = torch.tensor(B.T.copy(), dtype=torch.complex64, device="cuda")
+    Ct = torch.tensor(C0.T.copy(), dtype=torch.complex64, device="cuda")
+    D = lg.gemm_nn(At, Bt, alpha=-1.5, beta=1.0, C=Ct, D=Ct)
+    lg.check_timeouts()
+    A32 = At.cpu().numpy().T.astype(np.complex128)
+    B32 = Bt.cpu().numpy().T.astype(np.complex128)
+    C32 = C0.astype(np.complex64).astype(np.complex128)
+    ref = -1.5 * A32 @ B32 + C32
+    scale = 1.5 * np.abs(A32) @ np.abs(B32) + np.abs(C32)
+    got = D.cpu().numpy().T
+    assert (np.abs(got - ref) / scale).max() < 2e-6
+    # beta = 0 writes D without reading it
+    D2 = lg.gemm_nn(At, Bt, alpha=1.0, beta=0.0)
+    lg.check_timeouts()
+    assert (np.abs(D2.cpu().numpy().T - A32 @ B32) / (np.abs(A32) @ np.abs(B32))).max() < 2e-6
+
+
+def test_gemm_mode_rejects_unknown():
+    import paper_0707_3405_gb300 as lg
+    with pytest.raises(lg.LobpcgError):
+        lg.set_gemm_mode(1)
+    lg.set_gemm_mode(0)
+
+
 def _herm(rng, n):
     A = _c(rng, n, n)
     return A + A.conj().T
