@@ -105,7 +105,10 @@ typedef struct {
                             converge (rounded up to whole blocks; 0 = none).  They give the top wanted
                             bands a gap to the unresolved spectrum. */
     double mixed_switch; /* MIXED only: a block whose smallest residual after the previous sweep is
-                            below this (Ha) runs its iterations in FP64 (default 1e-6; 0 = never) */
+                            below this (Ha) runs its iterations in FP64 (default 0 = never) */
+    double mixed_early;  /* MIXED only: while the largest residual of the previous sweep is above this
+                            (Ha), block starts and the sweep-end Rayleigh-Ritz use the FP32 copies and
+                            skip the FP64 H X refresh (default 1e-3; 0 = never) */
 } lobpcg_options;
 
 /* Phases of a solve, for the per-phase timers of lobpcg_stats. */

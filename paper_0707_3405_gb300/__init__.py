@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("nline", ctypes.c_int), ("max_sweeps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gemm_split", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong),
-                ("timing", ctypes.c_int), ("nbuf", ctypes.c_int), ("mixed_switch", ctypes.c_double)]
+                ("timing", ctypes.c_int), ("nbuf", ctypes.c_int), ("mixed_switch", ctypes.c_double),
+                ("mixed_early", ctypes.c_double)]
 
 
 PHASES = ("fft", "nonlocal", "gram", "constraint", "rr", "update")
@@ -176,7 +177,7 @@ class Solver:
     def __init__(self, a: float, N: int, ecut: float, kpts, vloc, proj_E=None, beta=None,
                  block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
                  tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, nbuf: int = 0,
-                 mixed_switch: float | None = None, stream=None):
+                 mixed_switch: float | None = None, mixed_early: float | None = None, stream=None):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -187,7 +188,8 @@ class Solver:
         E = np.ascontiguousarray(np.zeros(0) if proj_E is None else np.asarray(proj_E, dtype=np.float64))
         self.nproj = int(E.shape[0])
         self.nk = int(kp.shape[0])
-        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch)
+        opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
+                            mixed_early)
         cell = Cell(a, N, ecut)
         self._stream = stream
         rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
@@ -203,7 +205,7 @@ class Solver:
 
     @staticmethod
     def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False, nbuf=0,
-                 mixed_switch=None) -> Options:
+                 mixed_switch=None, mixed_early=None) -> Options:
         o = default_options()
         o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -213,11 +215,14 @@ class Solver:
         o.nbuf = nbuf
         if mixed_switch is not None:
             o.mixed_switch = mixed_switch
+        if mixed_early is not None:
+            o.mixed_early = mixed_early
         return o
 
     def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0,
-                    timing=False, nbuf=0, mixed_switch=None):
-        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch)
+                    timing=False, nbuf=0, mixed_switch=None, mixed_early=None):
+        o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
+                          mixed_early)
         _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
 
     def set_stream(self, stream):

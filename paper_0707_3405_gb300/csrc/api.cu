@@ -176,7 +176,7 @@ struct lobpcg_ctx {
     EigWork ew;
     // solver buffers
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
-    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext;
+    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32;
     std::string err;
 };
 
@@ -354,16 +354,27 @@ bool is_device_ptr(const void *p) {
 // FP64 schedule: every vector, product and Gram matrix in FP64.
 //
 // Mixed schedule (the block iteration in FP32 around FP64 X and H X):
-//   * X_b and H X_b are kept in FP64; R = H X_b - X_b Theta is formed in FP64;
-//   * W = K(R), the constraint, H W (FP32 FFT and KB GEMMs), P and H P are FP32;
-//   * W and P are projected out of span(X_b) in FP32, so the Rayleigh-Ritz basis
+//   * block start in FP64: X_b is projected off the earlier blocks (H X_b along),
+//     then rotated by the Rayleigh-Ritz step of the block alone, so that X_b is
+//     orthonormal with X_b^H H X_b diagonal to FP64 accuracy;
+//   * X_b and H X_b are kept in FP64; R = H X_b - X_b Theta is formed in FP64 with
+//     exact FP64 Rayleigh quotients Theta;
+//   * W = K(R), the constraint, H W (FP32 FFT, tensor-core KB GEMMs), P and H P
+//     are FP32;
+//   * R, W and P are projected out of span(X_b) in FP32, so the Rayleigh-Ritz basis
 //     [X_b, W, P] has X-rows S = [I 0 0], A = [Theta, R^H W, R^H P]: the X-W and
 //     X-P couplings come from the FP64 residual (relatively accurate however small
 //     the residual is), never from X^H H W;
-//   * the Gram blocks of W and P are FP32 GEMMs, the Rayleigh-Ritz solve is FP64;
+//   * the Gram blocks of W and P are FP32 tensor-core GEMMs, the Rayleigh-Ritz
+//     solve is FP64;
 //   * X_b <- X_b C_X + P and H X_b <- H X_b C_X + H P are FP64;
 //   * every sweep ends with an FP64 H X refresh, the FP64 all-band Rayleigh-Ritz
-//     step and FP64 residual norms, which decide convergence.
+//     step and FP64 residual norms, which decide convergence;
+//   * early sweeps (largest residual of the previous sweep above opt.mixed_early):
+//     block starts and the sweep-end Rayleigh-Ritz run on the FP32 copies (tensor
+//     cores, FP64 diagonals and eigensolve) and H X is not refreshed; X and H X then
+//     carry FP32 accuracy, far below the residuals of those sweeps.  Convergence is
+//     only ever declared after a full (non-early) sweep.
 struct Solver {
     lobpcg_ctx *c;
     Prof *prof;
@@ -384,8 +395,8 @@ struct Solver {
     c32 *Q32[2], *HQ32[2];   // [R W P] and [. HW HP], npw x 3m
     c32 *X32, *HX32;         // FP32 copies of X_b, H X_b
     c32 *S32, *A32, *C32, *G32, *D32;
-    c32 *S32p, *A32p;        // FP32 Rayleigh-Ritz pencil (nz x nz)
-    float *theta32;          // FP32 Ritz values (only the FP64 Rayleigh quotients are used)
+    c32 *T32;                // npw x M FP32 scratch (early-sweep rotations)
+    bool early = false;      // current sweep is an early one of the mixed schedule
     long long applies64 = 0, applies32 = 0;
     int iterations = 0;
     int verbose = 0;          // LOBPCG_VERBOSE: 1 per sweep, 2 per iteration (synchronising diagnostics)
@@ -453,6 +464,11 @@ struct Solver {
     int cast(int cols, const cx<Ri> *a, cx<Ro> *b) {
         PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, (double)npw * cols * (sizeof(cx<Ri>) + sizeof(cx<Ro>)), false);
         return copy_cast<Ro, Ri>(npw, cols, a, npw, b, npw, s);
+    }
+    int copy32(c32 *dst, const c32 *src, int cols) {
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 2.0 * cbytes32(cols), false);
+        LG_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(c32) * (size_t)npw * cols, cudaMemcpyDeviceToDevice, s));
+        return LOBPCG_OK;
     }
     int copy64(z64 *dst, const z64 *src, int cols) {
         PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 2.0 * cbytes64(cols), false);
@@ -541,32 +557,29 @@ struct Solver {
         z64 *Xb = Z[cur], *HXb = HZ[cur];
         LG_TRY(copy64(Xb, col(X, j0), m));
         LG_TRY(copy64(HXb, col(HX, j0), m));
+        // Block start in FP64: the inner iterations take X_b as orthonormal, X_b^H H X_b as
+        // diagonal and X_b as orthogonal to the earlier blocks, and cannot repair an error there
+        // (the residual is projected off span(X_b)); FP32 products here would leave ~1e-7
+        // couplings and set a residual floor.  In early sweeps, far above that floor, the FP32
+        // copies and the tensor cores do it.
+        if (early) {
+            LG_TRY(block_start_early(b, Xb, HXb));
+        } else {
         if (b > 0) {
-            // X_b <- X_b - Y (Y^H X_b), H X_b likewise: small corrections, FP32 is enough
+            // X_b <- X_b - Y (Y^H X_b), H X_b <- H X_b - (H Y)(Y^H X_b), twice
             for (int rep = 0; rep < 2; ++rep) {
-                LG_TRY(cast<float, double>(m, Xb, X32));
-                LG_TRY(gemm_cn32(LOBPCG_PH_CONSTRAINT, j0, m, X32all, X32, G32, j0));
-                LG_TRY(gemm_nn32(LOBPCG_PH_CONSTRAINT, m, j0, 1.0f, X32all, G32, j0, 0.0f, nullptr, D32));
-                LG_TRY(cast<double, float>(m, D32, Tmp));
-                LG_TRY(gemm_nn64_axpy(Xb, Tmp, m));
-                LG_TRY(gemm_nn32(LOBPCG_PH_CONSTRAINT, m, j0, 1.0f, HX32all, G32, j0, 0.0f, nullptr, D32));
-                LG_TRY(cast<double, float>(m, D32, Tmp));
-                LG_TRY(gemm_nn64_axpy(HXb, Tmp, m));
+                LG_TRY(gemm_cn64(LOBPCG_PH_CONSTRAINT, j0, m, X, Xb, G, j0));
+                LG_TRY(gemm_nn64(LOBPCG_PH_CONSTRAINT, m, j0, -1.0, X, G, j0, 1.0, Xb, Xb));
+                LG_TRY(gemm_nn64(LOBPCG_PH_CONSTRAINT, m, j0, -1.0, HX, G, j0, 1.0, HXb, HXb));
             }
         }
-        // block Rayleigh-Ritz from FP32 Grams, solved in FP32; rotation in FP64
-        LG_TRY(cast<float, double>(m, Xb, X32));
-        LG_TRY(cast<float, double>(m, HXb, HX32));
-        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, X32, S32, m));
-        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, HX32, A32, m));
-        {
-            PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * m, cbytes64(2.0 * m), true);
-            LG_TRY(assemble_gram_mixed(m, 0, S32, m, A32, m, nullptr, S, A, s));
-            LG_TRY(diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s));
-        }
-        LG_TRY(rr(m, m, drop_tol32));
+        // Rayleigh-Ritz of the block alone (FP64 Grams), rotation in FP64
+        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Xb, Xb, S, m));
+        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Xb, HXb, A, m));
+        LG_TRY(rr(m, m, drop_tol));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, m, 0.0, nullptr, Z[1 - cur]));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, m, 0.0, nullptr, HZ[1 - cur]));
+        }
         cur = 1 - cur;
         trace("mixed-start", b, -1, Z[cur], HZ[cur], m);
         int nP = 0;
@@ -635,12 +648,42 @@ struct Solver {
         LG_TRY(cast<float, double>(m, col(X, b * m), col(X32all, b * m)));
         return cast<float, double>(m, col(HX, b * m), col(HX32all, b * m));
     }
+    // Early-sweep block start: constraint against the earlier blocks and the block's Rayleigh-Ritz
+    // from the FP32 copies (FP64 diagonals, FP64 eigensolve), rotation in FP64 into Z[1], HZ[1].
+    int block_start_early(int b, z64 *Xb, z64 *HXb) {
+        const int j0 = b * m;
+        if (b > 0) {
+            for (int rep = 0; rep < 2; ++rep) {
+                LG_TRY(cast<float, double>(m, Xb, X32));
+                LG_TRY(gemm_cn32(LOBPCG_PH_CONSTRAINT, j0, m, X32all, X32, G32, j0));
+                LG_TRY(gemm_nn32(LOBPCG_PH_CONSTRAINT, m, j0, 1.0f, X32all, G32, j0, 0.0f, nullptr, D32));
+                LG_TRY(cast<double, float>(m, D32, Tmp));
+                LG_TRY(gemm_nn64_axpy(Xb, Tmp, m));
+                LG_TRY(gemm_nn32(LOBPCG_PH_CONSTRAINT, m, j0, 1.0f, HX32all, G32, j0, 0.0f, nullptr, D32));
+                LG_TRY(cast<double, float>(m, D32, Tmp));
+                LG_TRY(gemm_nn64_axpy(HXb, Tmp, m));
+            }
+        }
+        LG_TRY(cast<float, double>(m, Xb, X32));
+        LG_TRY(cast<float, double>(m, HXb, HX32));
+        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, X32, S32, m));
+        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, m, m, X32, HX32, A32, m));
+        {
+            PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * m, cbytes64(2.0 * m), true);
+            LG_TRY(assemble_gram_mixed(m, 0, S32, m, A32, m, nullptr, S, A, s));
+            LG_TRY(diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s));
+        }
+        LG_TRY(rr(m, m, drop_tol32));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, m, 0.0, nullptr, Z[1]));
+        return gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, m, 0.0, nullptr, HZ[1]);
+    }
     int gemm_nn64_axpy(z64 *V, const z64 *D, int cols) {
         PhaseScope ps(prof, LOBPCG_PH_CONSTRAINT, 2.0 * npw * cols, 3.0 * cbytes64(cols), true);
         return axpy_cols(npw, cols, -1.0, D, npw, V, npw, s);
     }
     // Rayleigh-Ritz over all M bands closing a sweep (Sec. 3.2), then FP64 residuals.
     int final_rr(double *eig_h, double *res_h) {
+        if (early) return final_rr_early(eig_h, res_h);
         if (mixed) LG_TRY(applyH64(X, HX, M));  // FP64 H X for the residual test
         LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, X, S, M));
         LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, HX, A, M));
@@ -656,6 +699,39 @@ struct Solver {
         if (mixed) {
             LG_TRY(cast<float, double>(M, X, X32all));
             LG_TRY(cast<float, double>(M, HX, HX32all));
+        }
+        LG_CUDA_TRY(cudaMemcpyAsync(eig_h, theta, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+        LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+        LG_CUDA_TRY(cudaStreamSynchronize(s));
+        return LOBPCG_OK;
+    }
+    // The same step in an early sweep of the mixed schedule (residuals far above FP32
+    // resolution): Grams from the FP32 copies on the tensor cores with FP64 diagonals, FP64
+    // eigensolve, rotation of the FP32 copies, no FP64 H refresh (H X is the one the block
+    // iterations keep).  X and H X come out with FP32 accuracy, which the FP64 block starts of
+    // the later sweeps restore.
+    int final_rr_early(double *eig_h, double *res_h) {
+        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, M, M, X32all, X32all, S32, M));
+        LG_TRY(gemm_cn32(LOBPCG_PH_GRAM, M, M, X32all, HX32all, A32, M));
+        {
+            PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * M, cbytes64(2.0 * M), true);
+            LG_TRY(assemble_gram_mixed(M, 0, S32, M, A32, M, nullptr, S, A, s));
+            LG_TRY(diag_pencil(npw, M, X, npw, HX, npw, S, A, s));
+        }
+        LG_TRY(rr(M, M, drop_tol32));
+        {
+            PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * M * M, false);
+            LG_TRY(copy_cast<float, double>(M, M, C, M, C32, M, s));
+        }
+        LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, M, M, 1.0f, X32all, C32, M, 0.0f, nullptr, T32));
+        LG_TRY(cast<double, float>(M, T32, X));
+        LG_TRY(copy32(X32all, T32, M));
+        LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, M, M, 1.0f, HX32all, C32, M, 0.0f, nullptr, T32));
+        LG_TRY(cast<double, float>(M, T32, HX));
+        LG_TRY(copy32(HX32all, T32, M));
+        {
+            PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * M, cbytes64(2.0 * M), true);
+            LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
         }
         LG_CUDA_TRY(cudaMemcpyAsync(eig_h, theta, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
         LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
@@ -722,14 +798,12 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
         sv.X32 = carve<c32>(c, c->Z32, (size_t)npw * m, rc); LG_TRY(rc);
         sv.HX32 = carve<c32>(c, c->HZ32, (size_t)npw * m, rc); LG_TRY(rc);
         sv.D32 = carve<c32>(c, c->D32, (size_t)npw * m, rc); LG_TRY(rc);
-        c32 *sm = carve<c32>(c, c->Small32, 6 * (size_t)nzmax * nzmax + (size_t)M * m + nzmax, rc); LG_TRY(rc);
+        c32 *sm = carve<c32>(c, c->Small32, 3 * (size_t)nzmax * nzmax + (size_t)M * m, rc); LG_TRY(rc);
         sv.S32 = sm;
         sv.A32 = sm + (size_t)nzmax * nzmax;
         sv.C32 = sm + 2 * (size_t)nzmax * nzmax;
-        sv.S32p = sm + 3 * (size_t)nzmax * nzmax;
-        sv.A32p = sm + 4 * (size_t)nzmax * nzmax;
-        sv.G32 = sm + 5 * (size_t)nzmax * nzmax;
-        sv.theta32 = reinterpret_cast<float *>(sm + 5 * (size_t)nzmax * nzmax + (size_t)M * m);
+        sv.G32 = sm + 3 * (size_t)nzmax * nzmax;
+        sv.T32 = carve<c32>(c, c->T32, (size_t)npw * M, rc); LG_TRY(rc);
         // H X of the start vectors, and the FP32 copies the constraint uses
         LG_TRY(sv.applyH64(X, sv.HX, M));
         LG_TRY(sv.cast<float, double>(M, X, sv.X32all));
@@ -739,7 +813,9 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
     double maxr = 0.0;
     // residuals of the previous sweep choose each block's precision in a mixed solve
     std::vector<double> res_prev(M, HUGE_VAL);
+    double prev_max = HUGE_VAL;
     for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
+        sv.early = sv.mixed && c->opt.mixed_early > 0.0 && prev_max > c->opt.mixed_early;
         for (int b = 0; b < sv.nblk; ++b) {
             double rmin = HUGE_VAL;
             for (int i = b * m; i < (b + 1) * m; ++i) rmin = std::min(rmin, res_prev[i]);
@@ -762,10 +838,11 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
             maxr = std::max(maxr, res_h[i]);
         }
         if (sv.verbose >= 1) fprintf(stderr, "[lobpcg] k=%d sweep=%d max_resid=%.3e\n", k, sw, maxr);
-        if (sv.mixed) LG_TRY(tc_check_error());
+        LG_TRY(tc_check_error());
         if (!finite) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite Ritz value or residual");
         std::copy(res_h, res_h + M, res_prev.begin());
-        if (maxr <= c->opt.tol) break;
+        prev_max = maxr;
+        if (maxr <= c->opt.tol && !sv.early) break;
     }
     cnt.a64 += sv.applies64;
     cnt.a32 += sv.applies32;
@@ -785,6 +862,7 @@ int validate_options(const lobpcg_options &o) {
     if (o.gemm_split != 0 && o.gemm_split != 2 && o.gemm_split != 3)
         return fail(LOBPCG_ERR_ARG, "gemm_split must be 0, 2 or 3");
     if (!(o.mixed_switch >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_switch must be >= 0");
+    if (!(o.mixed_early >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_early must be >= 0");
     return LOBPCG_OK;
 }
 
@@ -807,7 +885,8 @@ int lobpcg_default_options(lobpcg_options *opt) {
     opt->mem_cap = 0;
     opt->timing = 0;
     opt->nbuf = 0;
-    opt->mixed_switch = 1e-6;
+    opt->mixed_switch = 0.0;
+    opt->mixed_early = 1e-3;
     return LOBPCG_OK;
 }
 
@@ -1104,7 +1183,7 @@ void lobpcg_destroy(lobpcg_ctx *ctx) {
                       &ctx->HZb[1], &ctx->Z32, &ctx->HZ32, &ctx->HXall, &ctx->Tmp, &ctx->Gram, &ctx->Gram2,
                       &ctx->Cbuf, &ctx->dtheta, &ctx->dres, &ctx->dwork, &ctx->Gc, &ctx->gw.part, &ctx->ew.buf,
                       &ctx->ew.ibuf, &ctx->ew.gw.part, &ctx->X32all, &ctx->HX32all, &ctx->Q32[0], &ctx->Q32[1],
-                      &ctx->HQ32[0], &ctx->HQ32[1], &ctx->D32, &ctx->Small32, &ctx->Xext};
+                      &ctx->HQ32[0], &ctx->HQ32[1], &ctx->D32, &ctx->Small32, &ctx->Xext, &ctx->T32};
     for (DevBuf *b : bufs) ctx->alloc.release(*b);
     delete ctx;
 }

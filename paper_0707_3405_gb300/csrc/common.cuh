@@ -230,7 +230,8 @@ int tc_gemm_cn(GemmWork &w, int m, int n, int K, float alpha, const c32 *A, int 
                float beta, c32 *C, int ldc, cudaStream_t s);
 int tc_gemm_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c32 *B, int ldb, float beta,
                const c32 *C, int ldc, c32 *D, int ldd, cudaStream_t s);
-int tc_check_error();   // LOBPCG_ERR_TIMEOUT if a tensor-core GEMM gave up waiting (clears the flag)
+int tc_check_error();   // LOBPCG_ERR_TIMEOUT if a bounded device wait ran out (clears the flag)
+int *device_wait_flag(); // device address of that flag (kernels with bounded waits set it)
 // FP32 GEMM engine, process-wide: 0 = auto / 2 = tensor cores (TF32x3) where the shape suits them,
 // 3 = CUDA cores only.
 void set_gemm_mode(int mode);

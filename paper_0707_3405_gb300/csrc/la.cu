@@ -245,12 +245,12 @@ struct Refl {
     cx<RT> scal;  // v[r] = x[r] * scal for r >= 1
 };
 
-template <typename RT>
+template <typename RT, bool CG = false>
 __device__ Refl<RT> make_reflector(const cx<RT> *__restrict__ col, int L, RT *sh) {
     RT s = 0.0;
-    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(col[r]);
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(CG ? ldcg_cx(col + r) : col[r]);
     s = block_sum(s, sh);
-    const cx<RT> alpha = col[0];
+    const cx<RT> alpha = CG ? ldcg_cx(col) : col[0];
     Refl<RT> R;
     if (s == 0.0 && alpha.y == 0.0) {
         R.tau = mkc<RT>(0.0, 0.0);
@@ -380,6 +380,117 @@ k_tri_step2(int n, int i, cx<RT> *__restrict__ A, int lda, const cx<RT> *__restr
     }
 }
 
+// Grid-wide barrier for co-resident blocks (cooperative launch): a monotone arrival
+// counter; block 0 thread 0 of every block waits for `target` arrivals.  Bounded: a
+// wait that runs out (or sees another block's failure) sets *err and the blocks leave.
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int target, int *err) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int ok = 0;
+        for (long long it = 0; it < (1LL << 22); ++it) {
+            if (*reinterpret_cast<volatile unsigned int *>(count) >= target) { ok = 1; break; }
+            if (*reinterpret_cast<volatile int *>(err)) break;
+        }
+        if (!ok) atomicExch(err, 1);
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Whole Householder tridiagonalisation in one cooperative launch (same arithmetic as
+// k_tri_step1 / k_tri_step2, same fixed summation order): per column, every block
+// forms the reflector, multiplies its 32 x 32 tiles of A22 by v, [barrier], sums the
+// partial products for all rows and forms w, updates its tiles, [barrier].  Data
+// written by other blocks is read through L2 (__ldcg).  Dynamic shared memory: v and w
+// (2 n complex).
+template <typename RT>
+__global__ void __launch_bounds__(256)
+k_tri_coop(int n, cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<RT> *__restrict__ taus,
+           RT *__restrict__ dg, RT *__restrict__ eg, cx<RT> *__restrict__ ypart, unsigned int *bar, int *err) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    cx<RT> *vsh = reinterpret_cast<cx<RT> *>(dsm);
+    cx<RT> *wsh = vsh + n;
+    __shared__ RT sh[32];
+    __shared__ cx<RT> acc[8][33];
+    const int tid = threadIdx.x, G = gridDim.x;
+    unsigned int arrivals = 0;
+    for (int i = 0; i + 1 < n; ++i) {
+        const int L = n - i - 1;
+        const int tl = (L + 31) / 32, ntiles = tl * tl;
+        const cx<RT> *col = A + (size_t)i * lda + i + 1;
+        const Refl<RT> R = make_reflector<RT, true>(col, L, sh);
+        for (int r = tid; r < L; r += blockDim.x) vsh[r] = (r == 0) ? mkc<RT>(1.0, 0.0) : ldcg_cx(col + r) * R.scal;
+        if (blockIdx.x == 0) {
+            for (int r = tid; r < L; r += blockDim.x) Hv[(size_t)i * n + i + 1 + r] = vsh[r];
+            if (tid == 0) {
+                taus[i] = R.tau;
+                dg[i] = ldcg_cx(A + (size_t)i * lda + i).x;
+                eg[i] = R.beta;
+            }
+        }
+        __syncthreads();
+        const cx<RT> *A22 = A + (size_t)(i + 1) * lda + i + 1;
+        const int rl = tid & 31, cg = tid >> 5;
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            const int tr = t % tl, tc = t / tl;
+            const int r = tr * 32 + rl;
+            cx<RT> sacc = mkc<RT>(0.0, 0.0);
+            if (r < L) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = tc * 32 + cg * 4 + q;
+                    if (c < L) sacc = sacc + ldcg_cx(A22 + (size_t)c * lda + r) * vsh[c];
+                }
+            }
+            acc[cg][rl] = sacc;
+            __syncthreads();
+            if (tid < 32) {
+                cx<RT> u = acc[0][tid];
+                for (int g = 1; g < 8; ++g) u = u + acc[g][tid];
+                const int rr = tr * 32 + tid;
+                if (rr < L) ypart[(size_t)tc * n + rr] = u;
+            }
+            __syncthreads();
+        }
+        arrivals += G;
+        if (!grid_barrier(bar, arrivals, err)) return;
+        // y = sum of the tile-column partials (fixed order), dot = v^H y, w = tau y - |tau|^2/2 (v^H y) v
+        RT dre = 0.0;
+        for (int rr = tid; rr < L; rr += blockDim.x) {
+            cx<RT> y = mkc<RT>(0.0, 0.0);
+            for (int c = 0; c < tl; ++c) y = y + ldcg_cx(ypart + (size_t)c * n + rr);
+            const cx<RT> v = vsh[rr];
+            dre += v.x * y.x + v.y * y.y;
+            wsh[rr] = y;
+        }
+        dre = block_sum(dre, sh);
+        const RT t2 = 0.5 * abs2(R.tau) * dre;
+        for (int rr = tid; rr < L; rr += blockDim.x) wsh[rr] = R.tau * wsh[rr] - t2 * vsh[rr];
+        __syncthreads();
+        // A22 -= w v^H + v w^H on this block's tiles
+        cx<RT> *A22w = A + (size_t)(i + 1) * lda + i + 1;
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            const int tr = t % tl, tc = t / tl;
+            for (int e = tid; e < 32 * 32; e += blockDim.x) {
+                const int r = tr * 32 + (e & 31), c = tc * 32 + (e >> 5);
+                if (r < L && c < L) {
+                    cx<RT> a = ldcg_cx(A22w + (size_t)c * lda + r);
+                    a = a - mul_conj(wsh[r], vsh[c]) - mul_conj(vsh[r], wsh[c]);
+                    A22w[(size_t)c * lda + r] = a;
+                }
+            }
+        }
+        arrivals += G;
+        if (!grid_barrier(bar, arrivals, err)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) dg[n - 1] = ldcg_cx(A + (size_t)(n - 1) * lda + n - 1).x;
+}
+
 template <typename RT>
 __global__ void k_tri_last(int n, const cx<RT> *__restrict__ A, int lda, RT *__restrict__ dg) {
     if (threadIdx.x == 0) dg[n - 1] = A[(size_t)(n - 1) * lda + n - 1].x;
@@ -422,38 +533,33 @@ __device__ void tri_bounds(const RT *__restrict__ d, const RT *__restrict__ e, i
     hi += pad;
 }
 
-// Four lanes per eigenvalue index k < m (eight eigenvalues per warp): each round
-// the group evaluates 4 Sturm counts inside the bracket and keeps the fifth of it
-// that holds eigenvalue k.  FP64 divisions are scarce on this GPU, so few lanes per
-// eigenvalue (less total work) beat wide multisection (fewer rounds).
-constexpr int kMsG = 4;
+// One warp per eigenvalue index k < m, one warp per block so that the m warps
+// spread over the SMs (the FP64 divisions of the Sturm counts are the cost, and
+// this GPU has few FP64 units per SM): each round the 32 lanes evaluate Sturm
+// counts at 32 points inside the bracket and keep the 1/33 of it that holds
+// eigenvalue k (about 5 bits per round).
+constexpr int kMsLanes = 32;
 template <typename RT>
-__global__ void k_multisect(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e,
-                            RT *__restrict__ theta) {
-    const int gid = (int)((blockIdx.x * blockDim.x + threadIdx.x) / kMsG);
-    const int sub = threadIdx.x & (kMsG - 1);
-    const int lane = threadIdx.x & 31;
-    const int base = lane & ~(kMsG - 1);
-    const bool active = gid < m;
-    const int k = active ? gid : m - 1;
+__global__ void __launch_bounds__(32)
+k_multisect(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, RT *__restrict__ theta) {
+    const int k = blockIdx.x;
+    const int sub = threadIdx.x;
+    if (k >= m) return;
     RT lo, hi, tnorm, pivmin;
     tri_bounds(d, e, n, lo, hi, tnorm, pivmin);
-    for (int it = 0; it < 48; ++it) {
+    for (int it = 0; it < 24; ++it) {
         const RT w = hi - lo;
-        const bool done = w <= 2.0 * Lim<RT>::eps() * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin;
-        if (__all_sync(0xffffffffu, done)) break;
-        const RT x = lo + w * (RT)(sub + 1) / (RT)(kMsG + 1);
-        const int c = done ? 0 : sturm_count(d, e, n, x, pivmin);
+        if (w <= 2.0 * Lim<RT>::eps() * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;  // warp-uniform
+        const RT x = lo + w * (RT)(sub + 1) / (RT)(kMsLanes + 1);
+        const int c = sturm_count(d, e, n, x, pivmin);
         const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
-        const int T = __popc((mask >> base) & ((1u << kMsG) - 1u)) - 1;  // counts are monotone in sub
-        const RT xlo = __shfl_sync(0xffffffffu, x, base + (T < 0 ? 0 : T));
-        const RT xhi = __shfl_sync(0xffffffffu, x, base + (T < kMsG - 1 ? T + 1 : kMsG - 1));
-        if (!done) {
-            if (T >= 0) lo = xlo;
-            if (T < kMsG - 1) hi = xhi;
-        }
+        const int T = __popc(mask) - 1;  // counts are monotone in sub: lanes 0..T have c <= k
+        const RT xlo = __shfl_sync(0xffffffffu, x, T < 0 ? 0 : T);
+        const RT xhi = __shfl_sync(0xffffffffu, x, T < kMsLanes - 1 ? T + 1 : kMsLanes - 1);
+        if (T >= 0) lo = xlo;
+        if (T < kMsLanes - 1) hi = xhi;
     }
-    if (active && sub == 0) theta[k] = 0.5 * (lo + hi);
+    if (sub == 0) theta[k] = 0.5 * (lo + hi);
 }
 
 // ------------------------------------------------------------------ eigenvectors (inverse iteration)
@@ -617,17 +723,42 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     unsigned int *cnt = reinterpret_cast<unsigned int *>(base + o_cnt);
     LG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n, s));
     LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(cx<RT>) * n, s));
-    for (int i = 0; i + 1 < n; ++i) {
-        const int L = n - i - 1;
-        const int tl = (L + 31) / 32;
-        k_tri_step1<RT><<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, taus, dg, eg, yp, wv, cnt);
-        LG_TRY(check_launch("tridiag step 1"));
-        k_tri_step2<RT><<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, wv);
-        LG_TRY(check_launch("tridiag step 2"));
+    bool coop_done = false;
+    if (n >= 2 && n <= 1024) {
+        // one cooperative launch; falls back to two launches per column if it cannot run
+        const int tl0 = (n - 1 + 31) / 32;
+        const size_t dsm = 2 * sizeof(cx<RT>) * (size_t)n;
+        int per_sm = 0, dev = 0, sms = 0, coop = 0;
+        LG_CUDA_TRY(cudaGetDevice(&dev));
+        LG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        LG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        if (dsm > 48 * 1024)
+            LG_CUDA_TRY(cudaFuncSetAttribute(k_tri_coop<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+        LG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_coop<RT>, 256, dsm));
+        const int G = std::min(tl0 * tl0, sms * std::max(per_sm, 0));
+        int *err = device_wait_flag();
+        if (coop && G >= 1 && err) {
+            unsigned int *bar = cnt;            // arrival counter (zeroed above)
+            void *args[] = {(void *)&n, (void *)&A, (void *)&lda, (void *)&Hv, (void *)&taus, (void *)&dg, (void *)&eg,
+                            (void *)&yp, (void *)&bar, (void *)&err};
+            LG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tri_coop<RT>, dim3(G), dim3(256), args, dsm, s));
+            LG_TRY(check_launch("tridiagonalisation (cooperative)"));
+            coop_done = true;
+        }
     }
-    k_tri_last<RT><<<1, 32, 0, s>>>(n, A, lda, dg);
-    LG_TRY(check_launch("tridiag last"));
-    k_multisect<RT><<<(m * kMsG + 255) / 256, 256, 0, s>>>(n, m, dg, eg, theta);
+    if (!coop_done) {
+        for (int i = 0; i + 1 < n; ++i) {
+            const int L = n - i - 1;
+            const int tl = (L + 31) / 32;
+            k_tri_step1<RT><<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, taus, dg, eg, yp, wv, cnt);
+            LG_TRY(check_launch("tridiag step 1"));
+            k_tri_step2<RT><<<dim3(tl, tl), 256, 0, s>>>(n, i, A, lda, Hv, wv);
+            LG_TRY(check_launch("tridiag step 2"));
+        }
+        k_tri_last<RT><<<1, 32, 0, s>>>(n, A, lda, dg);
+        LG_TRY(check_launch("tridiag last"));
+    }
+    k_multisect<RT><<<m, kMsLanes, 0, s>>>(n, m, dg, eg, theta);
     LG_TRY(check_launch("multisection"));
     k_inviter<RT><<<(m + 63) / 64, 64, 0, s>>>(n, m, dg, eg, theta, Z, sc, pv);
     LG_TRY(check_launch("inverse iteration"));

@@ -394,13 +394,27 @@ int tc_gemm_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c3
     return launch_nn<64>(M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s);
 }
 
+int *device_wait_flag() {
+    static int *p = nullptr;
+    if (!p) {
+        void *q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_tc_err) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p = static_cast<int *>(q);
+    }
+    return p;
+}
+
 int tc_check_error() {
     int h = 0;
     LG_CUDA_TRY(cudaMemcpyFromSymbol(&h, g_tc_err, sizeof(int)));
     if (h) {
         const int z = 0;
         LG_CUDA_TRY(cudaMemcpyToSymbol(g_tc_err, &z, sizeof(int)));
-        return fail(LOBPCG_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its MMAs");
+        return fail(LOBPCG_ERR_TIMEOUT,
+                    "a bounded device wait ran out (tensor-core GEMM mbarrier or tridiagonalisation grid barrier)");
     }
     return LOBPCG_OK;
 }
