@@ -566,8 +566,10 @@ struct Solver {
             LG_TRY(block_start_early(b, Xb, HXb));
         } else {
         if (b > 0) {
-            // X_b <- X_b - Y (Y^H X_b), H X_b <- H X_b - (H Y)(Y^H X_b), twice
-            for (int rep = 0; rep < 2; ++rep) {
+            // X_b <- X_b - Y (Y^H X_b), H X_b <- H X_b - (H Y)(Y^H X_b).  One pass: outside the
+            // early sweeps X_b already leaves the earlier blocks only at the FP32 level of the
+            // inner corrections (about 1e-7 of them), which a single FP64 projection removes.
+            for (int rep = 0; rep < 1; ++rep) {
                 LG_TRY(gemm_cn64(LOBPCG_PH_CONSTRAINT, j0, m, X, Xb, G, j0));
                 LG_TRY(gemm_nn64(LOBPCG_PH_CONSTRAINT, m, j0, -1.0, X, G, j0, 1.0, Xb, Xb));
                 LG_TRY(gemm_nn64(LOBPCG_PH_CONSTRAINT, m, j0, -1.0, HX, G, j0, 1.0, HXb, HXb));

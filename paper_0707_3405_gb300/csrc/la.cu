@@ -142,17 +142,19 @@ k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ 
         if (c < r && dflag[r]) T[r][c] = mkc<RT>(0.0, 0.0);
     }
     __syncthreads();
-    // inverse of the lower-triangular block, one column per thread
-    if (tid < kb) {
-        const int c = tid;
-        I[c][c] = mkc<RT>(1.0 / T[c][c].x, 0.0);  // real positive diagonal
-        for (int r = c + 1; r < kb; ++r) {
+    // inverse of the lower-triangular block (real positive diagonal), row by row:
+    // I[r][c] = -(1 / T[r][r]) sum_{l=c}^{r-1} T[r][l] I[l][c], thread c for column c
+    for (int r = 0; r < kb; ++r) {
+        if (tid < r) {
+            const int c = tid;
             cx<RT> s = mkc<RT>(0.0, 0.0);
             for (int l = c; l < r; ++l) s = s + T[r][l] * I[l][c];
             I[r][c] = (RT)(-1.0 / T[r][r].x) * s;
+        } else if (tid == r) {
+            I[r][r] = mkc<RT>(1.0 / T[r][r].x, 0.0);
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < kb * kb; e += blockDim.x) {
         const int r = e % kb, c = e / kb;
         L[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? T[r][c] : mkc<RT>(0.0, 0.0);
@@ -570,15 +572,21 @@ __device__ __forceinline__ RT hash_uniform(unsigned int a, unsigned int b) {
     return (RT)h * (2.0 / 4294967296.0) - 1.0;
 }
 
-// One thread per eigenvalue index; the thread whose eigenvalue starts a cluster
-// of close eigenvalues computes all vectors of that cluster, in order, on its own
-// (LU of T - lambda I with partial pivoting, three solves from a pseudo-random
-// start, each followed by modified Gram-Schmidt against the cluster's earlier
-// vectors and a normalisation).
+// One warp per eigenvalue index; the warp whose eigenvalue starts a cluster of
+// close eigenvalues computes all vectors of that cluster, in order: lane 0 runs the
+// LU of T - lambda I with partial pivoting and the solves (sequential recurrences,
+// kept in shared memory), from a pseudo-random start, three times; after each solve
+// the warp orthogonalises against the cluster's earlier vectors (modified
+// Gram-Schmidt) and normalises.  Dynamic shared memory: 5 n reals + n pivots.
 template <typename RT>
-__global__ void k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e,
-                          const RT *__restrict__ theta, RT *Z, RT *scratch, signed char *pivs) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32)
+k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, const RT *__restrict__ theta,
+          RT *Z) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    RT *dd = reinterpret_cast<RT *>(smraw);
+    RT *du = dd + n, *du2 = du + n, *dl = du2 + n, *z = dl + n;
+    signed char *pv = reinterpret_cast<signed char *>(z + n);
+    const int k = blockIdx.x, lane = threadIdx.x;
     if (k >= m) return;
     RT lo, hi, tnorm, pivmin;
     tri_bounds(d, e, n, lo, hi, tnorm, pivmin);
@@ -593,89 +601,99 @@ __global__ void k_inviter(int n, int m, const RT *__restrict__ d, const RT *__re
         RT lam = theta[j];
         if (j > k && lam < lam_prev + pert) lam = lam_prev + pert;
         lam_prev = lam;
-        RT *dd = scratch + (size_t)j * 5 * n;
-        RT *du = dd + n, *du2 = du + n, *dl = du2 + n;
-        RT *z = Z + (size_t)j * n;
-        signed char *pv = pivs + (size_t)j * n;
-        for (int i = 0; i < n; ++i) dd[i] = d[i] - lam;
-        for (int i = 0; i + 1 < n; ++i) { du[i] = e[i]; dl[i] = e[i]; du2[i] = 0.0; }
-        for (int i = 0; i + 1 < n; ++i) {
-            if (fabs(dd[i]) >= fabs(dl[i])) {
-                pv[i] = 0;
-                if (dd[i] == 0.0) dd[i] = pert;
-                const RT f = dl[i] / dd[i];
-                dl[i] = f;
-                dd[i + 1] -= f * du[i];
-            } else {
-                pv[i] = 1;
-                const RT f = dd[i] / dl[i];
-                dd[i] = dl[i];
-                dl[i] = f;
-                const RT t = du[i];
-                du[i] = dd[i + 1];
-                dd[i + 1] = t - f * dd[i + 1];
-                if (i + 2 < n) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
-            }
-        }
-        if (dd[n - 1] == 0.0) dd[n - 1] = pert;
-        for (int i = 0; i < n; ++i) z[i] = hash_uniform<RT>((unsigned)j, (unsigned)i);
-        for (int it = 0; it < 3; ++it) {
+        RT *zj = Z + (size_t)j * n;
+        if (lane == 0) {
+            for (int i = 0; i < n; ++i) dd[i] = d[i] - lam;
+            for (int i = 0; i + 1 < n; ++i) { du[i] = e[i]; dl[i] = e[i]; du2[i] = 0.0; }
             for (int i = 0; i + 1 < n; ++i) {
-                if (pv[i] == 0) {
-                    z[i + 1] -= dl[i] * z[i];
+                if (fabs(dd[i]) >= fabs(dl[i])) {
+                    pv[i] = 0;
+                    if (dd[i] == 0.0) dd[i] = pert;
+                    const RT f = dl[i] / dd[i];
+                    dl[i] = f;
+                    dd[i + 1] -= f * du[i];
                 } else {
-                    const RT t = z[i];
-                    z[i] = z[i + 1];
-                    z[i + 1] = t - dl[i] * z[i];
+                    pv[i] = 1;
+                    const RT f = dd[i] / dl[i];
+                    dd[i] = dl[i];
+                    dl[i] = f;
+                    const RT t = du[i];
+                    du[i] = dd[i + 1];
+                    dd[i + 1] = t - f * dd[i + 1];
+                    if (i + 2 < n) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
                 }
             }
-            z[n - 1] = z[n - 1] / dd[n - 1];
-            if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / dd[n - 2];
-            for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
+            if (dd[n - 1] == 0.0) dd[n - 1] = pert;
+        }
+        for (int i = lane; i < n; i += 32) z[i] = hash_uniform<RT>((unsigned)j, (unsigned)i);
+        __syncwarp();
+        for (int it = 0; it < 3; ++it) {
+            if (lane == 0) {
+                for (int i = 0; i + 1 < n; ++i) {
+                    if (pv[i] == 0) {
+                        z[i + 1] -= dl[i] * z[i];
+                    } else {
+                        const RT t = z[i];
+                        z[i] = z[i + 1];
+                        z[i + 1] = t - dl[i] * z[i];
+                    }
+                }
+                z[n - 1] = z[n - 1] / dd[n - 1];
+                if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / dd[n - 2];
+                for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
+            }
+            __syncwarp();
             for (int p = k; p < j; ++p) {
                 const RT *zp = Z + (size_t)p * n;
-                RT s = 0.0;
-                for (int i = 0; i < n; ++i) s += z[i] * zp[i];
-                for (int i = 0; i < n; ++i) z[i] -= s * zp[i];
+                RT sp = 0.0;
+                for (int i = lane; i < n; i += 32) sp += z[i] * zp[i];
+                sp = warp_sum(sp);
+                for (int i = lane; i < n; i += 32) z[i] -= sp * zp[i];
+                __syncwarp();
             }
             RT nr = 0.0;
-            for (int i = 0; i < n; ++i) nr += z[i] * z[i];
+            for (int i = lane; i < n; i += 32) nr += z[i] * z[i];
+            nr = warp_sum(nr);
             const RT inv = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
-            for (int i = 0; i < n; ++i) z[i] *= inv;
+            for (int i = lane; i < n; i += 32) z[i] *= inv;
+            __syncwarp();
         }
+        for (int i = lane; i < n; i += 32) zj[i] = z[i];
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------------ back-transformation
-// V[:, j] = H_0 H_1 ... H_{n-2} z_j (complex), one block per eigenvector.
+// V[:, j] = H_0 H_1 ... H_{n-2} z_j (complex), one warp per eigenvector (z in shared
+// memory, warp-shuffle dot products: no block-wide barrier per reflector).
 template <typename RT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32)
 k_backtransform(int n, int m, const cx<RT> *__restrict__ Hv, const cx<RT> *__restrict__ taus, const RT *__restrict__ Z,
                 cx<RT> *__restrict__ V, int ldv) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<RT> *z = reinterpret_cast<cx<RT> *>(smraw);
-    __shared__ RT sh[32], sh2[32];
-    const int j = blockIdx.x;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) z[r] = mkc<RT>(Z[(size_t)j * n + r], 0.0);
-    __syncthreads();
+    const int j = blockIdx.x, lane = threadIdx.x;
+    if (j >= m) return;
+    for (int r = lane; r < n; r += 32) z[r] = mkc<RT>(Z[(size_t)j * n + r], 0.0);
+    __syncwarp();
     for (int i = n - 2; i >= 0; --i) {
         const cx<RT> tau = taus[i];
         if (tau.x == 0.0 && tau.y == 0.0) continue;
         const int L = n - i - 1;
         const cx<RT> *v = Hv + (size_t)i * n + i + 1;
         RT sre = 0.0, sim = 0.0;
-        for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        for (int r = lane; r < L; r += 32) {
             const cx<RT> a = v[r], b = z[i + 1 + r];
             sre += a.x * b.x + a.y * b.y;
             sim += a.x * b.y - a.y * b.x;
         }
-        sre = block_sum(sre, sh);
-        sim = block_sum(sim, sh2);
+        sre = warp_sum(sre);
+        sim = warp_sum(sim);
         const cx<RT> ts = tau * mkc<RT>(sre, sim);
-        for (int r = threadIdx.x; r < L; r += blockDim.x) z[i + 1 + r] = z[i + 1 + r] - ts * v[r];
-        __syncthreads();
+        for (int r = lane; r < L; r += 32) z[i + 1 + r] = z[i + 1 + r] - ts * v[r];
+        __syncwarp();
     }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) V[(size_t)j * ldv + r] = z[r];
+    for (int r = lane; r < n; r += 32) V[(size_t)j * ldv + r] = z[r];
 }
 
 template <typename RT>
@@ -706,8 +724,6 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     const size_t o_yp = take(sizeof(cx<RT>) * (size_t)nt * n);
     const size_t o_wv = take(sizeof(cx<RT>) * n);
     const size_t o_z = take(sizeof(RT) * (size_t)n * m);
-    const size_t o_sc = take(sizeof(RT) * 5 * (size_t)n * m);
-    const size_t o_pv = take((size_t)n * m);
     const size_t o_cnt = take(sizeof(unsigned int) * n);
     LG_TRY(w.alloc->ensure(w.buf, off));
     char *base = reinterpret_cast<char *>(w.buf.p);
@@ -718,8 +734,6 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     cx<RT> *yp = reinterpret_cast<cx<RT> *>(base + o_yp);
     cx<RT> *wv = reinterpret_cast<cx<RT> *>(base + o_wv);
     RT *Z = reinterpret_cast<RT *>(base + o_z);
-    RT *sc = reinterpret_cast<RT *>(base + o_sc);
-    signed char *pv = reinterpret_cast<signed char *>(base + o_pv);
     unsigned int *cnt = reinterpret_cast<unsigned int *>(base + o_cnt);
     LG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n, s));
     LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(cx<RT>) * n, s));
@@ -760,13 +774,16 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     }
     k_multisect<RT><<<m, kMsLanes, 0, s>>>(n, m, dg, eg, theta);
     LG_TRY(check_launch("multisection"));
-    k_inviter<RT><<<(m + 63) / 64, 64, 0, s>>>(n, m, dg, eg, theta, Z, sc, pv);
+    const size_t smem_ii = 5 * sizeof(RT) * (size_t)n + (size_t)n;
+    if (smem_ii > 48 * 1024)
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_inviter<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ii));
+    k_inviter<RT><<<m, 32, smem_ii, s>>>(n, m, dg, eg, theta, Z);
     LG_TRY(check_launch("inverse iteration"));
     const size_t smem = sizeof(cx<RT>) * (size_t)n;
     if (smem > 48 * 1024) {
         LG_CUDA_TRY(cudaFuncSetAttribute(k_backtransform<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    k_backtransform<RT><<<m, 256, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
+    k_backtransform<RT><<<m, 32, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
     return check_launch("back-transform");
 }
 
