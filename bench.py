@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the warm-up and timed steps of --mode, no other legs")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "apply"],
-                    help="with --ncu: time LOBPCG sweeps or standalone apply_H on all bands")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply"],
+                    help="with --ncu: LOBPCG sweeps, full solves to --tol, or standalone apply_H on all bands")
     return ap.parse_args()
 
 
@@ -69,7 +69,10 @@ def ncu_run(args):
     import __graft_entry__
     __graft_entry__.build()
     w = make(args.workload)
-    s = solver_for(w, args.precision, timing=False, max_sweeps=1, tol=1e-30, nbuf=args.nbuf)
+    if args.mode == "solve":
+        s = solver_for(w, args.precision, timing=False, max_sweeps=args.max_sweeps, tol=args.tol, nbuf=args.nbuf)
+    else:
+        s = solver_for(w, args.precision, timing=False, max_sweeps=1, tol=1e-30, nbuf=args.nbuf)
     X = start_block(w, s)
     if args.mode == "apply" and args.precision == "mixed":
         X = X.to(torch.complex64)
@@ -77,8 +80,8 @@ def ncu_run(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.warmup + args.steps):
-        if args.mode == "sweep":
-            s.solve([X])
+        if args.mode in ("sweep", "solve"):
+            s.solve([X.clone()] if args.mode == "solve" else [X])
         else:
             s.apply_H(0, X, Y)
     torch.cuda.synchronize()

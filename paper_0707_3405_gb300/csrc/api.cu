@@ -626,11 +626,19 @@ struct Solver {
             c32 *Qn = Q32[1 - cur], *HQn = HQ32[1 - cur];
             LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, nw, 1.0f, W32, C32 + m, nz, 0.0f, nullptr, col(Qn, 2 * m)));
             LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, nw, 1.0f, HW32, C32 + m, nz, 0.0f, nullptr, col(HQn, 2 * m)));
-            // X = X Delta + P, H X = H X Delta + H P (FP64)
-            LG_TRY(cast<double, float>(m, col(Qn, 2 * m), Tmp));
-            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, nz, 1.0, Tmp, Z[1 - cur]));
-            LG_TRY(cast<double, float>(m, col(HQn, 2 * m), Tmp));
-            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, nz, 1.0, Tmp, HZ[1 - cur]));
+            // X = X Delta + P, H X = H X Delta + H P: FP64, or, in an early sweep (where X and H X
+            // carry FP32 accuracy), from the FP32 copies on the tensor cores
+            if (early) {
+                LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, X32, C32, nz, 1.0f, col(Qn, 2 * m), D32));
+                LG_TRY(cast<double, float>(m, D32, Z[1 - cur]));
+                LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, HX32, C32, nz, 1.0f, col(HQn, 2 * m), D32));
+                LG_TRY(cast<double, float>(m, D32, HZ[1 - cur]));
+            } else {
+                LG_TRY(cast<double, float>(m, col(Qn, 2 * m), Tmp));
+                LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, nz, 1.0, Tmp, Z[1 - cur]));
+                LG_TRY(cast<double, float>(m, col(HQn, 2 * m), Tmp));
+                LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, nz, 1.0, Tmp, HZ[1 - cur]));
+            }
             cur = 1 - cur;
             nP = 1;
             ++iterations;
@@ -651,7 +659,8 @@ struct Solver {
         return cast<float, double>(m, col(HX, b * m), col(HX32all, b * m));
     }
     // Early-sweep block start: constraint against the earlier blocks and the block's Rayleigh-Ritz
-    // from the FP32 copies (FP64 diagonals, FP64 eigensolve), rotation in FP64 into Z[1], HZ[1].
+    // from the FP32 copies (FP64 diagonals, FP64 eigensolve), rotation of the FP32 copies into
+    // Z[1], HZ[1].
     int block_start_early(int b, z64 *Xb, z64 *HXb) {
         const int j0 = b * m;
         if (b > 0) {
@@ -676,8 +685,14 @@ struct Solver {
             LG_TRY(diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s));
         }
         LG_TRY(rr(m, m, drop_tol32));
-        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, m, 0.0, nullptr, Z[1]));
-        return gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, m, 0.0, nullptr, HZ[1]);
+        {
+            PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * m * m, false);
+            LG_TRY(copy_cast<float, double>(m, m, C, m, C32, m, s));
+        }
+        LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, X32, C32, m, 0.0f, nullptr, D32));
+        LG_TRY(cast<double, float>(m, D32, Z[1]));
+        LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, HX32, C32, m, 0.0f, nullptr, D32));
+        return cast<double, float>(m, D32, HZ[1]);
     }
     int gemm_nn64_axpy(z64 *V, const z64 *D, int cols) {
         PhaseScope ps(prof, LOBPCG_PH_CONSTRAINT, 2.0 * npw * cols, 3.0 * cbytes64(cols), true);
