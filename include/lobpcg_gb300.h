@@ -96,8 +96,8 @@ typedef struct {
     int    gemm_split;   /* complex64 GEMM engine: 0 = auto (= 2), 2 = tensor cores with 3xTF32 split
                             operands for long reductions and tall products, 3 = CUDA cores only;
                             1 (BF16x3) is not built: ERR_UNSUPPORTED */
-    int    use_graph;    /* 1: replay block iterations as CUDA graphs */
-    int    autotune;     /* 1: time kernel variants once per shape and keep the fastest */
+    int    use_graph;    /* reserved (accepted, no effect yet) */
+    int    autotune;     /* reserved (accepted, no effect yet) */
     double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */
     long long mem_cap;   /* 0: no cap; else maximum bytes the handle may allocate (ERR_OOM above it) */
     int    timing;       /* 1: time each phase of lobpcg_solve with CUDA events on the handle's stream */
