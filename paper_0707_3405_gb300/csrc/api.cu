@@ -698,6 +698,19 @@ struct Solver {
         PhaseScope ps(prof, LOBPCG_PH_CONSTRAINT, 2.0 * npw * cols, 3.0 * cbytes64(cols), true);
         return axpy_cols(npw, cols, -1.0, D, npw, V, npw, s);
     }
+    // Ritz values and residuals to the host.  The all-band Rayleigh-Ritz step must keep all M
+    // directions: a dropped one means the bands lost linear independence (breakdown).
+    int fetch_results(double *eig_h, double *res_h) {
+        int nd_h = 0;
+        LG_CUDA_TRY(cudaMemcpyAsync(eig_h, theta, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+        LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+        LG_CUDA_TRY(cudaMemcpyAsync(&nd_h, ndrop, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (nd_h > 0)
+            return fail(LOBPCG_ERR_BREAKDOWN, "the bands lost linear independence (" + std::to_string(nd_h) +
+                                                  " dropped in the all-band Rayleigh-Ritz step)");
+        return LOBPCG_OK;
+    }
     // Rayleigh-Ritz over all M bands closing a sweep (Sec. 3.2), then FP64 residuals.
     int final_rr(double *eig_h, double *res_h) {
         if (early) return final_rr_early(eig_h, res_h);
@@ -717,10 +730,7 @@ struct Solver {
             LG_TRY(cast<float, double>(M, X, X32all));
             LG_TRY(cast<float, double>(M, HX, HX32all));
         }
-        LG_CUDA_TRY(cudaMemcpyAsync(eig_h, theta, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
-        LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
-        LG_CUDA_TRY(cudaStreamSynchronize(s));
-        return LOBPCG_OK;
+        return fetch_results(eig_h, res_h);
     }
     // The same step in an early sweep of the mixed schedule (residuals far above FP32
     // resolution): Grams from the FP32 copies on the tensor cores with FP64 diagonals, FP64
@@ -750,10 +760,7 @@ struct Solver {
             PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * M, cbytes64(2.0 * M), true);
             LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
         }
-        LG_CUDA_TRY(cudaMemcpyAsync(eig_h, theta, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
-        LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
-        LG_CUDA_TRY(cudaStreamSynchronize(s));
-        return LOBPCG_OK;
+        return fetch_results(eig_h, res_h);
     }
 };
 
@@ -832,7 +839,12 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
     std::vector<double> res_prev(M, HUGE_VAL);
     double prev_max = HUGE_VAL;
     for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
+        const bool was_early = sv.early;
         sv.early = sv.mixed && c->opt.mixed_early > 0.0 && prev_max > c->opt.mixed_early;
+        // First full sweep after early ones: H X carries the FP32 noise of the early sweeps
+        // (~1e-7 |H|), which dominates the residuals of well converged bands and makes their W
+        // nearly parallel; recompute it in FP64 from X first.
+        if (was_early && !sv.early) LG_TRY(sv.applyH64(X, sv.HX, M));
         for (int b = 0; b < sv.nblk; ++b) {
             double rmin = HUGE_VAL;
             for (int i = b * m; i < (b + 1) * m; ++i) rmin = std::min(rmin, res_prev[i]);
