@@ -160,3 +160,29 @@ def test_solve_with_buffer_bands(precision):
         res = s.solve([X])
         assert res.status == 0
         _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
+
+
+def test_mixed_early_sweeps_block128_gamma120():
+    """Mixed schedule with early sweeps on the 120^3 Gamma cell (113081 plane waves,
+    432 KB projectors), 256 bands in blocks of 128 plus 128 buffer bands.  Regression:
+    the first full sweep after the early ones must start from an FP64 H X (with the
+    early sweeps' FP32 noise in H X, the W of converged bands became nearly parallel
+    and the Rayleigh-Ritz step produced a spurious Ritz value).  Converged residuals
+    are re-checked with the oracle's own H on sampled bands."""
+    import torch
+    w = synth.make_workload("gamma120")
+    with make_solver(w, block_size=128, nline=4, max_sweeps=12, precision="mixed", tol=1e-8, nbuf=128) as s:
+        X = _start(w, s, M=256)
+        res = s.solve([X])
+        assert res.status == 0, res.stats
+        assert res.stats["sweeps"] <= 8
+        assert res.resid[0].max() <= 1e-8
+        assert np.all(np.diff(res.eig[0]) >= -1e-12)
+        G = (X.conj() @ X.T).cpu().numpy()
+        assert np.abs(G - np.eye(256)).max() < 1e-10
+        H = oracle_for(w, s)
+        pick = np.array([0, 1, 63, 127, 128, 200, 254, 255])
+        Xn = X[torch.as_tensor(pick, device=X.device)].cpu().numpy().T
+        r = checks.residuals(H, Xn, res.eig[0][pick])
+        assert r.max() <= 1e-8, r.max()
+        assert np.abs(res.resid[0][pick] - r).max() < 1e-9
