@@ -494,7 +494,7 @@ k_tri_coop(int n, cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<R
 }
 
 // Fused single-launch tridiagonalisation: one grid barrier per column.
-// Block g owns the 32 x 32 tiles t = g, g + G, ... of the matrix (row-major tile index) and keeps
+// Block g owns the TS x TS tiles t = g, g + G, ... of the matrix (row-major tile index) and keeps
 // them in shared memory for the whole factorisation.  Invariant at the top of column i (after a
 // barrier): ypart[i & 1] holds, per tile column, the partial products A^(i)[J,J] v_i
 // (J = i+1..n-1, A^(i) = the matrix after reflectors 0..i-1), and colbuf[i & 1] holds column
@@ -505,32 +505,35 @@ k_tri_coop(int n, cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<R
 //   (c) each owned tile: A -= w_i v_i^H + v_i w_i^H on J x J and, in the same pass, the partial
 //       product with v_{i+1} on J' x J' (J' = i+2..n-1) -> ypart[(i+1) & 1];
 //   (d) owners of column i+2 publish it (rows i+2..) -> colbuf[(i+1) & 1];  barrier.
-// Same formulas as k_tri_step1 / k_tri_step2.  Dynamic shared memory: the owned tiles, then
+// Same formulas as k_tri_step1 / k_tri_step2.  Small tiles spread the FP64 work of a column
+// over more SMs (this GPU has few FP64 units per SM).  256 threads: TS rows x (256 / TS)
+// column groups of CPT = TS*TS/256 columns.  Dynamic shared memory: the owned tiles, then
 // v_i, w_i, v_{i+1} and the working column (n complex each).
-template <typename RT>
+template <typename RT, int TS>
 __global__ void __launch_bounds__(256)
 k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<RT> *__restrict__ taus,
             RT *__restrict__ dg, RT *__restrict__ eg, cx<RT> *__restrict__ ypart, cx<RT> *__restrict__ colbuf,
             unsigned int *bar, int *err) {
+    constexpr int TT = TS * TS, NG = 256 / TS, CPT = TT / 256;
     extern __shared__ __align__(16) unsigned char dsm[];
-    const int T = (n + 31) / 32, G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+    const int T = (n + TS - 1) / TS, G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const int nown = (T * T - g + G - 1) / G;  // tiles g, g+G, ... below T*T
-    cx<RT> *tiles = reinterpret_cast<cx<RT> *>(dsm);  // nown x [32 cols][32 rows]
-    cx<RT> *v = tiles + (size_t)nown * 1024;           // v_i on [0, n)
+    cx<RT> *tiles = reinterpret_cast<cx<RT> *>(dsm);  // nown x [TS cols][TS rows]
+    cx<RT> *v = tiles + (size_t)nown * TT;             // v_i on [0, n)
     cx<RT> *w = v + n;                                  // w_i
     cx<RT> *vn = w + n;                                 // v_{i+1}
     cx<RT> *x = vn + n;                                 // working column
     __shared__ RT sh[32];
-    __shared__ cx<RT> acc[8][33];
-    const int rl = tid & 31, cg = tid >> 5;
+    __shared__ cx<RT> acc[NG][TS + 1];
+    const int rl = tid % TS, cg = tid / TS;
     const cx<RT> zero = mkc<RT>(0.0, 0.0);
     unsigned int arrivals = 0;
     // load the owned tiles (entries outside the matrix are zero)
     for (int q = 0; q < nown; ++q) {
         const int t = g + q * G, TR = t / T, TC = t % T;
-        for (int e = tid; e < 1024; e += blockDim.x) {
-            const int r = TR * 32 + (e & 31), c = TC * 32 + (e >> 5);
-            tiles[(size_t)q * 1024 + e] = (r < n && c < n) ? A[(size_t)c * lda + r] : zero;
+        for (int e = tid; e < TT; e += blockDim.x) {
+            const int r = TR * TS + (e % TS), c = TC * TS + (e / TS);
+            tiles[(size_t)q * TT + e] = (r < n && c < n) ? A[(size_t)c * lda + r] : zero;
         }
     }
     // reflector 0 from column 0 (read from A, unmodified), d[0]
@@ -542,25 +545,22 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
     // partial products A^(0)[J,J] v_0 and column 1 of A^(0)
     for (int q = 0; q < nown; ++q) {
         const int t = g + q * G, TR = t / T, TC = t % T;
-        const cx<RT> *tl = tiles + (size_t)q * 1024;
-        const int r = TR * 32 + rl;
+        const cx<RT> *tl = tiles + (size_t)q * TT;
+        const int r = TR * TS + rl;
         cx<RT> sacc = zero;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int cl = cg * 4 + k, c = TC * 32 + cl;
-            if (r >= 1 && r < n && c >= 1 && c < n) sacc = sacc + tl[cl * 32 + rl] * v[c];
+        for (int k = 0; k < CPT; ++k) {
+            const int cl = cg * CPT + k, c = TC * TS + cl;
+            if (r >= 1 && r < n && c >= 1 && c < n) sacc = sacc + tl[cl * TS + rl] * v[c];
         }
         acc[cg][rl] = sacc;
         __syncthreads();
-        if (tid < 32) {
+        if (tid < TS) {
             cx<RT> u = acc[0][tid];
-            for (int k = 1; k < 8; ++k) u = u + acc[k][tid];
-            const int rr = TR * 32 + tid;
+            for (int k = 1; k < NG; ++k) u = u + acc[k][tid];
+            const int rr = TR * TS + tid;
             if (rr < n) ypart[(size_t)TC * n + rr] = u;
-        }
-        if (n > 1 && TC == 1 / 32 && tid < 32) {
-            const int rr = TR * 32 + tid;
-            if (rr >= 1 && rr < n) colbuf[rr] = tl[(1 % 32) * 32 + tid];
+            if (n > 1 && TC == 1 / TS && rr >= 1 && rr < n) colbuf[rr] = tl[(1 % TS) * TS + tid];
         }
         __syncthreads();
     }
@@ -571,11 +571,9 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
         const int par = i & 1;
         const cx<RT> *yp = ypart + (size_t)par * T * n;
         const cx<RT> *cb = colbuf + (size_t)par * n;
-        // (a) y_i and w_i on J = [i+1, n)
+        // (a) y_i and w_i on J = [i+1, n); loads issued in groups of 8 before they are summed
         RT dre = 0.0;
         for (int r = i + 1 + tid; r < n; r += blockDim.x) {
-            // loads issued in groups of 8 before they are summed (in order), so the
-            // L2 round trips overlap instead of following one another
             cx<RT> y = zero;
             for (int c = 0; c < T; c += 8) {
                 cx<RT> t8[8];
@@ -616,42 +614,39 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
         const int c2 = i + 2;
         for (int q = 0; q < nown; ++q) {
             const int t = g + q * G, TR = t / T, TC = t % T;
-            if (TR * 32 + 31 < i + 1 || TC * 32 + 31 < i + 1) continue;  // tile outside J x J (uniform)
-            cx<RT> *tl = tiles + (size_t)q * 1024;
-            const int r = TR * 32 + rl;
+            cx<RT> *tl = tiles + (size_t)q * TT;
+            if (TR * TS + TS - 1 < i + 1 || TC * TS + TS - 1 < i + 1) {
+                // tile outside J x J: its share of y_{i+1} is zero (uniform branch)
+                if (tid < TS) {
+                    const int rr = TR * TS + tid;
+                    if (rr < n) ypn[(size_t)TC * n + rr] = zero;
+                }
+                continue;
+            }
+            const int r = TR * TS + rl;
             const bool rin = r >= i + 1 && r < n;
             const cx<RT> wr = rin ? w[r] : zero, vr = rin ? v[r] : zero;
             cx<RT> sacc = zero;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int cl = cg * 4 + k, c = TC * 32 + cl;
+            for (int k = 0; k < CPT; ++k) {
+                const int cl = cg * CPT + k, c = TC * TS + cl;
                 if (rin && c >= i + 1 && c < n) {
-                    cx<RT> a = tl[cl * 32 + rl];
+                    cx<RT> a = tl[cl * TS + rl];
                     a = a - mul_conj(wr, v[c]) - mul_conj(vr, w[c]);
-                    tl[cl * 32 + rl] = a;
+                    tl[cl * TS + rl] = a;
                     if (r >= c2 && c >= c2) sacc = sacc + a * vn[c];
                 }
             }
             acc[cg][rl] = sacc;
             __syncthreads();
-            if (tid < 32) {
+            if (tid < TS) {
                 cx<RT> u = acc[0][tid];
-                for (int k = 1; k < 8; ++k) u = u + acc[k][tid];
-                const int rr = TR * 32 + tid;
+                for (int k = 1; k < NG; ++k) u = u + acc[k][tid];
+                const int rr = TR * TS + tid;
                 if (rr < n) ypn[(size_t)TC * n + rr] = u;
-                if (TC == c2 / 32 && rr >= c2 && rr < n) cbn[rr] = tl[(c2 % 32) * 32 + tid];
+                if (TC == c2 / TS && rr >= c2 && rr < n) cbn[rr] = tl[(c2 % TS) * TS + tid];
             }
             __syncthreads();
-        }
-        // tiles of tile-columns entirely left of J' still own rows of ypart that (a) will sum:
-        // their contribution is zero, written by the owners above only when active -> zero the rest
-        for (int q = 0; q < nown; ++q) {
-            const int t = g + q * G, TR = t / T, TC = t % T;
-            if (!(TR * 32 + 31 < i + 1 || TC * 32 + 31 < i + 1)) continue;
-            if (tid < 32) {
-                const int rr = TR * 32 + tid;
-                if (rr < n) ypn[(size_t)TC * n + rr] = zero;
-            }
         }
         R = Rn;
         for (int r = tid; r < n; r += blockDim.x) v[r] = vn[r];
@@ -888,7 +883,7 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     const size_t o_tau = take(sizeof(cx<RT>) * n);
     const size_t o_d = take(sizeof(RT) * n);
     const size_t o_e = take(sizeof(RT) * n);
-    const size_t o_yp = take(sizeof(cx<RT>) * 2 * (size_t)nt * n);
+    const size_t o_yp = take(sizeof(cx<RT>) * 2 * (size_t)((n + 15) / 16) * n);
     const size_t o_wv = take(sizeof(cx<RT>) * 2 * (size_t)n);
     const size_t o_z = take(sizeof(RT) * (size_t)n * m);
     const size_t o_cnt = take(sizeof(unsigned int) * n);
@@ -906,28 +901,32 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(cx<RT>) * n, s));
     bool coop_done = false;
     if (n >= 2) {
-        // fused version: tiles resident in shared memory, one grid barrier per column
-        const int T = (n + 31) / 32;
+        // fused version: tiles resident in shared memory, one grid barrier per column; 16 x 16
+        // tiles for small matrices (more SMs share a column's FP64 work), else 32 x 32
         int dev = 0, sms = 0, coop = 0, smem_max = 0;
         LG_CUDA_TRY(cudaGetDevice(&dev));
         LG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         LG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         LG_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const bool small_tiles = n <= 256;
+        const int TS = small_tiles ? 16 : 32;
+        const int T = (n + TS - 1) / TS;
         const int G = std::min(T * T, sms);
         const int nown = (T * T + G - 1) / G;
-        const size_t dsm = sizeof(cx<RT>) * ((size_t)nown * 1024 + 4 * (size_t)n);
-        const size_t static_sm = sizeof(RT) * 32 + sizeof(cx<RT>) * 8 * 33 + 64;
+        const size_t dsm = sizeof(cx<RT>) * ((size_t)nown * TS * TS + 4 * (size_t)n);
+        const size_t static_sm = sizeof(RT) * 32 + sizeof(cx<RT>) * 16 * 33 + 64;
         int *err = device_wait_flag();
+        const void *fn = small_tiles ? (const void *)k_tri_fused<RT, 16> : (const void *)k_tri_fused<RT, 32>;
         if (coop && err && dsm + static_sm <= (size_t)smem_max) {
-            LG_CUDA_TRY(cudaFuncSetAttribute(k_tri_fused<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+            LG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
             int per_sm = 0;
-            LG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_fused<RT>, 256, dsm));
+            LG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, dsm));
             if (per_sm >= 1 && G <= sms * per_sm) {
                 unsigned int *bar = cnt;
                 const cx<RT> *Ac = A;
                 void *args[] = {(void *)&n, (void *)&Ac, (void *)&lda, (void *)&Hv, (void *)&taus, (void *)&dg,
                                 (void *)&eg, (void *)&yp, (void *)&wv, (void *)&bar, (void *)&err};
-                LG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tri_fused<RT>, dim3(G), dim3(256), args, dsm, s));
+                LG_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(256), args, dsm, s));
                 LG_TRY(check_launch("tridiagonalisation (fused cooperative)"));
                 coop_done = true;
             }
