@@ -7,6 +7,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -99,7 +100,7 @@ Prof::~Prof() {
 int Allocator::alloc(void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return LOBPCG_OK;
-    if (cap > 0 && used + (long long)bytes > cap)
+    if (cap > 0 && used.load() + (long long)bytes > cap)
         return fail(LOBPCG_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes exceeds the memory cap");
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
@@ -152,6 +153,35 @@ struct KPoint {
     bool has_beta = false;
 };
 
+// Everything one k-point solve (or one apply_H call) writes: scratch, solver buffers and the
+// stream it runs on.  Lane 0 runs on the handle's stream; a multi-k solve adds lanes with their
+// own streams so that k-points proceed concurrently.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevBuf T2, nlB, stageX, stageY;
+    GemmWork gw;
+    EigWork ew;
+    DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
+    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32;
+    void bind(Allocator *a, CoopGate *g, int share) {
+        gw.alloc = a;
+        ew.alloc = a;
+        ew.gw.alloc = a;
+        ew.gate = g;
+        ew.coop_share = share;
+    }
+    void release(Allocator &a) {
+        DevBuf *bufs[] = {&T2, &nlB, &stageX, &stageY, &Zb[0], &Zb[1], &HZb[0], &HZb[1], &Z32, &HZ32, &HXall,
+                          &Tmp, &Gram, &Gram2, &Cbuf, &dtheta, &dres, &dwork, &Gc, &gw.part, &ew.buf, &ew.ibuf,
+                          &ew.gw.part, &X32all, &HX32all, &Q32[0], &Q32[1], &HQ32[0], &HQ32[1], &D32, &Small32,
+                          &Xext, &T32};
+        for (DevBuf *b : bufs) a.release(*b);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+    }
+};
+
 }  // namespace
 
 struct lobpcg_ctx {
@@ -171,12 +201,9 @@ struct lobpcg_ctx {
     double *E64 = nullptr;
     float *E32 = nullptr;
     size_t fft_budget = (size_t)128 << 20;
-    DevBuf T2, nlB, stageX, stageY;
-    GemmWork gw;
-    EigWork ew;
-    // solver buffers
-    DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
-    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32;
+    int device = 0;
+    std::vector<std::unique_ptr<Lane>> lanes;  // lanes[0]: the handle's stream
+    CoopGate gate;
     std::string err;
 };
 
@@ -304,7 +331,8 @@ template <> struct Tables<float> {
 // Y = H X on device buffers (Sec. 2.2 items iii and iv): FFT route for
 // T + V_loc, then the KB projection B = beta^H X, B <- E B, Y += beta B.
 template <typename R>
-int apply_H_dev(lobpcg_ctx *c, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb, Prof *prof = nullptr) {
+int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
+                Prof *prof = nullptr) {
     if (nb <= 0) return LOBPCG_OK;
     KPoint &K = c->kp[k];
     const FFTGeom &g = K.geom;
@@ -313,7 +341,7 @@ int apply_H_dev(lobpcg_ctx *c, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy
     const size_t per_band = cb * (size_t)g.Px * g.N * g.N;
     int nbatch = (int)std::max<size_t>(1, c->fft_budget / per_band);
     nbatch = std::min(std::min(nbatch, nb), 65535);
-    LG_TRY(c->alloc.ensure(c->T2, per_band * nbatch));
+    LG_TRY(c->alloc.ensure(L.T2, per_band * nbatch));
     {
         // algorithmic DRAM bytes: sphere X read twice (scatter, kinetic), Y written,
         // kinetic table, half-box written / read-written / read (4 Px N^2), V once per batch
@@ -321,19 +349,19 @@ int apply_H_dev(lobpcg_ctx *c, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy
                           std::ceil((double)nb / nbatch) * sizeof(R) * (double)g.N * g.N * g.N;
         PhaseScope ps(prof, LOBPCG_PH_FFT, nb * fft_flops_per_band(g), by, f64);
         LG_TRY(fft_vloc_apply<R>(g, c->plan, X, ldx, Y, ldy, nb, Tables<R>::kin(K), Tables<R>::vt(c),
-                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(c->T2.p), nbatch, c->stream));
+                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(L.T2.p), nbatch, L.stream));
     }
     if (c->nproj > 0) {
         if (!K.has_beta) return fail(LOBPCG_ERR_ARG, "projectors of this k-point were not given");
-        LG_TRY(c->alloc.ensure(c->nlB, cb * (size_t)c->nproj * nb));
-        cx<R> *B = reinterpret_cast<cx<R> *>(c->nlB.p);
+        LG_TRY(c->alloc.ensure(L.nlB, cb * (size_t)c->nproj * nb));
+        cx<R> *B = reinterpret_cast<cx<R> *>(L.nlB.p);
         const cx<R> *beta = Tables<R>::beta(K);
         const double fl = 16.0 * K.npw * (double)c->nproj * nb;
         const double by = cb * (2.0 * K.npw * c->nproj + 3.0 * K.npw * nb);
         PhaseScope ps(prof, LOBPCG_PH_NONLOCAL, fl, by, f64);
-        LG_TRY(gemm_cn<R>(c->gw, c->nproj, nb, K.npw, (R)1, beta, K.npw, X, ldx, (R)0, B, c->nproj, c->stream));
-        LG_TRY(scale_rows<R>(c->nproj, nb, Tables<R>::E(c), B, c->nproj, c->stream));
-        LG_TRY(gemm_nn<R>(K.npw, nb, c->nproj, (R)1, beta, K.npw, B, c->nproj, (R)1, Y, ldy, Y, ldy, c->stream));
+        LG_TRY(gemm_cn<R>(L.gw, c->nproj, nb, K.npw, (R)1, beta, K.npw, X, ldx, (R)0, B, c->nproj, L.stream));
+        LG_TRY(scale_rows<R>(c->nproj, nb, Tables<R>::E(c), B, c->nproj, L.stream));
+        LG_TRY(gemm_nn<R>(K.npw, nb, c->nproj, (R)1, beta, K.npw, B, c->nproj, (R)1, Y, ldy, Y, ldy, L.stream));
     }
     return LOBPCG_OK;
 }
@@ -377,6 +405,7 @@ bool is_device_ptr(const void *p) {
 //     only ever declared after a full (non-early) sweep.
 struct Solver {
     lobpcg_ctx *c;
+    Lane *L = nullptr;
     Prof *prof;
     int k, npw, M, m, nblk;
     bool mixed;
@@ -426,17 +455,17 @@ struct Solver {
 
     int applyH64(const z64 *Xin, z64 *Yout, int nb) {
         applies64 += nb;
-        return apply_H_dev<double>(c, k, Xin, npw, Yout, npw, nb, prof);
+        return apply_H_dev<double>(c, *L, k, Xin, npw, Yout, npw, nb, prof);
     }
     int applyH32(const c32 *Xin, c32 *Yout, int nb) {
         applies32 += nb;
-        return apply_H_dev<float>(c, k, Xin, npw, Yout, npw, nb, prof);
+        return apply_H_dev<float>(c, *L, k, Xin, npw, Yout, npw, nb, prof);
     }
 
     // ---------------------------------------------------------- FP64 helpers
     int gemm_cn64(int ph, int mm, int nn, const z64 *Aa, const z64 *Bb, z64 *Cc, int ldc) {
         PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes64(mm + nn), true);
-        return gemm_cn<double>(c->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
+        return gemm_cn<double>(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
     }
     int gemm_nn64(int ph, int nn, int kk, double alpha, const z64 *Aa, const z64 *Bb, int ldb, double beta,
                   const z64 *Cc, z64 *Dd) {
@@ -445,7 +474,7 @@ struct Solver {
     }
     int gemm_cn32(int ph, int mm, int nn, const c32 *Aa, const c32 *Bb, c32 *Cc, int ldc) {
         PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes32(mm + nn), false);
-        return gemm_cn<float>(c->gw, mm, nn, npw, 1.0f, Aa, npw, Bb, npw, 0.0f, Cc, ldc, s);
+        return gemm_cn<float>(L->gw, mm, nn, npw, 1.0f, Aa, npw, Bb, npw, 0.0f, Cc, ldc, s);
     }
     int gemm_nn32(int ph, int nn, int kk, float alpha, const c32 *Aa, const c32 *Bb, int ldb, float beta,
                   const c32 *Cc, c32 *Dd) {
@@ -458,7 +487,7 @@ struct Solver {
     int rr(int nz, int mm, double tol) {
         const double n3 = (double)nz * nz * nz;
         PhaseScope ps(prof, LOBPCG_PH_RR, 8.0 * (3.0 * n3 + 2.0 * nz * (double)nz * mm), 0.0, true);
-        return rayleigh_ritz(c->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s);
+        return rayleigh_ritz(L->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s);
     }
     template <typename Ro, typename Ri>
     int cast(int cols, const cx<Ri> *a, cx<Ro> *b) {
@@ -777,10 +806,11 @@ struct SolveCounters {
 };
 
 // Solve one k-point for M bands of which the first Mreq must converge (the rest are buffer bands).
-int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h, int &sweeps_done,
+int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h, int &sweeps_done,
             Prof *prof, SolveCounters &cnt) {
     Solver sv;
     sv.c = c;
+    sv.L = &L;
     sv.prof = prof;
     sv.k = k;
     sv.npw = c->kp[k].npw;
@@ -789,7 +819,7 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
     sv.nblk = M / sv.m;
     sv.mixed = c->opt.precision == LOBPCG_MIXED;
     sv.X = X;
-    sv.s = c->stream;
+    sv.s = L.stream;
     sv.drop_tol = 1e-12;
     sv.drop_tol32 = 1e-3;
     if (const char *v = std::getenv("LOBPCG_VERBOSE")) sv.verbose = std::atoi(v);
@@ -798,36 +828,36 @@ int solve_k(lobpcg_ctx *c, int k, int M, int Mreq, z64 *X, double *eig_h, double
     int rc = 0;
     const int zcols = 3 * m;   // a mixed solve visits converged blocks in FP64
     for (int i = 0; i < 2; ++i) {
-        sv.Z[i] = carve<z64>(c, c->Zb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
-        sv.HZ[i] = carve<z64>(c, c->HZb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
+        sv.Z[i] = carve<z64>(c, L.Zb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
+        sv.HZ[i] = carve<z64>(c, L.HZb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
     }
-    sv.HX = carve<z64>(c, c->HXall, (size_t)npw * M, rc); LG_TRY(rc);
-    sv.Tmp = carve<z64>(c, c->Tmp, (size_t)npw * M, rc); LG_TRY(rc);
-    sv.S = carve<z64>(c, c->Gram, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
-    sv.A = carve<z64>(c, c->Gram2, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
-    sv.C = carve<z64>(c, c->Cbuf, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
-    sv.G = carve<z64>(c, c->Gc, (size_t)M * m, rc); LG_TRY(rc);
-    sv.theta = carve<double>(c, c->dtheta, nzmax, rc); LG_TRY(rc);
-    sv.res = carve<double>(c, c->dres, nzmax, rc); LG_TRY(rc);
-    double *w = carve<double>(c, c->dwork, 4 * (size_t)nzmax + 64, rc); LG_TRY(rc);
+    sv.HX = carve<z64>(c, L.HXall, (size_t)npw * M, rc); LG_TRY(rc);
+    sv.Tmp = carve<z64>(c, L.Tmp, (size_t)npw * M, rc); LG_TRY(rc);
+    sv.S = carve<z64>(c, L.Gram, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
+    sv.A = carve<z64>(c, L.Gram2, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
+    sv.C = carve<z64>(c, L.Cbuf, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
+    sv.G = carve<z64>(c, L.Gc, (size_t)M * m, rc); LG_TRY(rc);
+    sv.theta = carve<double>(c, L.dtheta, nzmax, rc); LG_TRY(rc);
+    sv.res = carve<double>(c, L.dres, nzmax, rc); LG_TRY(rc);
+    double *w = carve<double>(c, L.dwork, 4 * (size_t)nzmax + 64, rc); LG_TRY(rc);
     sv.work = w;
     sv.ndrop = reinterpret_cast<int *>(w + 4 * (size_t)nzmax);
     if (sv.mixed) {
-        sv.X32all = carve<c32>(c, c->X32all, (size_t)npw * M, rc); LG_TRY(rc);
-        sv.HX32all = carve<c32>(c, c->HX32all, (size_t)npw * M, rc); LG_TRY(rc);
+        sv.X32all = carve<c32>(c, L.X32all, (size_t)npw * M, rc); LG_TRY(rc);
+        sv.HX32all = carve<c32>(c, L.HX32all, (size_t)npw * M, rc); LG_TRY(rc);
         for (int i = 0; i < 2; ++i) {
-            sv.Q32[i] = carve<c32>(c, c->Q32[i], (size_t)npw * 3 * m, rc); LG_TRY(rc);
-            sv.HQ32[i] = carve<c32>(c, c->HQ32[i], (size_t)npw * 3 * m, rc); LG_TRY(rc);
+            sv.Q32[i] = carve<c32>(c, L.Q32[i], (size_t)npw * 3 * m, rc); LG_TRY(rc);
+            sv.HQ32[i] = carve<c32>(c, L.HQ32[i], (size_t)npw * 3 * m, rc); LG_TRY(rc);
         }
-        sv.X32 = carve<c32>(c, c->Z32, (size_t)npw * m, rc); LG_TRY(rc);
-        sv.HX32 = carve<c32>(c, c->HZ32, (size_t)npw * m, rc); LG_TRY(rc);
-        sv.D32 = carve<c32>(c, c->D32, (size_t)npw * m, rc); LG_TRY(rc);
-        c32 *sm = carve<c32>(c, c->Small32, 3 * (size_t)nzmax * nzmax + (size_t)M * m, rc); LG_TRY(rc);
+        sv.X32 = carve<c32>(c, L.Z32, (size_t)npw * m, rc); LG_TRY(rc);
+        sv.HX32 = carve<c32>(c, L.HZ32, (size_t)npw * m, rc); LG_TRY(rc);
+        sv.D32 = carve<c32>(c, L.D32, (size_t)npw * m, rc); LG_TRY(rc);
+        c32 *sm = carve<c32>(c, L.Small32, 3 * (size_t)nzmax * nzmax + (size_t)M * m, rc); LG_TRY(rc);
         sv.S32 = sm;
         sv.A32 = sm + (size_t)nzmax * nzmax;
         sv.C32 = sm + 2 * (size_t)nzmax * nzmax;
         sv.G32 = sm + 3 * (size_t)nzmax * nzmax;
-        sv.T32 = carve<c32>(c, c->T32, (size_t)npw * M, rc); LG_TRY(rc);
+        sv.T32 = carve<c32>(c, L.T32, (size_t)npw * M, rc); LG_TRY(rc);
         // H X of the start vectors, and the FP32 copies the constraint uses
         LG_TRY(sv.applyH64(X, sv.HX, M));
         LG_TRY(sv.cast<float, double>(M, X, sv.X32all));
@@ -972,9 +1002,11 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
         }
         LG_TRY(build_basis(c, c->kp[k]));
     }
-    c->gw.alloc = &c->alloc;
-    c->ew.alloc = &c->alloc;
-    c->ew.gw.alloc = &c->alloc;
+    LG_CUDA_TRY(cudaGetDevice(&c->device));
+    LG_CUDA_TRY(cudaEventCreateWithFlags(&c->gate.ev, cudaEventDisableTiming));
+    c->lanes.emplace_back(new Lane());
+    c->lanes[0]->stream = c->stream;
+    c->lanes[0]->bind(&c->alloc, nullptr, 1);
     if (beta && nproj > 0) {
         for (int k = 0; k < nk; ++k)
             if (beta[k]) LG_TRY(set_beta(c, k, beta[k]));
@@ -1015,6 +1047,7 @@ int lobpcg_set_projectors(lobpcg_ctx *ctx, int k, const void *beta_k) {
 int lobpcg_set_stream(lobpcg_ctx *ctx, void *stream) {
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (!ctx->lanes.empty()) ctx->lanes[0]->stream = ctx->stream;
     return LOBPCG_OK;
 }
 
@@ -1078,19 +1111,20 @@ static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int 
     const bool dx = is_device_ptr(X), dy = is_device_ptr(Y);
     const void *Xd = X;
     void *Yd = Y;
+    Lane &L = *c->lanes[0];
     if (!dx) {
-        LG_TRY(c->alloc.ensure(c->stageX, bytes));
-        LG_CUDA_TRY(cudaMemcpyAsync(c->stageX.p, X, bytes, cudaMemcpyHostToDevice, c->stream));
-        Xd = c->stageX.p;
+        LG_TRY(c->alloc.ensure(L.stageX, bytes));
+        LG_CUDA_TRY(cudaMemcpyAsync(L.stageX.p, X, bytes, cudaMemcpyHostToDevice, c->stream));
+        Xd = L.stageX.p;
     }
     if (!dy) {
-        LG_TRY(c->alloc.ensure(c->stageY, bytes));
-        Yd = c->stageY.p;
+        LG_TRY(c->alloc.ensure(L.stageY, bytes));
+        Yd = L.stageY.p;
     }
     if (precision == LOBPCG_C128)
-        LG_TRY(apply_H_dev<double>(c, k, static_cast<const z64 *>(Xd), npw, static_cast<z64 *>(Yd), npw, nb));
+        LG_TRY(apply_H_dev<double>(c, L, k, static_cast<const z64 *>(Xd), npw, static_cast<z64 *>(Yd), npw, nb));
     else
-        LG_TRY(apply_H_dev<float>(c, k, static_cast<const c32 *>(Xd), npw, static_cast<c32 *>(Yd), npw, nb));
+        LG_TRY(apply_H_dev<float>(c, L, k, static_cast<const c32 *>(Xd), npw, static_cast<c32 *>(Yd), npw, nb));
     if (!dy) {
         LG_CUDA_TRY(cudaMemcpyAsync(Y, Yd, bytes, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -1102,6 +1136,46 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
     set_gemm_mode(ctx->opt.gemm_split);
     return ret(ctx, apply_impl(ctx, k, X, Y, nb, precision));
+}
+
+// Concurrent k-point lanes of one solve (k-points are independent, Sec. 5.2).
+constexpr int kMaxLanes = 4;
+
+// One k-point on one lane: stage host vectors, add buffer bands, solve, copy back.
+static int solve_one(lobpcg_ctx *c, Lane &L, int k, int M, int nbuf, void *Xk, double *eig_k, double *res_k,
+                     int &sw, Prof *prof, SolveCounters &cnt) {
+    const bool host = !is_device_ptr(Xk);
+    const int npw = c->kp[k].npw;
+    const size_t bytes = sizeof(z64) * (size_t)npw * M;
+    z64 *Xd = static_cast<z64 *>(Xk);
+    if (host) {
+        LG_TRY(c->alloc.ensure(L.stageX, bytes));
+        Xd = static_cast<z64 *>(L.stageX.p);
+        LG_CUDA_TRY(cudaMemcpyAsync(Xd, Xk, bytes, cudaMemcpyHostToDevice, L.stream));
+    }
+    int rc;
+    if (nbuf > 0) {
+        // buffer bands: an internal block of M + nbuf columns, the extra ones pseudo-random
+        LG_TRY(c->alloc.ensure(L.Xext, sizeof(z64) * (size_t)npw * (M + nbuf)));
+        z64 *Xe = static_cast<z64 *>(L.Xext.p);
+        LG_CUDA_TRY(cudaMemcpyAsync(Xe, Xd, bytes, cudaMemcpyDeviceToDevice, L.stream));
+        LG_TRY(fill_random(npw, nbuf, Xe + (size_t)npw * M, npw, 0x51ED270Bu + 977u * (unsigned)k, L.stream));
+        std::vector<double> ebuf(2 * (size_t)(M + nbuf));
+        rc = solve_k(c, L, k, M + nbuf, M, Xe, ebuf.data(), ebuf.data() + (M + nbuf), sw, prof, cnt);
+        if (rc < 0) return rc;
+        LG_CUDA_TRY(cudaMemcpyAsync(Xd, Xe, bytes, cudaMemcpyDeviceToDevice, L.stream));
+        LG_CUDA_TRY(cudaStreamSynchronize(L.stream));
+        std::memcpy(eig_k, ebuf.data(), sizeof(double) * M);
+        std::memcpy(res_k, ebuf.data() + (M + nbuf), sizeof(double) * M);
+    } else {
+        rc = solve_k(c, L, k, M, M, Xd, eig_k, res_k, sw, prof, cnt);
+        if (rc < 0) return rc;
+    }
+    if (host) {
+        LG_CUDA_TRY(cudaMemcpyAsync(Xk, Xd, bytes, cudaMemcpyDeviceToHost, L.stream));
+        LG_CUDA_TRY(cudaStreamSynchronize(L.stream));
+    }
+    return rc;
 }
 
 static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double *resid, lobpcg_stats *st) {
@@ -1117,55 +1191,71 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
     }
     const auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launch_count();
-    int worst = LOBPCG_OK, sweeps = 0;
-    SolveCounters cnt;
-    double maxr = 0.0;
-    Prof prof;
-    prof.on = c->opt.timing != 0;
     const int nbuf = c->opt.nbuf > 0 ? ((c->opt.nbuf + m - 1) / m) * m : 0;
-    std::vector<double> ebuf;
-    prof.s = c->stream;
+    // lanes: lane 0 is the handle's stream; more lanes (own streams) for a multi-k solve
+    const int nl = std::max(1, std::min(c->nk, kMaxLanes));
+    while ((int)c->lanes.size() < nl) {
+        std::unique_ptr<Lane> L(new Lane());
+        LG_CUDA_TRY(cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking));
+        L->own_stream = true;
+        c->lanes.push_back(std::move(L));
+    }
+    for (int l = 0; l < nl; ++l) c->lanes[l]->bind(&c->alloc, nl > 1 ? &c->gate : nullptr, nl);
+    c->lanes[0]->stream = c->stream;
+    c->gate.used = false;
+    if (nl > 1) {
+        // the other lanes start after the work already queued on the handle's stream
+        LG_CUDA_TRY(cudaEventRecord(c->gate.ev, c->stream));
+        for (int l = 1; l < nl; ++l) LG_CUDA_TRY(cudaStreamWaitEvent(c->lanes[l]->stream, c->gate.ev, 0));
+    }
+    std::vector<Prof> profs(nl);
+    std::vector<SolveCounters> cnts(nl);
+    std::vector<int> sweeps_k(c->nk, 0), rc_k(c->nk, LOBPCG_OK);
+    std::vector<int> lane_rc(nl, LOBPCG_OK);
+    std::vector<std::string> lane_err(nl);
+    auto run_lane = [&](int l) {
+        if (l > 0) cudaSetDevice(c->device);
+        Prof &pr = profs[l];
+        pr.on = c->opt.timing != 0;
+        pr.s = c->lanes[l]->stream;
+        for (int k = l; k < c->nk; k += nl) {
+            const int rc = solve_one(c, *c->lanes[l], k, M, nbuf, X[k], eig + (size_t)k * M, resid + (size_t)k * M,
+                                     sweeps_k[k], pr.on ? &pr : nullptr, cnts[l]);
+            if (rc < 0) {
+                lane_rc[l] = rc;
+                lane_err[l] = last_fail();
+                return;
+            }
+            rc_k[k] = rc;
+        }
+        pr.collect();
+    };
+    if (nl == 1) {
+        run_lane(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int l = 1; l < nl; ++l) th.emplace_back(run_lane, l);
+        run_lane(0);
+        for (auto &t : th) t.join();
+        for (int l = 1; l < nl; ++l) LG_CUDA_TRY(cudaStreamSynchronize(c->lanes[l]->stream));
+    }
+    for (int l = 0; l < nl; ++l)
+        if (lane_rc[l] < 0) return fail(lane_rc[l], lane_err[l]);
+    int worst = LOBPCG_OK, sweeps = 0;
+    double maxr = 0.0;
+    SolveCounters cnt;
+    for (int l = 0; l < nl; ++l) {
+        cnt.a64 += cnts[l].a64;
+        cnt.a32 += cnts[l].a32;
+        cnt.visits32 += cnts[l].visits32;
+        cnt.visits64 += cnts[l].visits64;
+        cnt.iters += cnts[l].iters;
+    }
     for (int k = 0; k < c->nk; ++k) {
-        int sw = 0;
-        // host start vectors are staged through a device buffer and copied back
-        const bool host = !is_device_ptr(X[k]);
-        const size_t bytes = sizeof(z64) * (size_t)c->kp[k].npw * M;
-        z64 *Xd = static_cast<z64 *>(X[k]);
-        if (host) {
-            LG_TRY(c->alloc.ensure(c->stageX, bytes));
-            Xd = static_cast<z64 *>(c->stageX.p);
-            LG_CUDA_TRY(cudaMemcpyAsync(Xd, X[k], bytes, cudaMemcpyHostToDevice, c->stream));
-        }
-        // buffer bands: an internal block of M + nbuf columns, the extra ones pseudo-random
-        int rc;
-        if (nbuf > 0) {
-            const int npw = c->kp[k].npw;
-            LG_TRY(c->alloc.ensure(c->Xext, sizeof(z64) * (size_t)npw * (M + nbuf)));
-            z64 *Xe = static_cast<z64 *>(c->Xext.p);
-            LG_CUDA_TRY(cudaMemcpyAsync(Xe, Xd, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            LG_TRY(fill_random(npw, nbuf, Xe + (size_t)npw * M, npw, 0x51ED270Bu + 977u * (unsigned)k, c->stream));
-            ebuf.resize(2 * (size_t)(M + nbuf));
-            rc = solve_k(c, k, M + nbuf, M, Xe, ebuf.data(), ebuf.data() + (M + nbuf), sw, prof.on ? &prof : nullptr,
-                         cnt);
-            if (rc < 0) return rc;
-            LG_CUDA_TRY(cudaMemcpyAsync(Xd, Xe, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            LG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-            std::memcpy(eig + (size_t)k * M, ebuf.data(), sizeof(double) * M);
-            std::memcpy(resid + (size_t)k * M, ebuf.data() + (M + nbuf), sizeof(double) * M);
-        } else {
-            rc = solve_k(c, k, M, M, Xd, eig + (size_t)k * M, resid + (size_t)k * M, sw, prof.on ? &prof : nullptr,
-                         cnt);
-            if (rc < 0) return rc;
-        }
-        if (host) {
-            LG_CUDA_TRY(cudaMemcpyAsync(X[k], Xd, bytes, cudaMemcpyDeviceToHost, c->stream));
-            LG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        }
-        if (rc == LOBPCG_NOT_CONVERGED) worst = rc;
-        sweeps = std::max(sweeps, sw);
+        if (rc_k[k] == LOBPCG_NOT_CONVERGED) worst = LOBPCG_NOT_CONVERGED;
+        sweeps = std::max(sweeps, sweeps_k[k]);
         for (int i = 0; i < M; ++i) maxr = std::max(maxr, resid[(size_t)k * M + i]);
     }
-    prof.collect();
     if (st) {
         std::memset(st, 0, sizeof(*st));
         st->sweeps = sweeps;
@@ -1178,15 +1268,17 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         st->block_visits_fp32 = cnt.visits32;
         st->block_visits_fp64 = cnt.visits64;
         st->kernel_launches = launch_count() - l0;
-        for (int p = 0; p < LOBPCG_PH_COUNT; ++p) {
-            st->ph_ms[p] = prof.ms[p];
-            st->ph_flops[p] = prof.flops[p];
-            st->ph_bytes[p] = prof.bytes[p];
-            st->ph_calls[p] = prof.calls[p];
-            st->ph_fp64_flops[p] = prof.fp64_flops[p];
-            st->ph_ms_fp64[p] = prof.ms64[p];
-            st->ph_bytes_fp64[p] = prof.bytes64[p];
-        }
+        for (int l = 0; l < nl; ++l)
+            for (int p = 0; p < LOBPCG_PH_COUNT; ++p) {
+                const Prof &pr = profs[l];
+                st->ph_ms[p] += pr.ms[p];
+                st->ph_flops[p] += pr.flops[p];
+                st->ph_bytes[p] += pr.bytes[p];
+                st->ph_calls[p] += pr.calls[p];
+                st->ph_fp64_flops[p] += pr.fp64_flops[p];
+                st->ph_ms_fp64[p] += pr.ms64[p];
+                st->ph_bytes_fp64[p] += pr.bytes64[p];
+            }
     }
     return worst;
 }
@@ -1207,13 +1299,12 @@ const char *lobpcg_last_error(const lobpcg_ctx *ctx) {
 void lobpcg_destroy(lobpcg_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    for (auto &L : ctx->lanes) {
+        if (L->stream) cudaStreamSynchronize(L->stream);
+        L->release(ctx->alloc);
+    }
     for (auto &b : ctx->owned) ctx->alloc.release(b);
-    DevBuf *bufs[] = {&ctx->T2, &ctx->nlB, &ctx->stageX, &ctx->stageY, &ctx->Zb[0], &ctx->Zb[1], &ctx->HZb[0],
-                      &ctx->HZb[1], &ctx->Z32, &ctx->HZ32, &ctx->HXall, &ctx->Tmp, &ctx->Gram, &ctx->Gram2,
-                      &ctx->Cbuf, &ctx->dtheta, &ctx->dres, &ctx->dwork, &ctx->Gc, &ctx->gw.part, &ctx->ew.buf,
-                      &ctx->ew.ibuf, &ctx->ew.gw.part, &ctx->X32all, &ctx->HX32all, &ctx->Q32[0], &ctx->Q32[1],
-                      &ctx->HQ32[0], &ctx->HQ32[1], &ctx->D32, &ctx->Small32, &ctx->Xext, &ctx->T32};
-    for (DevBuf *b : bufs) ctx->alloc.release(*b);
+    if (ctx->gate.ev) cudaEventDestroy(ctx->gate.ev);
     delete ctx;
 }
 

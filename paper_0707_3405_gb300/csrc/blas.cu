@@ -142,11 +142,13 @@ __global__ void k_reduce_parts(int m, int n, int nsplit, R alpha, const z64 *__r
 }
 
 int num_sms() {
-    static int v = 0;
+    static std::atomic<int> cached{0};
+    int v = cached.load();
     if (!v) {
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 132;
+        cached.store(v);
     }
     return v;
 }

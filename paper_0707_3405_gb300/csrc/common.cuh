@@ -3,6 +3,9 @@
 // float2 / double2 and with numpy complex64 / complex128.
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -140,7 +143,7 @@ struct DevBuf {
 // Allocation accounting with an optional cap (lobpcg_options.mem_cap).
 struct Allocator {
     long long cap = 0;
-    long long used = 0;
+    std::atomic<long long> used{0};  // concurrent k-point lanes allocate from one allocator
     int alloc(void **p, size_t bytes);
     void free(void *p, size_t bytes);
     // Make `b` at least `bytes` large (contents are not preserved).
@@ -249,11 +252,20 @@ int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alp
                 const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s);
 
 // ------------------------------------------------------------------ dense FP64 eigen-solvers
+// Orders the cooperative launches (grid-barrier kernels) of concurrent streams one after
+// another, so that two such grids never compete for residency.
+struct CoopGate {
+    std::mutex mu;
+    cudaEvent_t ev = nullptr;
+    bool used = false;
+};
 struct EigWork {
     Allocator *alloc = nullptr;
     DevBuf buf;      // generic workspace
     DevBuf ibuf;     // integer workspace
     GemmWork gw;
+    CoopGate *gate = nullptr;  // set when several streams may run Rayleigh-Ritz steps at once
+    int coop_share = 1;        // >1: cooperative grids use at most 1/coop_share of the resident blocks
 };
 // Rayleigh-Ritz: lowest m pairs of A c = theta S c (n x n, ld n). See lobpcg_k_rayleigh_ritz.
 int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,

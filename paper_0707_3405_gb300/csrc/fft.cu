@@ -335,12 +335,14 @@ size_t smem_ac(const FFTGeom &g, int zc) {
 }
 
 int max_dyn_smem() {
-    static int v = -1;
+    static std::atomic<int> cached{-1};
+    int v = cached.load();
     if (v < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
             v = 48 * 1024;
+        cached.store(v);
     }
     return v;
 }
@@ -387,13 +389,13 @@ int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
     const size_t sm_ac = smem_ac<R>(g, zc);
     const int yc = 16;
     const size_t sm_b = sizeof(cx<R>) * ((size_t)N + (size_t)yc * (N + 1));
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load()) {
         const int lim = max_dyn_smem();
         LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_a<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_b<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_c<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        attr_set = true;
+        attr_set.store(true);
     }
     const int ny0m = ((g.ny0 % N) + N) % N;
     const int nx0m = ((g.nx0 % N) + N) % N;

@@ -482,12 +482,21 @@ int run_reg(const FFTGeom &g, const C *X, int ldx, C *Y, int ldy, int nb, const 
     constexpr int LPW = 32 / RP<N>::T;
     constexpr int NZC = (N + LPW - 1) / LPW;
     const size_t sm = tile_bytes(N, g.Py);
-    // the attribute is a maximum: raise it when a larger sphere comes
-    static size_t sm_set = 0;
-    if (sm > sm_set) {
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_ra<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_rc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        sm_set = sm;
+    // dynamic shared-memory ceiling: the device maximum, set once (process-wide attribute)
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        int dev = 0, smem_max = 0;
+        LG_CUDA_TRY(cudaGetDevice(&dev));
+        LG_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (sm > (size_t)smem_max) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plane tile exceeds shared memory");
+        cudaFuncAttributes fa, fc;
+        LG_CUDA_TRY(cudaFuncGetAttributes(&fa, k_ra<N>));
+        LG_CUDA_TRY(cudaFuncGetAttributes(&fc, k_rc<N>));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_ra<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_max - (int)fa.sharedSizeBytes));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_rc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_max - (int)fc.sharedSizeBytes));
+        attr.store(true);
     }
     const int ny0m = ((g.ny0 % N) + N) % N;
     const int nx0m = ((g.nx0 % N) + N) % N;

@@ -871,6 +871,20 @@ size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Raise a kernel's dynamic shared-memory ceiling to the device maximum.  The attribute is
+// process-wide, so it is never lowered: launches of different sizes on concurrent streams
+// then never see a ceiling below their own request.
+int allow_max_dyn_smem(const void *fn) {
+    int dev = 0, smem_max = 0;
+    LG_CUDA_TRY(cudaGetDevice(&dev));
+    LG_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    LG_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    LG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem_max - (int)fa.sharedSizeBytes));
+    return LOBPCG_OK;
+}
+
 template <typename RT>
 int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT> *V, int ldv, cudaStream_t s) {
     if (n <= 0 || m <= 0) return LOBPCG_OK;
@@ -911,22 +925,34 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
         const bool small_tiles = n <= 256;
         const int TS = small_tiles ? 16 : 32;
         const int T = (n + TS - 1) / TS;
-        const int G = std::min(T * T, sms);
+        // with concurrent streams each cooperative grid gets its share of the SMs, so that all of
+        // them fit at once (no gate needed then)
+        const int share = std::max(1, w.coop_share);
+        const int G = std::max(1, std::min(T * T, sms / share));
         const int nown = (T * T + G - 1) / G;
         const size_t dsm = sizeof(cx<RT>) * ((size_t)nown * TS * TS + 4 * (size_t)n);
         const size_t static_sm = sizeof(RT) * 32 + sizeof(cx<RT>) * 16 * 33 + 64;
         int *err = device_wait_flag();
         const void *fn = small_tiles ? (const void *)k_tri_fused<RT, 16> : (const void *)k_tri_fused<RT, 32>;
         if (coop && err && dsm + static_sm <= (size_t)smem_max) {
-            LG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+            LG_TRY(allow_max_dyn_smem(fn));
             int per_sm = 0;
             LG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, dsm));
-            if (per_sm >= 1 && G <= sms * per_sm) {
+            if (per_sm >= 1 && (size_t)G * share <= (size_t)sms * per_sm) {
                 unsigned int *bar = cnt;
                 const cx<RT> *Ac = A;
                 void *args[] = {(void *)&n, (void *)&Ac, (void *)&lda, (void *)&Hv, (void *)&taus, (void *)&dg,
                                 (void *)&eg, (void *)&yp, (void *)&wv, (void *)&bar, (void *)&err};
-                LG_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(256), args, dsm, s));
+                if (w.gate && share == 1) {
+                    // one cooperative grid at a time across concurrent streams
+                    std::lock_guard<std::mutex> lk(w.gate->mu);
+                    if (w.gate->used) LG_CUDA_TRY(cudaStreamWaitEvent(s, w.gate->ev, 0));
+                    LG_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(256), args, dsm, s));
+                    LG_CUDA_TRY(cudaEventRecord(w.gate->ev, s));
+                    w.gate->used = true;
+                } else {
+                    LG_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(256), args, dsm, s));
+                }
                 LG_TRY(check_launch("tridiagonalisation (fused cooperative)"));
                 coop_done = true;
             }
@@ -941,7 +967,7 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
         LG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         LG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         if (dsm > 48 * 1024)
-            LG_CUDA_TRY(cudaFuncSetAttribute(k_tri_coop<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+            LG_TRY(allow_max_dyn_smem((const void *)k_tri_coop<RT>));
         LG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_coop<RT>, 256, dsm));
         const int G = std::min(tl0 * tl0, sms * std::max(per_sm, 0));
         int *err = device_wait_flag();
@@ -949,7 +975,15 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
             unsigned int *bar = cnt;            // arrival counter (zeroed above)
             void *args[] = {(void *)&n, (void *)&A, (void *)&lda, (void *)&Hv, (void *)&taus, (void *)&dg, (void *)&eg,
                             (void *)&yp, (void *)&bar, (void *)&err};
-            LG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tri_coop<RT>, dim3(G), dim3(256), args, dsm, s));
+            if (w.gate) {
+                std::lock_guard<std::mutex> lk(w.gate->mu);
+                if (w.gate->used) LG_CUDA_TRY(cudaStreamWaitEvent(s, w.gate->ev, 0));
+                LG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tri_coop<RT>, dim3(G), dim3(256), args, dsm, s));
+                LG_CUDA_TRY(cudaEventRecord(w.gate->ev, s));
+                w.gate->used = true;
+            } else {
+                LG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tri_coop<RT>, dim3(G), dim3(256), args, dsm, s));
+            }
             LG_TRY(check_launch("tridiagonalisation (cooperative)"));
             coop_done = true;
         }
@@ -970,12 +1004,12 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     LG_TRY(check_launch("multisection"));
     const size_t smem_ii = 5 * sizeof(RT) * (size_t)n + (size_t)n;
     if (smem_ii > 48 * 1024)
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_inviter<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ii));
+        LG_TRY(allow_max_dyn_smem((const void *)k_inviter<RT>));
     k_inviter<RT><<<m, 32, smem_ii, s>>>(n, m, dg, eg, theta, Z);
     LG_TRY(check_launch("inverse iteration"));
     const size_t smem = sizeof(cx<RT>) * (size_t)n;
     if (smem > 48 * 1024) {
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_backtransform<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LG_TRY(allow_max_dyn_smem((const void *)k_backtransform<RT>));
     }
     k_backtransform<RT><<<m, 32, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
     return check_launch("back-transform");

@@ -322,20 +322,22 @@ k_tc_nn(int M, int n, int k, float alpha, const c32 *__restrict__ A, int lda, co
 }
 
 template <typename Kern>
-int ensure_smem(Kern kern, size_t bytes, bool &done) {
-    if (!done) {
+int ensure_smem(Kern kern, size_t bytes, std::atomic<bool> &done) {
+    if (!done.load()) {
         LG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        done = true;
+        done.store(true);
     }
     return LOBPCG_OK;
 }
 
 int num_sms_tc() {
-    static int v = 0;
+    static std::atomic<int> cached{0};
+    int v = cached.load();
     if (!v) {
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cached.store(v);
     }
     return v;
 }
@@ -345,7 +347,7 @@ int launch_cn(GemmWork &w, int m, int n, int K, float alpha, const c32 *A, int l
               float beta, c32 *C, int ldc, cudaStream_t s) {
     constexpr int STAGE = 2 * 128 * ROWB + 2 * 2 * NT * ROWB;
     constexpr size_t SMEM = smem_bytes<STAGE>();
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     LG_TRY(ensure_smem(k_tc_cn<NT>, SMEM, attr));
     const int tm = (m + 127) / 128, tn = (n + NT - 1) / NT;
     const int tiles = tm * tn;
@@ -370,7 +372,7 @@ int launch_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c32
               const c32 *C, int ldc, c32 *D, int ldd, cudaStream_t s) {
     constexpr int STAGE = 2 * 128 * ROWB + 2 * NN * ROWB;
     constexpr size_t SMEM = smem_bytes<STAGE>();
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     LG_TRY(ensure_smem(k_tc_nn<NN>, SMEM, attr));
     const dim3 grid((M + 63) / 64, (n + NN - 1) / NN);
     k_tc_nn<NN><<<grid, kThreads, SMEM, s>>>(M, n, k, alpha, A, lda, B, ldb, beta, beta != 0.f ? C : D, ldc, D, ldd);
@@ -395,7 +397,8 @@ int tc_gemm_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c3
 }
 
 int *device_wait_flag() {
-    static int *p = nullptr;
+    static std::atomic<int *> cached{nullptr};
+    int *p = cached.load();
     if (!p) {
         void *q = nullptr;
         if (cudaGetSymbolAddress(&q, g_tc_err) != cudaSuccess) {
@@ -403,6 +406,7 @@ int *device_wait_flag() {
             return nullptr;
         }
         p = static_cast<int *>(q);
+        cached.store(p);
     }
     return p;
 }
