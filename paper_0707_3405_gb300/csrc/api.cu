@@ -163,7 +163,7 @@ struct Lane {
     GemmWork gw;
     EigWork ew;
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
-    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32;
+    DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32, E32;
     void bind(Allocator *a, CoopGate *g, int share) {
         gw.alloc = a;
         ew.alloc = a;
@@ -175,7 +175,7 @@ struct Lane {
         DevBuf *bufs[] = {&T2, &nlB, &stageX, &stageY, &Zb[0], &Zb[1], &HZb[0], &HZb[1], &Z32, &HZ32, &HXall,
                           &Tmp, &Gram, &Gram2, &Cbuf, &dtheta, &dres, &dwork, &Gc, &gw.part, &ew.buf, &ew.ibuf,
                           &ew.gw.part, &X32all, &HX32all, &Q32[0], &Q32[1], &HQ32[0], &HQ32[1], &D32, &Small32,
-                          &Xext, &T32};
+                          &Xext, &T32, &E32};
         for (DevBuf *b : bufs) a.release(*b);
         if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
@@ -425,6 +425,8 @@ struct Solver {
     c32 *X32, *HX32;         // FP32 copies of X_b, H X_b
     c32 *S32, *A32, *C32, *G32, *D32;
     c32 *T32;                // npw x M FP32 scratch (early-sweep rotations)
+    c32 *E32;                // C - I of a near-identity rotation (FP32)
+    unsigned int *dmax;      // device scratch for max |C - I|
     bool early = false;      // current sweep is an early one of the mixed schedule
     long long applies64 = 0, applies32 = 0;
     int iterations = 0;
@@ -572,6 +574,9 @@ struct Solver {
     // solved in FP64; the coefficients also come back in FP32 for the FP32 updates.
     int rr_mixed(int nz, int mm) {
         LG_TRY(rr(nz, mm, drop_tol32));
+        // a Ritz vector's phase is free: make C's X-diagonal real positive, so that a step which
+        // barely moves X_b has C_X close to I (see near_identity)
+        LG_TRY(fix_phases(nz, mm, C, nz, s));
         PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * nz * mm, false);
         return copy_cast<float, double>(nz, mm, C, nz, C32, nz, s);
     }
@@ -663,10 +668,20 @@ struct Solver {
                 LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, HX32, C32, nz, 1.0f, col(HQn, 2 * m), D32));
                 LG_TRY(cast<double, float>(m, D32, HZ[1 - cur]));
             } else {
-                LG_TRY(cast<double, float>(m, col(Qn, 2 * m), Tmp));
-                LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, nz, 1.0, Tmp, Z[1 - cur]));
-                LG_TRY(cast<double, float>(m, col(HQn, 2 * m), Tmp));
-                LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, nz, 1.0, Tmp, HZ[1 - cur]));
+                bool small = false;
+                LG_TRY(near_identity(m, C, nz, small));
+                if (small) {
+                    // X_new = X + (X32 (C_X - I) + P), H X likewise (near-identity C_X of a late sweep)
+                    LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, X32, E32, m, 1.0f, col(Qn, 2 * m), D32));
+                    LG_TRY(add_cast_cols(Xb, D32, Z[1 - cur], m));
+                    LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, HX32, E32, m, 1.0f, col(HQn, 2 * m), D32));
+                    LG_TRY(add_cast_cols(HXb, D32, HZ[1 - cur], m));
+                } else {
+                    LG_TRY(cast<double, float>(m, col(Qn, 2 * m), Tmp));
+                    LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, nz, 1.0, Tmp, Z[1 - cur]));
+                    LG_TRY(cast<double, float>(m, col(HQn, 2 * m), Tmp));
+                    LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, nz, 1.0, Tmp, HZ[1 - cur]));
+                }
             }
             cur = 1 - cur;
             nP = 1;
@@ -723,6 +738,23 @@ struct Solver {
         LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, m, m, 1.0f, HX32, C32, m, 0.0f, nullptr, D32));
         return cast<double, float>(m, D32, HZ[1]);
     }
+    // Is the rotation C (leading k x k of ld ldc) the identity up to E = C - I with
+    // max|E| * k <= kRotSmall?  Then X C = X + X E can take X E from the FP32 copies on the
+    // tensor cores: its error, ~2e-6 of the column 1-norm of E, stays at the FP64 level of X.
+    static constexpr double kRotSmall = 1e-4;
+    int near_identity(int kk, const z64 *Cm, int ldc, bool &small) {
+        float emax = 0.f;
+        {
+            PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 24.0 * kk * kk, false);
+            LG_TRY(near_identity32(kk, kk, Cm, ldc, E32, kk, dmax, &emax, s));
+        }
+        small = (double)emax * kk <= kRotSmall;
+        return LOBPCG_OK;
+    }
+    int add_cast_cols(const z64 *Aa, const c32 *Tt, z64 *Out, int cols) {
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 2.0 * npw * cols, 2.0 * cbytes64(cols) + cbytes32(cols), true);
+        return add_cast(npw, cols, Aa, npw, Tt, npw, Out, npw, s);
+    }
     int gemm_nn64_axpy(z64 *V, const z64 *D, int cols) {
         PhaseScope ps(prof, LOBPCG_PH_CONSTRAINT, 2.0 * npw * cols, 3.0 * cbytes64(cols), true);
         return axpy_cols(npw, cols, -1.0, D, npw, V, npw, s);
@@ -747,10 +779,25 @@ struct Solver {
         LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, X, S, M));
         LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, HX, A, M));
         LG_TRY(rr(M, M, drop_tol));
-        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, M, M, 1.0, X, C, M, 0.0, nullptr, Tmp));
-        LG_TRY(copy64(X, Tmp, M));
-        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, M, M, 1.0, HX, C, M, 0.0, nullptr, Tmp));
-        LG_TRY(copy64(HX, Tmp, M));
+        bool small = false;
+        if (mixed) {
+            LG_TRY(fix_phases(M, M, C, M, s));
+            LG_TRY(near_identity(M, C, M, small));
+        }
+        if (small) {
+            // near-identity all-band rotation: X += X32 (C - I), H X likewise
+            LG_TRY(cast<float, double>(M, X, X32all));
+            LG_TRY(cast<float, double>(M, HX, HX32all));
+            LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, M, M, 1.0f, X32all, E32, M, 0.0f, nullptr, T32));
+            LG_TRY(add_cast_cols(X, T32, X, M));
+            LG_TRY(gemm_nn32(LOBPCG_PH_UPDATE, M, M, 1.0f, HX32all, E32, M, 0.0f, nullptr, T32));
+            LG_TRY(add_cast_cols(HX, T32, HX, M));
+        } else {
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, M, M, 1.0, X, C, M, 0.0, nullptr, Tmp));
+            LG_TRY(copy64(X, Tmp, M));
+            LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, M, M, 1.0, HX, C, M, 0.0, nullptr, Tmp));
+            LG_TRY(copy64(HX, Tmp, M));
+        }
         {
             PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * M, cbytes64(2.0 * M), true);
             LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
@@ -858,6 +905,8 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
         sv.C32 = sm + 2 * (size_t)nzmax * nzmax;
         sv.G32 = sm + 3 * (size_t)nzmax * nzmax;
         sv.T32 = carve<c32>(c, L.T32, (size_t)npw * M, rc); LG_TRY(rc);
+        sv.E32 = carve<c32>(c, L.E32, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
+        sv.dmax = reinterpret_cast<unsigned int *>(w + 4 * (size_t)nzmax + 8);
         // H X of the start vectors, and the FP32 copies the constraint uses
         LG_TRY(sv.applyH64(X, sv.HX, M));
         LG_TRY(sv.cast<float, double>(M, X, sv.X32all));

@@ -300,6 +300,13 @@ int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int
 int assemble_gram_mixed32(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
                           c32 *S, c32 *A, cudaStream_t s);
 int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, cudaStream_t s);
+// E = C - I (leading rows x cols, FP32) and its largest component magnitude on the host (synchronises).
+int near_identity32(int rows, int cols, const z64 *C, int ldc, c32 *E, int lde, unsigned int *dmax, float *hmax,
+                    cudaStream_t s);
+// Scale column j of C by conj(C_jj)/|C_jj| (leading rows x cols, j < min(rows, cols)).
+int fix_phases(int rows, int cols, z64 *C, int ldc, cudaStream_t s);
+// out = A + fp64(T).
+int add_cast(int rows, int cols, const z64 *A, int lda, const c32 *T, int ldt, z64 *out, int ldo, cudaStream_t s);
 int residual32(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta, c32 *R, int ldr,
                cudaStream_t s);
 int precond32(int npw, int m, const z64 *X, int ldx, const double *kin, const c32 *R, int ldr, c32 *W, int ldw,

@@ -5,6 +5,8 @@
 // row scalings.
 #include "common.cuh"
 
+#include <cstring>
+
 #include <algorithm>
 
 namespace lg {
@@ -349,6 +351,78 @@ int scale_rows(int rows, int cols, const R *d, cx<R> *A, int lda, cudaStream_t s
     if (rows <= 0 || cols <= 0) return LOBPCG_OK;
     k_scale_rows<R><<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, d, A, lda);
     return check_launch("scale rows");
+}
+
+// E = C - I on the leading rows x cols block of C (FP64 in, FP32 out) and max |E| (as float bits,
+// an atomic max on non-negative floats).
+__global__ void k_near_identity32(int rows, int cols, const z64 *__restrict__ C, int ldc, c32 *__restrict__ E,
+                                  int lde, unsigned int *__restrict__ maxbits) {
+    const size_t tot = (size_t)rows * cols;
+    float mx = 0.f;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        z64 v = C[(size_t)j * ldc + i];
+        if (i == j) v.x -= 1.0;
+        const c32 f = mkc<float>((float)v.x, (float)v.y);
+        E[(size_t)j * lde + i] = f;
+        mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(mx));
+}
+
+// out = A + fp64(T) column by column (out may be A).
+__global__ void k_add_cast(int rows, int cols, const z64 *A, int lda, const c32 *__restrict__ T, int ldt, z64 *out,
+                           int ldo) {
+    const size_t tot = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        const c32 t = T[(size_t)j * ldt + i];
+        const z64 a = A[(size_t)j * lda + i];
+        out[(size_t)j * ldo + i] = mkc(a.x + (double)t.x, a.y + (double)t.y);
+    }
+}
+
+// Column j of C times conj(C_jj)/|C_jj| (a Ritz vector's phase is free): the diagonal becomes
+// real and non-negative, so a rotation that only re-phases is the identity.
+__global__ void k_fix_phases(int rows, int cols, z64 *__restrict__ C, int ldc) {
+    const int j = blockIdx.x;
+    if (j >= cols || j >= rows) return;
+    const z64 p = C[(size_t)j * ldc + j];
+    const double a = sqrt(p.x * p.x + p.y * p.y);
+    if (!(a > 0.0)) return;
+    const z64 ph = mkc(p.x / a, -p.y / a);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) C[(size_t)j * ldc + i] = C[(size_t)j * ldc + i] * ph;
+}
+
+int fix_phases(int rows, int cols, z64 *C, int ldc, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_fix_phases<<<cols, 128, 0, s>>>(rows, cols, C, ldc);
+    return check_launch("fix phases");
+}
+
+int near_identity32(int rows, int cols, const z64 *C, int ldc, c32 *E, int lde, unsigned int *dmax, float *hmax,
+                    cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) {
+        *hmax = 0.f;
+        return LOBPCG_OK;
+    }
+    LG_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(unsigned int), s));
+    k_near_identity32<<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, C, ldc, E, lde, dmax);
+    LG_TRY(check_launch("near-identity part"));
+    unsigned int h = 0;
+    LG_CUDA_TRY(cudaMemcpyAsync(&h, dmax, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    LG_CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(hmax, &h, sizeof(float));
+    return LOBPCG_OK;
+}
+
+int add_cast(int rows, int cols, const z64 *A, int lda, const c32 *T, int ldt, z64 *out, int ldo, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_add_cast<<<grid_for((size_t)rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, T, ldt, out, ldo);
+    return check_launch("add cast");
 }
 
 template int residual_precond<double>(int, int, const z64 *, int, const z64 *, int, const double *, const double *,
