@@ -109,6 +109,10 @@ typedef struct {
     double mixed_early;  /* MIXED only: while the largest residual of the previous sweep is above this
                             (Ha), block starts and the sweep-end Rayleigh-Ritz use the FP32 copies and
                             skip the FP64 H X refresh (default 1e-3; 0 = never) */
+    int    fp64_gemm;    /* arithmetic of the FP64-class tall GEMMs (Grams, constraint, Ritz updates,
+                            KB projections of FP64 H X): 0 = auto (MIXED: double-FP32 on the FP32 units,
+                            about 2^-47 relative per product; FP64: native FP64), 1 = native FP64,
+                            2 = double-FP32 on both schedules */
 } lobpcg_options;
 
 /* Phases of a solve, for the per-phase timers of lobpcg_stats. */

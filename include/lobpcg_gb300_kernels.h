@@ -9,7 +9,12 @@
  * Common rules
  *   - Matrices are column-major with a leading dimension (elements).
  *   - Complex numbers are interleaved (re, im); prec = LOBPCG_C128 selects
- *     complex128 with FP64 arithmetic, LOBPCG_C64 complex64 with FP32.
+ *     complex128 with FP64 arithmetic, LOBPCG_C64 complex64 with FP32, and
+ *     (GEMMs only) LOBPCG_C128_DF32 complex128 with double-FP32 arithmetic:
+ *     every operand split into two FP32 parts, exact FP32 products by FMA
+ *     (Dekker's TwoProd) and pair accumulators (Knuth's TwoSum), about 2^-47
+ *     relative per product, run on the FP32 units (FP64 class, several
+ *     times the FP64 rate of this GPU).
  *   - Pointers are device pointers; work is enqueued on `stream`
  *     (cudaStream_t, NULL = legacy default stream) and the call returns
  *     without synchronising, except where noted.
@@ -22,6 +27,8 @@
 #define LOBPCG_GB300_KERNELS_H
 
 #include "lobpcg_gb300.h"
+
+#define LOBPCG_C128_DF32 2   /* complex128 in/out, double-FP32 arithmetic (GEMMs only) */
 
 #ifdef __cplusplus
 extern "C" {
@@ -39,6 +46,21 @@ extern "C" {
  */
 int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A, int lda,
                      const void *B, int ldb, double beta, void *C, int ldc, void *stream);
+
+/*
+ * Lower triangle of C = A^H B, complex128 (prec = LOBPCG_C128 or
+ * LOBPCG_C128_DF32): the FP64-class Gram matrices of
+ * Algorithm 1, step 4 and of the all-band Rayleigh-Ritz closing a sweep
+ * (Sec. 3.2).  Both Grams of the Rayleigh-Ritz pencil are Hermitian and the
+ * pencil solver reads only their lower triangles, so 64 x 64 output tiles
+ * strictly above the diagonal are skipped: about half the work for n >> 64.
+ *   A and B are K x n (lda, ldb >= K), C is n x n (ldc >= n).  Every element
+ *   C(i, j) with i >= j is written; tiles strictly above the diagonal are
+ *   left untouched, and the rest of the upper triangle holds A^H B values.
+ *   Same split and fixed summation order as lobpcg_k_gemm_cn.
+ */
+int lobpcg_k_gram_lower(int prec, int n, int K, const void *A, int lda, const void *B, int ldb, void *C,
+                        int ldc, void *stream);
 
 /*
  * D = alpha * A B + beta * C: the Ritz updates of Algorithm 1, steps 4-5

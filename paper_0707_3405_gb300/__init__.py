@@ -25,14 +25,14 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblobpcg_gb300.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BREAKDOWN, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-C128, C64 = 0, 1
+C128, C64, C128_DF32 = 0, 1, 2
 FP64, MIXED = 0, 1
 
 EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
-    "lobpcg_k_gemm_cn", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
+    "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
     "lobpcg_k_set_gemm_mode", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
 
@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("gemm_split", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong),
                 ("timing", ctypes.c_int), ("nbuf", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("mixed_early", ctypes.c_double)]
+                ("mixed_early", ctypes.c_double), ("fp64_gemm", ctypes.c_int)]
 
 
 PHASES = ("fft", "nonlocal", "gram", "constraint", "rr", "update")
@@ -109,6 +109,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_launch_count": (ctypes.c_longlong, []),
         "lobpcg_apply_local_noalloc": (i, [vp, i, vp, vp, i, i]),
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
+        "lobpcg_k_gram_lower": (i, [i, i, i, vp, i, vp, i, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
         "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_rayleigh_ritz32": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
@@ -177,7 +178,8 @@ class Solver:
     def __init__(self, a: float, N: int, ecut: float, kpts, vloc, proj_E=None, beta=None,
                  block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
                  tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, nbuf: int = 0,
-                 mixed_switch: float | None = None, mixed_early: float | None = None, stream=None):
+                 mixed_switch: float | None = None, mixed_early: float | None = None, stream=None,
+                 fp64_gemm: int = 0):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -189,7 +191,7 @@ class Solver:
         self.nproj = int(E.shape[0])
         self.nk = int(kp.shape[0])
         opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
-                            mixed_early)
+                            mixed_early, fp64_gemm)
         cell = Cell(a, N, ecut)
         self._stream = stream
         rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
@@ -205,7 +207,7 @@ class Solver:
 
     @staticmethod
     def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False, nbuf=0,
-                 mixed_switch=None, mixed_early=None) -> Options:
+                 mixed_switch=None, mixed_early=None, fp64_gemm=0) -> Options:
         o = default_options()
         o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -217,12 +219,13 @@ class Solver:
             o.mixed_switch = mixed_switch
         if mixed_early is not None:
             o.mixed_early = mixed_early
+        o.fp64_gemm = fp64_gemm
         return o
 
     def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0,
-                    timing=False, nbuf=0, mixed_switch=None, mixed_early=None):
+                    timing=False, nbuf=0, mixed_switch=None, mixed_early=None, fp64_gemm=0):
         o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
-                          mixed_early)
+                          mixed_early, fp64_gemm)
         _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
 
     def set_stream(self, stream):
@@ -333,12 +336,17 @@ def check_timeouts():
     _check(load().lobpcg_k_check_timeouts(), None, kernels=True)
 
 
-def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None):
+def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None, df32=False):
     """C = alpha A^H B + beta C for torch CUDA tensors given as (cols, rows) row-major
-    (i.e. column-major matrices): A is (m, K), B is (n, K), C is (n, m)."""
+    (i.e. column-major matrices): A is (m, K), B is (n, K), C is (n, m).  df32=True
+    (complex128 only) runs the double-FP32 engine instead of FP64 arithmetic."""
     import torch
     lib = load()
     prec = C128 if A.dtype == torch.complex128 else C64
+    if df32:
+        if prec != C128:
+            raise ValueError("df32 needs complex128 operands")
+        prec = C128_DF32
     m, K = A.shape
     n = B.shape[0]
     if C is None:
@@ -348,12 +356,32 @@ def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None):
     return C
 
 
-def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None):
+def gram_lower(A, B, C=None, stream=None, df32=False):
+    """Lower triangle of C = A^H B (complex128), column-major as in gemm_cn: A and B are
+    (n, K), C is (n, n).  Tiles of C strictly above the diagonal are left untouched.
+    df32=True runs the double-FP32 engine instead of FP64 arithmetic."""
+    import torch
+    lib = load()
+    n, K = A.shape
+    if A.dtype != torch.complex128 or B.dtype != torch.complex128 or B.shape != A.shape:
+        raise ValueError("gram_lower: A and B must be complex128 of the same shape")
+    if C is None:
+        C = torch.zeros((n, n), dtype=A.dtype, device=A.device)
+    _check(lib.lobpcg_k_gram_lower(C128_DF32 if df32 else C128, n, K, _ptr(A), K, _ptr(B), K, _ptr(C), n,
+                                   _stream_handle(stream)), None, kernels=True)
+    return C
+
+
+def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None, df32=False):
     """D = alpha A B + beta C, column-major stored as transposed torch tensors:
-    A is (k, M), B is (n, k), C and D are (n, M)."""
+    A is (k, M), B is (n, k), C and D are (n, M).  df32=True as in gemm_cn."""
     import torch
     lib = load()
     prec = C128 if A.dtype == torch.complex128 else C64
+    if df32:
+        if prec != C128:
+            raise ValueError("df32 needs complex128 operands")
+        prec = C128_DF32
     k, M = A.shape
     n = B.shape[0]
     if D is None:

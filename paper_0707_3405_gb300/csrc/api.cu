@@ -332,7 +332,7 @@ template <> struct Tables<float> {
 // T + V_loc, then the KB projection B = beta^H X, B <- E B, Y += beta B.
 template <typename R>
 int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
-                Prof *prof = nullptr) {
+                Prof *prof = nullptr, bool df = false) {
     if (nb <= 0) return LOBPCG_OK;
     KPoint &K = c->kp[k];
     const FFTGeom &g = K.geom;
@@ -358,7 +358,14 @@ int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y
         const cx<R> *beta = Tables<R>::beta(K);
         const double fl = 16.0 * K.npw * (double)c->nproj * nb;
         const double by = cb * (2.0 * K.npw * c->nproj + 3.0 * K.npw * nb);
-        PhaseScope ps(prof, LOBPCG_PH_NONLOCAL, fl, by, f64);
+        PhaseScope ps(prof, LOBPCG_PH_NONLOCAL, fl, by, f64 && !df);
+        if constexpr (sizeof(R) == 8) {
+            if (df) {  // double-FP32 projections (FP64 class)
+                LG_TRY(zgemm_cn_df(L.gw, c->nproj, nb, K.npw, 1.0, beta, K.npw, X, ldx, 0.0, B, c->nproj, L.stream));
+                LG_TRY(scale_rows<R>(c->nproj, nb, Tables<R>::E(c), B, c->nproj, L.stream));
+                return zgemm_nn_df(K.npw, nb, c->nproj, 1.0, beta, K.npw, B, c->nproj, 1.0, Y, ldy, Y, ldy, L.stream);
+            }
+        }
         LG_TRY(gemm_cn<R>(L.gw, c->nproj, nb, K.npw, (R)1, beta, K.npw, X, ldx, (R)0, B, c->nproj, L.stream));
         LG_TRY(scale_rows<R>(c->nproj, nb, Tables<R>::E(c), B, c->nproj, L.stream));
         LG_TRY(gemm_nn<R>(K.npw, nb, c->nproj, (R)1, beta, K.npw, B, c->nproj, (R)1, Y, ldy, Y, ldy, L.stream));
@@ -409,6 +416,7 @@ struct Solver {
     Prof *prof;
     int k, npw, M, m, nblk;
     bool mixed;
+    bool df = false;  // FP64-class tall GEMMs in double-FP32 arithmetic
     cudaStream_t s;
     z64 *X, *HX;             // all bands, FP64 (X is the caller's buffer)
     z64 *Z[2], *HZ[2];       // FP64 block bases [X W P] (mixed: only the X part)
@@ -457,7 +465,7 @@ struct Solver {
 
     int applyH64(const z64 *Xin, z64 *Yout, int nb) {
         applies64 += nb;
-        return apply_H_dev<double>(c, *L, k, Xin, npw, Yout, npw, nb, prof);
+        return apply_H_dev<double>(c, *L, k, Xin, npw, Yout, npw, nb, prof, df);
     }
     int applyH32(const c32 *Xin, c32 *Yout, int nb) {
         applies32 += nb;
@@ -466,12 +474,19 @@ struct Solver {
 
     // ---------------------------------------------------------- FP64 helpers
     int gemm_cn64(int ph, int mm, int nn, const z64 *Aa, const z64 *Bb, z64 *Cc, int ldc) {
-        PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes64(mm + nn), true);
+        PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes64(mm + nn), !df);
+        if (df) return zgemm_cn_df(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
         return gemm_cn<double>(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
+    }
+    // Hermitian Gram (lower triangle only; the Rayleigh-Ritz reads no more)
+    int gram64(int nn, const z64 *Aa, const z64 *Bb, z64 *Cc) {
+        PhaseScope ps(prof, LOBPCG_PH_GRAM, 4.0 * nn * (nn + 1) * (double)npw, cbytes64(2 * nn), !df);
+        return zgemm_cn_lower(L->gw, nn, npw, Aa, npw, Bb, npw, Cc, nn, s, df);
     }
     int gemm_nn64(int ph, int nn, int kk, double alpha, const z64 *Aa, const z64 *Bb, int ldb, double beta,
                   const z64 *Cc, z64 *Dd) {
-        PhaseScope ps(prof, ph, 8.0 * nn * kk * (double)npw, cbytes64(kk + nn * (beta != 0.0 ? 2 : 1)), true);
+        PhaseScope ps(prof, ph, 8.0 * nn * kk * (double)npw, cbytes64(kk + nn * (beta != 0.0 ? 2 : 1)), !df);
+        if (df) return zgemm_nn_df(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
         return gemm_nn<double>(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
     }
     int gemm_cn32(int ph, int mm, int nn, const c32 *Aa, const c32 *Bb, c32 *Cc, int ldc) {
@@ -533,8 +548,8 @@ struct Solver {
         LG_TRY(constrain64(Z[cur], m, b * m));
         LG_TRY(applyH64(Z[cur], HZ[cur], m));
         // Rayleigh-Ritz on the block alone: orthonormal Ritz basis, Upsilon (step 1)
-        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Z[cur], Z[cur], S, m));
-        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Z[cur], HZ[cur], A, m));
+        LG_TRY(gram64(m, Z[cur], Z[cur], S));
+        LG_TRY(gram64(m, Z[cur], HZ[cur], A));
         LG_TRY(rr(m, m, drop_tol));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Z[cur], C, m, 0.0, nullptr, Z[1 - cur]));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HZ[cur], C, m, 0.0, nullptr, HZ[1 - cur]));
@@ -551,8 +566,8 @@ struct Solver {
             LG_TRY(applyH64(W, HW, m));
             // step 4: Rayleigh-Ritz on span[X, W, P]
             const int nz = (2 + nP) * m;
-            LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, nz, nz, Zc, Zc, S, nz));
-            LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, nz, nz, Zc, HZc, A, nz));
+            LG_TRY(gram64(nz, Zc, Zc, S));
+            LG_TRY(gram64(nz, Zc, HZc, A));
             LG_TRY(rr(nz, m, drop_tol));
             // steps 4-5: P = W Lambda + P Gamma, X = X Delta + P (and their H images)
             z64 *Zn = Z[1 - cur], *HZn = HZ[1 - cur];
@@ -610,8 +625,8 @@ struct Solver {
             }
         }
         // Rayleigh-Ritz of the block alone (FP64 Grams), rotation in FP64
-        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Xb, Xb, S, m));
-        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, m, m, Xb, HXb, A, m));
+        LG_TRY(gram64(m, Xb, Xb, S));
+        LG_TRY(gram64(m, Xb, HXb, A));
         LG_TRY(rr(m, m, drop_tol));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, Xb, C, m, 0.0, nullptr, Z[1 - cur]));
         LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, 1.0, HXb, C, m, 0.0, nullptr, HZ[1 - cur]));
@@ -776,8 +791,8 @@ struct Solver {
     int final_rr(double *eig_h, double *res_h) {
         if (early) return final_rr_early(eig_h, res_h);
         if (mixed) LG_TRY(applyH64(X, HX, M));  // FP64 H X for the residual test
-        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, X, S, M));
-        LG_TRY(gemm_cn64(LOBPCG_PH_GRAM, M, M, X, HX, A, M));
+        LG_TRY(gram64(M, X, X, S));
+        LG_TRY(gram64(M, X, HX, A));
         LG_TRY(rr(M, M, drop_tol));
         bool small = false;
         if (mixed) {
@@ -865,6 +880,7 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     sv.m = c->opt.block_size;
     sv.nblk = M / sv.m;
     sv.mixed = c->opt.precision == LOBPCG_MIXED;
+    sv.df = c->opt.fp64_gemm == 2 || (c->opt.fp64_gemm == 0 && sv.mixed);
     sv.X = X;
     sv.s = L.stream;
     sv.drop_tol = 1e-12;
@@ -971,6 +987,7 @@ int validate_options(const lobpcg_options &o) {
         return fail(LOBPCG_ERR_ARG, "gemm_split must be 0, 2 or 3");
     if (!(o.mixed_switch >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_switch must be >= 0");
     if (!(o.mixed_early >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_early must be >= 0");
+    if (o.fp64_gemm < 0 || o.fp64_gemm > 2) return fail(LOBPCG_ERR_ARG, "fp64_gemm must be 0, 1 or 2");
     return LOBPCG_OK;
 }
 
@@ -995,6 +1012,7 @@ int lobpcg_default_options(lobpcg_options *opt) {
     opt->nbuf = 0;
     opt->mixed_switch = 0.0;
     opt->mixed_early = 1e-3;
+    opt->fp64_gemm = 0;
     return LOBPCG_OK;
 }
 

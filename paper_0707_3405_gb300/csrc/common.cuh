@@ -225,6 +225,17 @@ struct GemmWork {
 template <typename R>
 int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
             R beta, cx<R> *C, int ldc, cudaStream_t s);
+// Lower triangle of C = A^H B (n x n, complex128): 64 x 64 tiles strictly above the
+// diagonal are skipped (Hermitian Grams whose consumers read the lower triangle only).
+// df = true: double-FP32 arithmetic (FP64 class, ~2^-47 per product) instead of FP64.
+int zgemm_cn_lower(GemmWork &w, int n, int K, const z64 *A, int lda, const z64 *B, int ldb, z64 *C, int ldc,
+                   cudaStream_t s, bool df = false);
+// Complex128 C = alpha A^H B + beta C and D = alpha A B + beta C in double-FP32
+// arithmetic on the FP32 units (tall products; K split as for gemm_cn).
+int zgemm_cn_df(GemmWork &w, int m, int n, int K, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
+                double beta, z64 *C, int ldc, cudaStream_t s);
+int zgemm_nn_df(int M, int n, int k, double alpha, const z64 *A, int lda, const z64 *B, int ldb, double beta,
+                const z64 *C, int ldc, z64 *D, int ldd, cudaStream_t s);
 // Complex64 products on the tensor cores (3xTF32 split operands, FP32 accumulation):
 // C = alpha A^H B + beta C (K split over the GPU, FP64 partial sums) and
 // D = alpha A B + beta C.  gemm_cn<float> / gemm_nn<float> route here for long

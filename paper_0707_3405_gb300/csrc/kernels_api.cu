@@ -2,6 +2,7 @@
 // GEMMs and FP64 eigen-solvers of one LOBPCG block iteration, callable on
 // their own.  Scratch memory comes from one library-owned pool.
 #include "common.cuh"
+#include "lobpcg_gb300_kernels.h"
 
 #include <mutex>
 
@@ -43,10 +44,25 @@ int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A,
     if (prec == LOBPCG_C128)
         return gemm_cn<double>(pool().gw, m, n, K, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B),
                                ldb, beta, static_cast<z64 *>(C), ldc, s);
+    if (prec == LOBPCG_C128_DF32)
+        return zgemm_cn_df(pool().gw, m, n, K, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B),
+                           ldb, beta, static_cast<z64 *>(C), ldc, s);
     if (prec == LOBPCG_C64)
         return gemm_cn<float>(pool().gw, m, n, K, (float)alpha, static_cast<const c32 *>(A), lda,
                               static_cast<const c32 *>(B), ldb, (float)beta, static_cast<c32 *>(C), ldc, s);
     return fail(LOBPCG_ERR_ARG, "unknown precision");
+}
+
+int lobpcg_k_gram_lower(int prec, int n, int K, const void *A, int lda, const void *B, int ldb, void *C,
+                        int ldc, void *stream) {
+    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32) return fail(LOBPCG_ERR_ARG, "unknown precision");
+    if (n < 0 || K < 0) return fail(LOBPCG_ERR_ARG, "negative size");
+    if (n == 0) return LOBPCG_OK;
+    if (!A || !B || !C || lda < K || ldb < K || ldc < n) return fail(LOBPCG_ERR_ARG, "bad pointer or leading dimension");
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    return zgemm_cn_lower(pool().gw, n, K, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb,
+                          static_cast<z64 *>(C), ldc, reinterpret_cast<cudaStream_t>(stream),
+                          prec == LOBPCG_C128_DF32);
 }
 
 int lobpcg_k_gemm_nn(int prec, int M, int n, int k, double alpha, const void *A, int lda, const void *B, int ldb,
@@ -59,6 +75,9 @@ int lobpcg_k_gemm_nn(int prec, int M, int n, int k, double alpha, const void *A,
     if (prec == LOBPCG_C128)
         return gemm_nn<double>(M, n, k, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb, beta,
                                static_cast<const z64 *>(C), ldc, static_cast<z64 *>(D), ldd, s);
+    if (prec == LOBPCG_C128_DF32)
+        return zgemm_nn_df(M, n, k, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb, beta,
+                           static_cast<const z64 *>(C), ldc, static_cast<z64 *>(D), ldd, s);
     if (prec == LOBPCG_C64)
         return gemm_nn<float>(M, n, k, (float)alpha, static_cast<const c32 *>(A), lda, static_cast<const c32 *>(B), ldb,
                               (float)beta, static_cast<const c32 *>(C), ldc, static_cast<c32 *>(D), ldd, s);

@@ -30,3 +30,4 @@ def test_default_options_without_gpu():
     ensure_built()
     o = lg.default_options()
     assert o.block_size == 64 and o.nline == 4 and o.precision == lg.FP64 and abs(o.tol - 1e-8) < 1e-20
+    assert o.fp64_gemm == 0 and abs(o.mixed_early - 1e-3) < 1e-20

@@ -43,6 +43,76 @@ def test_gemm_cn(m, n, K, prec):
     assert (np.abs(got - ref) / scale).max() < tol
 
 
+# double-FP32 engine: ~2^-47 per product, the pair accumulator renormalised every 16 terms;
+# bound 2e-12 relative to sum |a||b| (the FP64 engine: 1e-13)
+DF32_TOL = 2e-12
+
+
+@pytest.mark.parametrize("n,K", [(1, 1), (64, 925), (65, 5000), (200, 57925), (320, 3001), (33, 100)])
+@pytest.mark.parametrize("df32", [False, True])
+def test_gram_lower(n, K, df32):
+    """Lower triangle of A^H B (complex128); tiles strictly above the diagonal untouched."""
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(n * 3 + K)
+    A, B = _c(rng, K, n), _c(rng, K, n)
+    At = torch.tensor(A.T.copy(), device="cuda")
+    Bt = torch.tensor(B.T.copy(), device="cuda")
+    sentinel = 12345.0 + 0j
+    Ct = torch.full((n, n), sentinel, dtype=torch.complex128, device="cuda")
+    lg.gram_lower(At, Bt, C=Ct, df32=df32)
+    got = Ct.cpu().numpy().T
+    ref = A.conj().T @ B
+    scale = np.abs(A).T @ np.abs(B)
+    i, j = np.tril_indices(n)
+    assert (np.abs(got[i, j] - ref[i, j]) / scale[i, j]).max() < (DF32_TOL if df32 else 1e-13)
+    # 64 x 64 (or 32 x 32 for small FP64 products) tiles strictly above the diagonal keep the sentinel
+    bt = 32 if n * n <= 512 * 512 and K <= 8192 and not df32 else 64
+    ti, tj = np.meshgrid(np.arange(n) // bt, np.arange(n) // bt, indexing="ij")
+    up = ti < tj
+    assert np.all(got[up] == sentinel)
+    assert np.allclose(got[~up], ref[~up], rtol=0, atol=(1e-11 if df32 else 1e-12) * scale.max())
+
+
+@pytest.mark.parametrize("m,n,K", [(1, 1, 1), (16, 16, 925), (64, 37, 5000), (192, 192, 57925), (256, 320, 57925),
+                                   (7, 130, 100)])
+def test_gemm_cn_df32(m, n, K):
+    """Double-FP32 A^H B against FP64 numpy, with a planted-cancellation column: a Gram entry
+    that is tiny next to sum |a||b| must still come out to FP64 class (an FP32 accumulator
+    would leave ~1e-7 of sum |a||b| there)."""
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(m * 11 + n + K)
+    A, B, C0 = _c(rng, K, m), _c(rng, K, n), _c(rng, m, n)
+    if K > 1 and n > 1:
+        B[:, 0] = B[:, 0] - A[:, 0] * (A[:, 0].conj() @ B[:, 0]) / (A[:, 0].conj() @ A[:, 0])  # a0 ^H b0 ~ 0
+    At = torch.tensor(A.T.copy(), device="cuda")
+    Bt = torch.tensor(B.T.copy(), device="cuda")
+    Ct = torch.tensor(C0.T.copy(), device="cuda")
+    lg.gemm_cn(At, Bt, alpha=0.5, beta=-2.0, C=Ct, df32=True)
+    got = Ct.cpu().numpy().T
+    ref = 0.5 * A.conj().T @ B - 2.0 * C0
+    scale = 0.5 * np.abs(A).T @ np.abs(B) + 2.0 * np.abs(C0)
+    assert (np.abs(got - ref) / scale).max() < DF32_TOL
+
+
+@pytest.mark.parametrize("M,n,k", [(1, 1, 1), (925, 16, 16), (57925, 64, 128), (57925, 320, 320), (3001, 7, 432),
+                                   (100, 130, 65)])
+def test_gemm_nn_df32(M, n, k):
+    import torch
+    import paper_0707_3405_gb300 as lg
+    rng = np.random.default_rng(M + 5 * n + k)
+    A, B, C0 = _c(rng, M, k), _c(rng, k, n), _c(rng, M, n)
+    At = torch.tensor(A.T.copy(), device="cuda")
+    Bt = torch.tensor(B.T.copy(), device="cuda")
+    Ct = torch.tensor(C0.T.copy(), device="cuda")
+    D = lg.gemm_nn(At, Bt, alpha=-1.0, beta=1.0, C=Ct, D=Ct, df32=True)   # in-place accumulate
+    got = D.cpu().numpy().T
+    ref = -A @ B + C0
+    scale = np.abs(A) @ np.abs(B) + np.abs(C0)
+    assert (np.abs(got - ref) / scale).max() < DF32_TOL
+
+
 @pytest.mark.parametrize("M,n,k", [(1, 1, 1), (925, 16, 16), (57925, 64, 128), (3001, 7, 432), (100, 130, 65)])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_gemm_nn(M, n, k, prec):

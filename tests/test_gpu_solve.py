@@ -64,6 +64,20 @@ def test_solve_tiny_kb_kpoint(precision, M, m):
         _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
 
 
+@pytest.mark.parametrize("precision,fp64_gemm", [("fp64", 2), ("mixed", 1), ("mixed", 2)])
+def test_solve_fp64_gemm_engines(precision, fp64_gemm):
+    """The FP64-class tall GEMMs in native FP64 (1) or double-FP32 (2) arithmetic on either
+    schedule: the same eigenpairs to 1e-9 Ha (several blocks, constraint, KB projectors)."""
+    w = synth.tiny_workload(a=6.0, N=12, natoms=2, kpt=(0.25, 0.125, -0.375))
+    ref = np.loadtxt(os.path.join(GOLDEN, "tiny_kb_eig.txt"))
+    with make_solver(w, block_size=8, nline=4, max_sweeps=200, precision=precision, tol=1e-8,
+                     fp64_gemm=fp64_gemm) as s:
+        X = _start(w, s, M=24)
+        res = s.solve([X])
+        assert res.status == 0
+        _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
+
+
 def test_solve_free_electron_degenerate():
     """V = 0, no projectors: the closed-form spectrum 1/2|k+G|^2 with its degenerate shells."""
     a, N = 6.0, 12
