@@ -109,10 +109,13 @@ typedef struct {
     double mixed_early;  /* MIXED only: while the largest residual of the previous sweep is above this
                             (Ha), block starts and the sweep-end Rayleigh-Ritz use the FP32 copies and
                             skip the FP64 H X refresh (default 1e-3; 0 = never) */
-    int    fp64_gemm;    /* arithmetic of the FP64-class tall GEMMs (Grams, constraint, Ritz updates,
-                            KB projections of FP64 H X): 0 = auto (MIXED: double-FP32 on the FP32 units,
-                            about 2^-47 relative per product; FP64: native FP64), 1 = native FP64,
-                            2 = double-FP32 on both schedules */
+    int    fp64_gemm;    /* arithmetic of the FP64-class work limited by this GPU's FP64 units: the tall
+                            GEMMs (Grams, constraint, Ritz updates, KB projections of FP64 H X) and, in
+                            the Rayleigh-Ritz step, the Cholesky diagonal blocks, the tridiagonalisation's
+                            column work and the small products.  0 = auto (MIXED: double-FP32 on the FP32
+                            units, about 2^-47 relative per operation; FP64: native FP64), 1 = native
+                            FP64, 2 = double-FP32 on both schedules.  The serial recurrences
+                            (multisection, inverse iteration, back-transformation) stay FP64. */
 } lobpcg_options;
 
 /* Phases of a solve, for the per-phase timers of lobpcg_stats. */

@@ -92,6 +92,18 @@ int lobpcg_k_rayleigh_ritz(int n, int m, const void *S, const void *A, double dr
                            double *theta, void *C, int *ndropped, void *stream);
 
 /*
+ * The same Rayleigh-Ritz step with the parts that one SM's FP64 units limit on
+ * this GPU in double-FP32 arithmetic (the LOBPCG_C128_DF32 scheme above): the
+ * Cholesky diagonal blocks, the column work of the Householder
+ * tridiagonalisation and the small dense products.  The serial recurrences
+ * (multisection, inverse iteration, back-transformation) stay FP64.  Same
+ * arguments, layout and errors as lobpcg_k_rayleigh_ritz; results agree with
+ * it to about 1e-13 relative.
+ */
+int lobpcg_k_rayleigh_ritz_df32(int n, int m, const void *S, const void *A, double drop_tol,
+                                double *theta, void *C, int *ndropped, void *stream);
+
+/*
  * The same Rayleigh-Ritz step in FP32 arithmetic: S, A and C are complex64
  * (n x n and n x m, column-major), theta is float.  The mixed-precision
  * schedule uses it inside the block iterations, where only the search

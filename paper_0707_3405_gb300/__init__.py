@@ -32,7 +32,7 @@ EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
-    "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
+    "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz_df32", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
     "lobpcg_k_set_gemm_mode", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
 
@@ -112,6 +112,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_k_gram_lower": (i, [i, i, i, vp, i, vp, i, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
         "lobpcg_k_rayleigh_ritz": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
+        "lobpcg_k_rayleigh_ritz_df32": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_rayleigh_ritz32": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_heev": (i, [i, vp, vp, vp, vp]),
         "lobpcg_k_set_gemm_mode": (i, [i]),
@@ -392,18 +393,20 @@ def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None, df32=False):
     return D
 
 
-def rayleigh_ritz(S, A, m, drop_tol=1e-12, stream=None):
+def rayleigh_ritz(S, A, m, drop_tol=1e-12, stream=None, df32=False):
     """Lowest m pairs of A c = theta S c (n x n complex128 CUDA tensors, column-major
     i.e. pass the transpose of a numpy matrix).  Returns (theta (m,), C (m, n) whose
-    row j is column j of the coefficient matrix, ndropped)."""
+    row j is column j of the coefficient matrix, ndropped).  df32=True runs the
+    FP64-unit-bound parts in double-FP32 arithmetic."""
     import torch
     lib = load()
     n = S.shape[0]
     theta = torch.empty(m, dtype=torch.float64, device=S.device)
     C = torch.empty((m, n), dtype=torch.complex128, device=S.device)
     nd = torch.zeros(1, dtype=torch.int32, device=S.device)
-    _check(lib.lobpcg_k_rayleigh_ritz(n, m, _ptr(S), _ptr(A), drop_tol, _ptr(theta), _ptr(C), _ptr(nd),
-                                      _stream_handle(stream)), None, kernels=True)
+    fn = lib.lobpcg_k_rayleigh_ritz_df32 if df32 else lib.lobpcg_k_rayleigh_ritz
+    _check(fn(n, m, _ptr(S), _ptr(A), drop_tol, _ptr(theta), _ptr(C), _ptr(nd), _stream_handle(stream)), None,
+           kernels=True)
     return theta, C, nd
 
 

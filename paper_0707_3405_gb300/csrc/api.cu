@@ -881,6 +881,7 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     sv.nblk = M / sv.m;
     sv.mixed = c->opt.precision == LOBPCG_MIXED;
     sv.df = c->opt.fp64_gemm == 2 || (c->opt.fp64_gemm == 0 && sv.mixed);
+    L.ew.df = sv.df;  // the Rayleigh-Ritz step's FP64-unit-bound parts likewise
     sv.X = X;
     sv.s = L.stream;
     sv.drop_tol = 1e-12;

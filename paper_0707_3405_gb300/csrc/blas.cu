@@ -168,12 +168,12 @@ __device__ __forceinline__ void df_norm(float &h, float &l) {
     h = t;
 }
 
-template <bool CA, bool CB>
+template <bool CA, bool CB, int T>
 __global__ void __launch_bounds__(TH)
 k_gemm_df(int m, int n, int K, int kchunk, double alpha, const z64 *__restrict__ A, int lda,
           const z64 *__restrict__ B, int ldb, double beta, const z64 *C, int ldc, z64 *D, int ldd,
           z64 *__restrict__ part, int lower) {
-    constexpr int T = 4, BM = 16 * T, BN = 16 * T;
+    constexpr int BM = 16 * T, BN = 16 * T;
     __shared__ dfc As[BK][BM + 1];
     __shared__ dfc Bs[BK][BN + 1];
     const int tid = threadIdx.x;
@@ -312,8 +312,8 @@ int launch_gemm_t(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int
     nsplit = K > 0 ? (K + kchunk - 1) / kchunk : 1;
     auto kern = [&](dim3 grid, z64 *part) {
         if constexpr (DF)
-            k_gemm_df<CA, CB><<<grid, TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd,
-                                                  part, lower ? 1 : 0);
+            k_gemm_df<CA, CB, T><<<grid, TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd,
+                                                     part, lower ? 1 : 0);
         else
             k_gemm<R, CA, CB, T><<<grid, TH, 0, s>>>(m, n, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd,
                                                      part, lower ? 1 : 0);
@@ -337,6 +337,15 @@ template <typename R, bool CA, bool CB>
 int launch_gemm(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
                 R beta, const cx<R> *C, int ldc, cx<R> *D, int ldd, cudaStream_t s, bool allow_split,
                 bool lower = false) {
+    if constexpr (std::is_same<R, double>::value) {
+        if (w && w->df) {  // double-FP32 arithmetic, same tiles and split
+            if ((long long)m * n <= 512LL * 512LL && K <= 8192)
+                return launch_gemm_t<R, CA, CB, 2, true>(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s,
+                                                         allow_split, 2 * BK, lower);
+            return launch_gemm_t<R, CA, CB, 4, true>(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s,
+                                                     allow_split, 4 * BK, lower);
+        }
+    }
     // tall-skinny and large products: 64 x 64 tiles; small dense ones: 32 x 32 tiles + fine split
     if ((long long)m * n <= 512LL * 512LL && K <= 8192)
         return launch_gemm_t<R, CA, CB, 2>(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s, allow_split,

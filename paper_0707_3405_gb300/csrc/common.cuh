@@ -221,6 +221,7 @@ bool is_device_pointer(const void *p);
 struct GemmWork {
     Allocator *alloc = nullptr;
     DevBuf part;
+    bool df = false;  // complex128 gemm_small in double-FP32 arithmetic
 };
 template <typename R>
 int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
@@ -277,6 +278,9 @@ struct EigWork {
     GemmWork gw;
     CoopGate *gate = nullptr;  // set when several streams may run Rayleigh-Ritz steps at once
     int coop_share = 1;        // >1: cooperative grids use at most 1/coop_share of the resident blocks
+    // FP64 Rayleigh-Ritz: run the parts limited by one SM's FP64 units (Cholesky diagonal
+    // blocks, the tridiagonalisation's column work, the small products) in double-FP32
+    bool df = false;
 };
 // Rayleigh-Ritz: lowest m pairs of A c = theta S c (n x n, ld n). See lobpcg_k_rayleigh_ritz.
 int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,

@@ -93,6 +93,19 @@ int lobpcg_k_rayleigh_ritz(int n, int m, const void *S, const void *A, double dr
                          theta, static_cast<z64 *>(C), n, ndropped, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int lobpcg_k_rayleigh_ritz_df32(int n, int m, const void *S, const void *A, double drop_tol, double *theta, void *C,
+                                int *ndropped, void *stream) {
+    if (n < 1 || m < 1 || m > n || n > 4096) return fail(LOBPCG_ERR_ARG, "need 1 <= m <= n <= 4096");
+    if (!S || !A || !theta || !C) return fail(LOBPCG_ERR_ARG, "NULL pointer");
+    std::lock_guard<std::mutex> lk(pool_mutex());
+    EigWork &ew = pool().ew;
+    ew.df = true;
+    const int rc = rayleigh_ritz(ew, n, m, static_cast<const z64 *>(S), n, static_cast<const z64 *>(A), n, drop_tol,
+                                 theta, static_cast<z64 *>(C), n, ndropped, reinterpret_cast<cudaStream_t>(stream));
+    ew.df = false;
+    return rc;
+}
+
 int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double drop_tol, float *theta, void *C,
                              int *ndropped, void *stream) {
     if (n < 1 || m < 1 || m > n || n > 4096) return fail(LOBPCG_ERR_ARG, "need 1 <= m <= n <= 4096");

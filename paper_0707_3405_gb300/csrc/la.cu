@@ -19,10 +19,12 @@
 //   5. C = D L^-H Q.
 // Every step runs on the GPU in FP64; no host synchronisation.
 #include "common.cuh"
+#include "df64.cuh"
 
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
 namespace lg {
 
@@ -41,6 +43,13 @@ template <> struct Lim<float> {
     static __device__ __forceinline__ float tiny() { return FLT_MIN; }
     static __device__ __forceinline__ float big() { return FLT_MAX; }
 };
+// double-FP32: 2^-46 covers a few units of the pair's 2^-48 per operation; the range is
+// FP32's, kept well inside it so that the low part does not underflow
+template <> struct Lim<df64> {
+    static __device__ __forceinline__ df64 eps() { return df64(1.4210854715202004e-14f); }
+    static __device__ __forceinline__ df64 tiny() { return df64(7.888609052210118e-31f); }
+    static __device__ __forceinline__ df64 big() { return df64(1.2676506002282294e30f); }
+};
 __device__ __forceinline__ z64 ldcg_cx(const z64 *p) {
     const double2 t = __ldcg(reinterpret_cast<const double2 *>(p));
     return mkc(t.x, t.y);
@@ -48,6 +57,27 @@ __device__ __forceinline__ z64 ldcg_cx(const z64 *p) {
 __device__ __forceinline__ c32 ldcg_cx(const c32 *p) {
     const float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
     return mkc(t.x, t.y);
+}
+__device__ __forceinline__ cx<df64> ldcg_cx(const cx<df64> *p) {
+    const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+    return mkc(df64(t.x, t.y), df64(t.z, t.w));
+}
+// Load a complex stored as cx<PT> into the compute type CT.
+template <typename CT, typename PT>
+__device__ __forceinline__ cx<CT> ld_as(const cx<PT> *p) {
+    if constexpr (std::is_same<CT, PT>::value) return *p;
+    else return mkc<CT>((CT)p->x, (CT)p->y);
+}
+template <typename CT, typename PT>
+__device__ __forceinline__ cx<CT> ldcg_as(const cx<PT> *p) {
+    const cx<PT> v = ldcg_cx(p);
+    if constexpr (std::is_same<CT, PT>::value) return v;
+    else return mkc<CT>((CT)v.x, (CT)v.y);
+}
+template <typename PT, typename CT>
+__device__ __forceinline__ cx<PT> as_store(cx<CT> v) {
+    if constexpr (std::is_same<CT, PT>::value) return v;
+    else return mkc<PT>((PT)v.x, (PT)v.y);
 }
 
 
@@ -98,33 +128,35 @@ __global__ void k_scale_gram(int n, const cx<RT> *__restrict__ S, int lds, const
 // ------------------------------------------------------------------ Cholesky with dropping
 // Factor the kb x kb diagonal block at k0 (already updated by earlier panels),
 // write L_kk over it and its inverse into Linv.
-template <typename RT>
+// CT: compute type (double-FP32 where one SM's FP64 units would be the limit).
+template <typename RT, typename CT = RT>
 __global__ void __launch_bounds__(256)
-k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ Linv, RT drop_tol,
+k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ Linv, RT drop_tol_in,
             int *__restrict__ dropped, int *__restrict__ ndrop) {
-    __shared__ cx<RT> T[NBK][NBK + 1];
-    __shared__ cx<RT> I[NBK][NBK + 1];
+    __shared__ cx<CT> T[NBK][NBK + 1];
+    __shared__ cx<CT> I[NBK][NBK + 1];
     __shared__ int dflag[NBK];
+    const CT drop_tol = (CT)drop_tol_in;
     const int tid = threadIdx.x;
     for (int e = tid; e < NBK * NBK; e += blockDim.x) {
         const int r = e % NBK, c = e / NBK;
-        cx<RT> v = mkc<RT>(0.0, 0.0);
-        if (r < kb && c < kb && r >= c) v = L[(size_t)(k0 + c) * n + k0 + r];
+        cx<CT> v = mkc<CT>(0.0, 0.0);
+        if (r < kb && c < kb && r >= c) v = ld_as<CT>(L + (size_t)(k0 + c) * n + k0 + r);
         T[r][c] = v;
-        I[r][c] = mkc<RT>(0.0, 0.0);
+        I[r][c] = mkc<CT>(0.0, 0.0);
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
-        const RT p = T[j][j].x;
+        const CT p = T[j][j].x;
         const bool drop = !(p > drop_tol);
         __syncthreads();
         if (drop) {
-            for (int r = j + 1 + tid; r < kb; r += blockDim.x) T[r][j] = mkc<RT>(0.0, 0.0);
-            if (tid == 0) { T[j][j] = mkc<RT>(1.0, 0.0); dflag[j] = 1; }
+            for (int r = j + 1 + tid; r < kb; r += blockDim.x) T[r][j] = mkc<CT>(0.0, 0.0);
+            if (tid == 0) { T[j][j] = mkc<CT>(1.0, 0.0); dflag[j] = 1; }
         } else {
-            const RT rt = sqrt(p), inv = 1.0 / rt;
+            const CT rt = sqrt(p), inv = (CT)1.0 / rt;
             for (int r = j + 1 + tid; r < kb; r += blockDim.x) T[r][j] = inv * T[r][j];
-            if (tid == 0) { T[j][j] = mkc<RT>(rt, 0.0); dflag[j] = 0; }
+            if (tid == 0) { T[j][j] = mkc<CT>(rt, 0.0); dflag[j] = 0; }
         }
         __syncthreads();
         if (!drop) {
@@ -139,7 +171,7 @@ k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ 
     // clear the rows of dropped columns inside the block
     for (int e = tid; e < kb * kb; e += blockDim.x) {
         const int r = e % kb, c = e / kb;
-        if (c < r && dflag[r]) T[r][c] = mkc<RT>(0.0, 0.0);
+        if (c < r && dflag[r]) T[r][c] = mkc<CT>(0.0, 0.0);
     }
     __syncthreads();
     // inverse of the lower-triangular block (real positive diagonal), row by row:
@@ -147,18 +179,18 @@ k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ 
     for (int r = 0; r < kb; ++r) {
         if (tid < r) {
             const int c = tid;
-            cx<RT> s = mkc<RT>(0.0, 0.0);
+            cx<CT> s = mkc<CT>(0.0, 0.0);
             for (int l = c; l < r; ++l) s = s + T[r][l] * I[l][c];
-            I[r][c] = (RT)(-1.0 / T[r][r].x) * s;
+            I[r][c] = ((CT)(-1.0) / T[r][r].x) * s;
         } else if (tid == r) {
-            I[r][r] = mkc<RT>(1.0 / T[r][r].x, 0.0);
+            I[r][r] = mkc<CT>((CT)1.0 / T[r][r].x, 0.0);
         }
         __syncthreads();
     }
     for (int e = tid; e < kb * kb; e += blockDim.x) {
         const int r = e % kb, c = e / kb;
-        L[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? T[r][c] : mkc<RT>(0.0, 0.0);
-        Linv[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? I[r][c] : mkc<RT>(0.0, 0.0);
+        L[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? as_store<RT>(T[r][c]) : mkc<RT>(0.0, 0.0);
+        Linv[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? as_store<RT>(I[r][c]) : mkc<RT>(0.0, 0.0);
     }
     if (tid < kb) {
         dropped[k0 + tid] = dflag[tid];
@@ -247,12 +279,12 @@ struct Refl {
     cx<RT> scal;  // v[r] = x[r] * scal for r >= 1
 };
 
-template <typename RT, bool CG = false>
-__device__ Refl<RT> make_reflector(const cx<RT> *__restrict__ col, int L, RT *sh) {
+template <typename RT, bool CG = false, typename PT = RT>
+__device__ Refl<RT> make_reflector(const cx<PT> *__restrict__ col, int L, RT *sh) {
     RT s = 0.0;
-    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(CG ? ldcg_cx(col + r) : col[r]);
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(CG ? ldcg_as<RT>(col + r) : ld_as<RT>(col + r));
     s = block_sum(s, sh);
-    const cx<RT> alpha = CG ? ldcg_cx(col) : col[0];
+    const cx<RT> alpha = CG ? ldcg_as<RT>(col) : ld_as<RT>(col);
     Refl<RT> R;
     if (s == 0.0 && alpha.y == 0.0) {
         R.tau = mkc<RT>(0.0, 0.0);
@@ -509,45 +541,48 @@ k_tri_coop(int n, cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<R
 // over more SMs (this GPU has few FP64 units per SM).  256 threads: TS rows x (256 / TS)
 // column groups of CPT = TS*TS/256 columns.  Dynamic shared memory: the owned tiles, then
 // v_i, w_i, v_{i+1} and the working column (n complex each).
-template <typename RT, int TS>
+template <typename RT, int TS, typename CT = RT>
 __global__ void __launch_bounds__(256)
 k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<RT> *__restrict__ taus,
-            RT *__restrict__ dg, RT *__restrict__ eg, cx<RT> *__restrict__ ypart, cx<RT> *__restrict__ colbuf,
+            RT *__restrict__ dg, RT *__restrict__ eg, cx<RT> *__restrict__ ypart_st, cx<RT> *__restrict__ colbuf_st,
             unsigned int *bar, int *err) {
+    static_assert(sizeof(cx<CT>) == sizeof(cx<RT>), "the compute type keeps the storage size");
+    cx<CT> *ypart = reinterpret_cast<cx<CT> *>(ypart_st);   // scratch kept in the compute type
+    cx<CT> *colbuf = reinterpret_cast<cx<CT> *>(colbuf_st);
     constexpr int TT = TS * TS, NG = 256 / TS, CPT = TT / 256;
     extern __shared__ __align__(16) unsigned char dsm[];
     const int T = (n + TS - 1) / TS, G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const int nown = (T * T - g + G - 1) / G;  // tiles g, g+G, ... below T*T
-    cx<RT> *tiles = reinterpret_cast<cx<RT> *>(dsm);  // nown x [TS cols][TS rows]
-    cx<RT> *v = tiles + (size_t)nown * TT;             // v_i on [0, n)
-    cx<RT> *w = v + n;                                  // w_i
-    cx<RT> *vn = w + n;                                 // v_{i+1}
-    cx<RT> *x = vn + n;                                 // working column
-    __shared__ RT sh[32];
-    __shared__ cx<RT> acc[NG][TS + 1];
+    cx<CT> *tiles = reinterpret_cast<cx<CT> *>(dsm);  // nown x [TS cols][TS rows]
+    cx<CT> *v = tiles + (size_t)nown * TT;             // v_i on [0, n)
+    cx<CT> *w = v + n;                                  // w_i
+    cx<CT> *vn = w + n;                                 // v_{i+1}
+    cx<CT> *x = vn + n;                                 // working column
+    __shared__ CT sh[32];
+    __shared__ cx<CT> acc[NG][TS + 1];
     const int rl = tid % TS, cg = tid / TS;
-    const cx<RT> zero = mkc<RT>(0.0, 0.0);
+    const cx<CT> zero = mkc<CT>(0.0, 0.0);
     unsigned int arrivals = 0;
     // load the owned tiles (entries outside the matrix are zero)
     for (int q = 0; q < nown; ++q) {
         const int t = g + q * G, TR = t / T, TC = t % T;
         for (int e = tid; e < TT; e += blockDim.x) {
             const int r = TR * TS + (e % TS), c = TC * TS + (e / TS);
-            tiles[(size_t)q * TT + e] = (r < n && c < n) ? A[(size_t)c * lda + r] : zero;
+            tiles[(size_t)q * TT + e] = (r < n && c < n) ? ld_as<CT>(A + (size_t)c * lda + r) : zero;
         }
     }
     // reflector 0 from column 0 (read from A, unmodified), d[0]
-    Refl<RT> R = make_reflector<RT>(A + 1, n - 1, sh);
+    Refl<CT> R = make_reflector<CT, false, RT>(A + 1, n - 1, sh);
     for (int r = tid; r < n; r += blockDim.x)
-        v[r] = (r < 1) ? zero : (r == 1 ? mkc<RT>(1.0, 0.0) : A[r] * R.scal);
+        v[r] = (r < 1) ? zero : (r == 1 ? mkc<CT>(1.0, 0.0) : ld_as<CT>(A + r) * R.scal);
     if (g == 0 && tid == 0) dg[0] = A[0].x;
     __syncthreads();
     // partial products A^(0)[J,J] v_0 and column 1 of A^(0)
     for (int q = 0; q < nown; ++q) {
         const int t = g + q * G, TR = t / T, TC = t % T;
-        const cx<RT> *tl = tiles + (size_t)q * TT;
+        const cx<CT> *tl = tiles + (size_t)q * TT;
         const int r = TR * TS + rl;
-        cx<RT> sacc = zero;
+        cx<CT> sacc = zero;
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
             const int cl = cg * CPT + k, c = TC * TS + cl;
@@ -556,7 +591,7 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
         acc[cg][rl] = sacc;
         __syncthreads();
         if (tid < TS) {
-            cx<RT> u = acc[0][tid];
+            cx<CT> u = acc[0][tid];
             for (int k = 1; k < NG; ++k) u = u + acc[k][tid];
             const int rr = TR * TS + tid;
             if (rr < n) ypart[(size_t)TC * n + rr] = u;
@@ -569,14 +604,14 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
 
     for (int i = 0; i + 1 < n; ++i) {
         const int par = i & 1;
-        const cx<RT> *yp = ypart + (size_t)par * T * n;
-        const cx<RT> *cb = colbuf + (size_t)par * n;
+        const cx<CT> *yp = ypart + (size_t)par * T * n;
+        const cx<CT> *cb = colbuf + (size_t)par * n;
         // (a) y_i and w_i on J = [i+1, n); loads issued in groups of 8 before they are summed
-        RT dre = 0.0;
+        CT dre = 0.0;
         for (int r = i + 1 + tid; r < n; r += blockDim.x) {
-            cx<RT> y = zero;
+            cx<CT> y = zero;
             for (int c = 0; c < T; c += 8) {
-                cx<RT> t8[8];
+                cx<CT> t8[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) t8[k] = (c + k < T) ? ldcg_cx(yp + (size_t)(c + k) * n + r) : zero;
 #pragma unroll
@@ -587,34 +622,34 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
             w[r] = y;
         }
         dre = block_sum(dre, sh);
-        const RT t2 = 0.5 * abs2(R.tau) * dre;
+        const CT t2 = (CT)0.5 * abs2(R.tau) * dre;
         for (int r = i + 1 + tid; r < n; r += blockDim.x) w[r] = R.tau * w[r] - t2 * v[r];
         __syncthreads();
         // (b) column i+1 of A^(i+1) from row i+1; d[i+1]; reflector i+1
-        const cx<RT> vi1 = v[i + 1], wi1 = w[i + 1];
+        const cx<CT> vi1 = v[i + 1], wi1 = w[i + 1];
         for (int r = i + 1 + tid; r < n; r += blockDim.x)
             x[r] = ldcg_cx(cb + r) - mul_conj(w[r], vi1) - mul_conj(v[r], wi1);
         __syncthreads();
         if (g == 0) {
-            for (int r = i + 1 + tid; r < n; r += blockDim.x) Hv[(size_t)i * n + r] = v[r];
+            for (int r = i + 1 + tid; r < n; r += blockDim.x) Hv[(size_t)i * n + r] = as_store<RT>(v[r]);
             if (tid == 0) {
-                taus[i] = R.tau;
-                eg[i] = R.beta;
-                dg[i + 1] = x[i + 1].x;
+                taus[i] = as_store<RT>(R.tau);
+                eg[i] = (RT)R.beta;
+                dg[i + 1] = (RT)x[i + 1].x;
             }
         }
         if (i + 2 >= n) break;  // last column: nothing left to transform
-        const Refl<RT> Rn = make_reflector<RT>(x + i + 2, n - i - 2, sh);
+        const Refl<CT> Rn = make_reflector<CT>(x + i + 2, n - i - 2, sh);
         for (int r = tid; r < n; r += blockDim.x)
-            vn[r] = (r < i + 2) ? zero : (r == i + 2 ? mkc<RT>(1.0, 0.0) : x[r] * Rn.scal);
+            vn[r] = (r < i + 2) ? zero : (r == i + 2 ? mkc<CT>(1.0, 0.0) : x[r] * Rn.scal);
         __syncthreads();
         // (c) update the owned tiles with (w_i, v_i) and multiply by v_{i+1}; (d) publish column i+2
-        cx<RT> *ypn = ypart + (size_t)(1 - par) * T * n;
-        cx<RT> *cbn = colbuf + (size_t)(1 - par) * n;
+        cx<CT> *ypn = ypart + (size_t)(1 - par) * T * n;
+        cx<CT> *cbn = colbuf + (size_t)(1 - par) * n;
         const int c2 = i + 2;
         for (int q = 0; q < nown; ++q) {
             const int t = g + q * G, TR = t / T, TC = t % T;
-            cx<RT> *tl = tiles + (size_t)q * TT;
+            cx<CT> *tl = tiles + (size_t)q * TT;
             if (TR * TS + TS - 1 < i + 1 || TC * TS + TS - 1 < i + 1) {
                 // tile outside J x J: its share of y_{i+1} is zero (uniform branch)
                 if (tid < TS) {
@@ -625,13 +660,13 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
             }
             const int r = TR * TS + rl;
             const bool rin = r >= i + 1 && r < n;
-            const cx<RT> wr = rin ? w[r] : zero, vr = rin ? v[r] : zero;
-            cx<RT> sacc = zero;
+            const cx<CT> wr = rin ? w[r] : zero, vr = rin ? v[r] : zero;
+            cx<CT> sacc = zero;
 #pragma unroll
             for (int k = 0; k < CPT; ++k) {
                 const int cl = cg * CPT + k, c = TC * TS + cl;
                 if (rin && c >= i + 1 && c < n) {
-                    cx<RT> a = tl[cl * TS + rl];
+                    cx<CT> a = tl[cl * TS + rl];
                     a = a - mul_conj(wr, v[c]) - mul_conj(vr, w[c]);
                     tl[cl * TS + rl] = a;
                     if (r >= c2 && c >= c2) sacc = sacc + a * vn[c];
@@ -640,7 +675,7 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
             acc[cg][rl] = sacc;
             __syncthreads();
             if (tid < TS) {
-                cx<RT> u = acc[0][tid];
+                cx<CT> u = acc[0][tid];
                 for (int k = 1; k < NG; ++k) u = u + acc[k][tid];
                 const int rr = TR * TS + tid;
                 if (rr < n) ypn[(size_t)TC * n + rr] = u;
@@ -691,7 +726,7 @@ __device__ void tri_bounds(const RT *__restrict__ d, const RT *__restrict__ e, i
         hi = fmax(hi, d[i] + r);
     }
     tnorm = fmax(fabs(lo), fabs(hi));
-    pivmin = Lim<RT>::tiny() * fmax(1.0, emax2);
+    pivmin = Lim<RT>::tiny() * fmax((RT)1.0, emax2);
     const RT pad = 2.0 * Lim<RT>::eps() * tnorm * n + 2.0 * pivmin;
     lo -= pad;
     hi += pad;
@@ -934,6 +969,10 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
         const size_t static_sm = sizeof(RT) * 32 + sizeof(cx<RT>) * 16 * 33 + 64;
         int *err = device_wait_flag();
         const void *fn = small_tiles ? (const void *)k_tri_fused<RT, 16> : (const void *)k_tri_fused<RT, 32>;
+        if constexpr (std::is_same<RT, double>::value) {
+            if (w.df)  // the column's vector work in double-FP32 (this GPU has few FP64 units per SM)
+                fn = small_tiles ? (const void *)k_tri_fused<RT, 16, df64> : (const void *)k_tri_fused<RT, 32, df64>;
+        }
         if (coop && err && dsm + static_sm <= (size_t)smem_max) {
             LG_TRY(allow_max_dyn_smem(fn));
             int per_sm = 0;
@@ -1052,6 +1091,7 @@ int rayleigh_ritz_t(EigWork &w, int n, int m, const cx<RT> *S, int lds, const cx
     int *dr = reinterpret_cast<int *>(base + o_dr);
     int *nd = reinterpret_cast<int *>(base + o_nd);
 
+    w.gw.df = std::is_same<RT, double>::value && w.df;  // the small products below
     LG_CUDA_TRY(cudaMemsetAsync(nd, 0, sizeof(int), s));
     LG_CUDA_TRY(cudaMemsetAsync(Li, 0, sizeof(cx<RT>) * (size_t)n * n, s));
     k_scale_gram<RT><<<dim3((n + 127) / 128, n), 128, 0, s>>>(n, S, lds, A, lda, Ss, As, d);
@@ -1059,7 +1099,14 @@ int rayleigh_ritz_t(EigWork &w, int n, int m, const cx<RT> *S, int lds, const cx
     // blocked Cholesky with dropping (L overwrites Ss)
     for (int k0 = 0; k0 < n; k0 += NBK) {
         const int kb = std::min(NBK, n - k0);
-        k_chol_diag<RT><<<1, 256, 0, s>>>(n, k0, kb, Ss, Li, (RT)drop_tol, dr, nd);
+        bool chol_done = false;
+        if constexpr (std::is_same<RT, double>::value) {
+            if (w.df) {  // one block: double-FP32 instead of that SM's FP64 units
+                k_chol_diag<RT, df64><<<1, 256, 0, s>>>(n, k0, kb, Ss, Li, (RT)drop_tol, dr, nd);
+                chol_done = true;
+            }
+        }
+        if (!chol_done) k_chol_diag<RT><<<1, 256, 0, s>>>(n, k0, kb, Ss, Li, (RT)drop_tol, dr, nd);
         LG_TRY(check_launch("cholesky diag"));
         const int rem = n - k0 - kb;
         if (rem > 0) {

@@ -235,7 +235,10 @@ def test_heev_degenerate_clusters():
 
 
 @pytest.mark.parametrize("n,m", [(3, 1), (48, 16), (192, 64), (384, 128)])
-def test_rayleigh_ritz_generalized(n, m):
+@pytest.mark.parametrize("df32", [False, True])
+def test_rayleigh_ritz_generalized(n, m, df32):
+    """FP64 Rayleigh-Ritz against scipy's generalized eigh; df32 = the double-FP32 variant
+    (Cholesky diagonal blocks, tridiagonalisation column work, small products), same bounds."""
     import torch
     import paper_0707_3405_gb300 as lg
     rng = np.random.default_rng(n + m)
@@ -243,7 +246,8 @@ def test_rayleigh_ritz_generalized(n, m):
     H = _herm(rng, 4 * n)
     S = Z.conj().T @ Z
     A = Z.conj().T @ H @ Z
-    theta, C, nd = lg.rayleigh_ritz(torch.tensor(S.T.copy(), device="cuda"), torch.tensor(A.T.copy(), device="cuda"), m)
+    theta, C, nd = lg.rayleigh_ritz(torch.tensor(S.T.copy(), device="cuda"), torch.tensor(A.T.copy(), device="cuda"), m,
+                                    df32=df32)
     theta = theta.cpu().numpy()
     C = C.cpu().numpy().T
     ref = scipy.linalg.eigh(A, S, eigvals_only=True)[:m]
@@ -268,6 +272,13 @@ def test_rayleigh_ritz_drops_dependent_columns():
     A = Z.conj().T @ H @ Z
     keep = [0, 1, 2, 3, 4, 5, 8, 9, 10]
     ref = scipy.linalg.eigh(A[np.ix_(keep, keep)], S[np.ix_(keep, keep)], eigvals_only=True)[:4]
+    for df32 in (False, True):
+        theta, C, nd = lg.rayleigh_ritz(torch.tensor(S.T.copy(), device="cuda"),
+                                        torch.tensor(A.T.copy(), device="cuda"), 4, drop_tol=1e-10, df32=df32)
+        assert int(nd.item()) == 2
+        assert np.abs(theta.cpu().numpy() - ref).max() < 1e-8 * np.abs(ref).max()
+        Cn = C.cpu().numpy().T
+        assert np.abs(Cn[[6, 7]]).max() < 1e-12 * np.abs(Cn).max()
     theta, C, nd = lg.rayleigh_ritz(torch.tensor(S.T.copy(), device="cuda"), torch.tensor(A.T.copy(), device="cuda"),
                                     4, drop_tol=1e-10)
     assert int(nd.item()) == 2
