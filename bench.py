@@ -383,16 +383,17 @@ def main():
 
     # standalone apply_H throughput on all bands
     applyh = {}
-    for dt, name in ((torch.complex128, "c128"), (torch.complex64, "c64")):
+    for dt, name, df in ((torch.complex128, "c128", False), (torch.complex64, "c64", False),
+                         (torch.complex128, "c128_df32", True)):
         Xa = X0.to(dt)
         Ya = torch.empty_like(Xa)
         for _ in range(2):
-            s.apply_H(0, Xa, Ya)
+            s.apply_H(0, Xa, Ya, df32=df)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         reps = 3
         for _ in range(reps):
-            s.apply_H(0, Xa, Ya)
+            s.apply_H(0, Xa, Ya, df32=df)
         a1.record(stream)
         torch.cuda.synchronize()
         applyh[f"{name}_band_applies_per_s"] = reps * w.nbands / (a0.elapsed_time(a1) / 1e3)

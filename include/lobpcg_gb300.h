@@ -72,6 +72,10 @@ extern "C" {
 /* Arithmetic of lobpcg_apply_H (element type of X and Y, and compute precision). */
 #define LOBPCG_C128 0               /* complex128 in/out, FP64 FFT and GEMMs */
 #define LOBPCG_C64  1               /* complex64  in/out, FP32 FFT and GEMMs */
+#define LOBPCG_C128_DF32 2          /* complex128 in/out, FFT and GEMMs in double-FP32 arithmetic:
+                                       pairs of FP32 numbers, error-free TwoSum / TwoProd steps,
+                                       about 2^-47 relative per operation (FP64 class) at several
+                                       times this GPU's FP64 rate */
 
 /* Precision schedule of lobpcg_solve (lobpcg_options.precision). */
 #define LOBPCG_FP64  0              /* every step in FP64 */
@@ -192,7 +196,8 @@ int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller);
 /*
  * Y = H X for nb bands of k-point k (Sec. 2.2 items iii and iv).
  *   X, Y       npw_k x nb, column-major (ld = npw_k), complex128 when
- *              precision = LOBPCG_C128 or complex64 when LOBPCG_C64.  Device
+ *              precision = LOBPCG_C128 or LOBPCG_C128_DF32, complex64 when
+ *              LOBPCG_C64.  Device
  *              pointers run fully asynchronously on the handle's stream; host
  *              pointers are staged through device buffers and the call returns
  *              after Y has been written back (synchronous).  X and Y must not

@@ -10,7 +10,7 @@
  *   - Matrices are column-major with a leading dimension (elements).
  *   - Complex numbers are interleaved (re, im); prec = LOBPCG_C128 selects
  *     complex128 with FP64 arithmetic, LOBPCG_C64 complex64 with FP32, and
- *     (GEMMs only) LOBPCG_C128_DF32 complex128 with double-FP32 arithmetic:
+ *     (GEMMs) LOBPCG_C128_DF32 complex128 with double-FP32 arithmetic:
  *     every operand split into two FP32 parts, exact FP32 products by FMA
  *     (Dekker's TwoProd) and pair accumulators (Knuth's TwoSum), about 2^-47
  *     relative per product, run on the FP32 units (FP64 class, several
@@ -28,7 +28,6 @@
 
 #include "lobpcg_gb300.h"
 
-#define LOBPCG_C128_DF32 2   /* complex128 in/out, double-FP32 arithmetic (GEMMs only) */
 
 #ifdef __cplusplus
 extern "C" {

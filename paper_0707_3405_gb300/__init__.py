@@ -248,10 +248,10 @@ class Solver:
         colmajor = np.ascontiguousarray(b.T)
         _check(self._lib.lobpcg_set_projectors(self.handle, k, colmajor.ctypes.data), self.handle)
 
-    def apply_H(self, k: int, X, Y=None):
+    def apply_H(self, k: int, X, Y=None, df32: bool = False):
         """Y = H X for a (nb, npw) block: torch CUDA tensor (asynchronous on the
         handle's stream) or numpy array (staged, synchronous).  complex128 runs
-        in FP64, complex64 in FP32."""
+        in FP64 (or double-FP32 with df32=True), complex64 in FP32."""
         import torch
         if isinstance(X, np.ndarray):
             prec = C128 if X.dtype == np.complex128 else C64
@@ -271,6 +271,10 @@ class Solver:
         nb = 0 if X.shape[0] == 0 else int(X.shape[0])
         if nb and X.shape[-1] != self.npw(k):
             raise ValueError("X must have shape (nb, npw_k)")
+        if df32:
+            if prec != C128:
+                raise ValueError("df32 needs complex128 vectors")
+            prec = C128_DF32
         _check(self._lib.lobpcg_apply_H(self.handle, k, _ptr(X), _ptr(Y), nb, prec), self.handle)
         return Y
 

@@ -347,9 +347,9 @@ int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y
         // kinetic table, half-box written / read-written / read (4 Px N^2), V once per batch
         const double by = nb * (3.0 * cb * K.npw + sizeof(R) * (double)K.npw + 4.0 * per_band) +
                           std::ceil((double)nb / nbatch) * sizeof(R) * (double)g.N * g.N * g.N;
-        PhaseScope ps(prof, LOBPCG_PH_FFT, nb * fft_flops_per_band(g), by, f64);
+        PhaseScope ps(prof, LOBPCG_PH_FFT, nb * fft_flops_per_band(g), by, f64 && !df);
         LG_TRY(fft_vloc_apply<R>(g, c->plan, X, ldx, Y, ldy, nb, Tables<R>::kin(K), Tables<R>::vt(c),
-                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(L.T2.p), nbatch, L.stream));
+                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(L.T2.p), nbatch, L.stream, df));
     }
     if (c->nproj > 0) {
         if (!K.has_beta) return fail(LOBPCG_ERR_ARG, "projectors of this k-point were not given");
@@ -1170,9 +1170,10 @@ static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int 
     if (nb < 0) return fail(LOBPCG_ERR_ARG, "nb must be >= 0");
     if (nb == 0) return LOBPCG_OK;
     if (!X || !Y) return fail(LOBPCG_ERR_ARG, "X and Y must not be NULL");
-    if (precision != LOBPCG_C128 && precision != LOBPCG_C64) return fail(LOBPCG_ERR_ARG, "unknown precision");
+    if (precision != LOBPCG_C128 && precision != LOBPCG_C64 && precision != LOBPCG_C128_DF32)
+        return fail(LOBPCG_ERR_ARG, "unknown precision");
     const int npw = c->kp[k].npw;
-    const size_t esz = precision == LOBPCG_C128 ? sizeof(z64) : sizeof(c32);
+    const size_t esz = precision == LOBPCG_C64 ? sizeof(c32) : sizeof(z64);
     const size_t bytes = esz * (size_t)npw * nb;
     const char *xa = static_cast<const char *>(X), *ya = static_cast<const char *>(Y);
     if (xa < ya + bytes && ya < xa + bytes) return fail(LOBPCG_ERR_ARG, "X and Y overlap");
@@ -1189,8 +1190,9 @@ static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int 
         LG_TRY(c->alloc.ensure(L.stageY, bytes));
         Yd = L.stageY.p;
     }
-    if (precision == LOBPCG_C128)
-        LG_TRY(apply_H_dev<double>(c, L, k, static_cast<const z64 *>(Xd), npw, static_cast<z64 *>(Yd), npw, nb));
+    if (precision != LOBPCG_C64)
+        LG_TRY(apply_H_dev<double>(c, L, k, static_cast<const z64 *>(Xd), npw, static_cast<z64 *>(Yd), npw, nb,
+                                   nullptr, precision == LOBPCG_C128_DF32));
     else
         LG_TRY(apply_H_dev<float>(c, L, k, static_cast<const c32 *>(Xd), npw, static_cast<c32 *>(Yd), npw, nb));
     if (!dy) {

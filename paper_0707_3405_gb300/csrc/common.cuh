@@ -178,10 +178,12 @@ bool make_fft_plan(int N, FFTPlan &plan);
 //         FP32 register variant)
 //   tw:   device twiddles e^{-2 pi i t / N}, t < N
 //   T2:   scratch of at least nbatch * Px * N * N cx<R>
+//   df:   complex128 only: transform in double-FP32 arithmetic (FP32 pairs, ~2^-48 per
+//         operation) instead of FP64
 template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy,
                    int nb, const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch,
-                   cudaStream_t s);
+                   cudaStream_t s, bool df = false);
 // FP32 register-resident variant of the three passes for the grid edges it is
 // compiled for (8, 12, 16, 20, 24, 36, 48, 64, 72, 96, 120, 128, 160).  Its scratch is laid out T2[b][px][y][z]
 // and its potential table vt as [y][x][z] (pre-scaled by 1/N^3);

@@ -20,6 +20,7 @@
 // and writes its outputs after it.  Twiddles e^{-2 pi i t/N} come from a
 // host-computed FP64 table (rounded to the compute precision).
 #include "common.cuh"
+#include "df64.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -46,8 +47,8 @@ bool make_fft_plan(int N, FFTPlan &p) {
 namespace {
 
 template <typename R>
-__device__ __forceinline__ cx<R> mul_isg(cx<R> a, R sg) {  // a * (i * sg)
-    return mkc<R>(-sg * a.y, sg * a.x);
+__device__ __forceinline__ cx<R> mul_isg(cx<R> a, int sg) {  // a * (i * sg), sg = +-1
+    return sg > 0 ? mkc<R>(-a.y, a.x) : mkc<R>(a.y, -a.x);
 }
 
 template <typename R, int RDX>
@@ -55,7 +56,7 @@ struct DFT;
 
 template <typename R>
 struct DFT<R, 2> {
-    static __device__ __forceinline__ void run(cx<R> *v, R) {
+    static __device__ __forceinline__ void run(cx<R> *v, int) {
         cx<R> a = v[0], b = v[1];
         v[0] = a + b;
         v[1] = a - b;
@@ -64,7 +65,7 @@ struct DFT<R, 2> {
 
 template <typename R>
 struct DFT<R, 3> {
-    static __device__ __forceinline__ void run(cx<R> *v, R sg) {
+    static __device__ __forceinline__ void run(cx<R> *v, int sg) {
         const R s3 = (R)0.86602540378443864676;  // sin(2 pi / 3)
         cx<R> a = v[0], t1 = v[1] + v[2];
         cx<R> t2 = a - (R)0.5 * t1;
@@ -77,7 +78,7 @@ struct DFT<R, 3> {
 
 template <typename R>
 struct DFT<R, 4> {
-    static __device__ __forceinline__ void run(cx<R> *v, R sg) {
+    static __device__ __forceinline__ void run(cx<R> *v, int sg) {
         cx<R> t0 = v[0] + v[2], t1 = v[0] - v[2];
         cx<R> t2 = v[1] + v[3], t3 = mul_isg(v[1] - v[3], sg);
         v[0] = t0 + t2;
@@ -89,7 +90,7 @@ struct DFT<R, 4> {
 
 template <typename R>
 struct DFT<R, 5> {
-    static __device__ __forceinline__ void run(cx<R> *v, R sg) {
+    static __device__ __forceinline__ void run(cx<R> *v, int sg) {
         const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
         const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
         const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
@@ -111,7 +112,7 @@ struct DFT<R, 5> {
 
 template <typename R>
 struct DFT<R, 8> {
-    static __device__ __forceinline__ void run(cx<R> *v, R sg) {
+    static __device__ __forceinline__ void run(cx<R> *v, int sg) {
         const R h = (R)0.70710678118654752440;  // 1/sqrt(2)
         cx<R> e[4] = {v[0], v[2], v[4], v[6]};
         cx<R> o[4] = {v[1], v[3], v[5], v[7]};
@@ -133,7 +134,7 @@ struct DFT<R, 8> {
 // between the two barriers, so the stage can run in place).
 template <typename R, int RDX, int VPT>
 __device__ __forceinline__ void fft_stage(cx<R> *buf, int nlines, int ls, int es, int N, int Ns,
-                                          const cx<R> *tw, R sg) {
+                                          const cx<R> *tw, int sg) {
     constexpr int NB = (VPT + RDX - 1) / RDX;
     const int bpl = N / RDX;
     const int total = nlines * bpl;
@@ -182,7 +183,7 @@ constexpr int kThreads = 256;
 // In-place FFT of `nlines` lines (line stride ls, element stride es) by the whole block.
 // sg = -1: forward (e^{-i...}); sg = +1: inverse without 1/N.
 template <typename R>
-__device__ void fft_lines(cx<R> *buf, int nlines, int ls, int es, const FFTPlan &plan, const cx<R> *tw, R sg) {
+__device__ void fft_lines(cx<R> *buf, int nlines, int ls, int es, const FFTPlan &plan, const cx<R> *tw, int sg) {
     const int N = plan.N;
     int lpg = (int)(blockDim.x * kVPT) / N;
     if (lpg < 1) lpg = 1;
@@ -204,29 +205,37 @@ __device__ void fft_lines(cx<R> *buf, int nlines, int ls, int es, const FFTPlan 
     }
 }
 
-template <typename R>
+// R: storage type of X, Y, V, T and the twiddles; CT: compute type of the transforms and of
+// the half-box scratch T2 (double-FP32 for FP64 data on a GPU with few FP64 units).
+template <typename CT, typename R>
+__device__ __forceinline__ cx<CT> to_ct(cx<R> v) {
+    if constexpr (std::is_same<CT, R>::value) return v;
+    else return mkc<CT>((CT)v.x, (CT)v.y);
+}
+
+template <typename R, typename CT = R>
 __global__ void __launch_bounds__(kThreads)
-k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<R> *__restrict__ T2, FFTPlan plan, int Px, int Py, int ny0m,
+k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int Py, int ny0m,
          const int *__restrict__ plane_begin, const int2 *__restrict__ yrange, const int *__restrict__ gmap,
          const cx<R> *__restrict__ twg, int zc_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = plan.N;
-    cx<R> *tw = reinterpret_cast<cx<R> *>(smem_raw);
-    cx<R> *A = tw + N;
-    cx<R> *L = A + Py * N;
+    cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
+    cx<CT> *A = tw + N;
+    cx<CT> *L = A + Py * N;
     const int lsL = N + 1;
     const int px = blockIdx.x, b = blockIdx.y;
     const cx<R> *Xb = X + (size_t)b * ldx;
-    const cx<R> zero = mkc<R>(0, 0);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    const cx<CT> zero = mkc<CT>(0, 0);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = to_ct<CT>(twg[i]);
     for (int i = threadIdx.x; i < Py * N; i += blockDim.x) A[i] = zero;
     __syncthreads();
     const int g0 = plane_begin[px], g1 = plane_begin[px + 1];
-    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) A[gmap[g]] = Xb[g];
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) A[gmap[g]] = to_ct<CT>(Xb[g]);
     __syncthreads();
     const int2 yr = yrange[px];
-    fft_lines<R>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, (R)1);
-    cx<R> *out = T2 + ((size_t)b * Px + px) * (size_t)N * N;  // [z][y]
+    fft_lines<CT>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, 1);
+    cx<CT> *out = T2 + ((size_t)b * Px + px) * (size_t)N * N;  // [z][y]
     for (int z0 = 0; z0 < N; z0 += zc_max) {
         const int nz = min(zc_max, N - z0);
         for (int i = threadIdx.x; i < nz * N; i += blockDim.x) {
@@ -236,7 +245,7 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<R> *__restrict__ T2, FFTPlan p
             L[zc * lsL + iy] = (py < Py) ? A[py * N + z0 + zc] : zero;
         }
         __syncthreads();
-        fft_lines<R>(L, nz, lsL, 1, plan, tw, (R)1);
+        fft_lines<CT>(L, nz, lsL, 1, plan, tw, 1);
         for (int i = threadIdx.x; i < nz * N; i += blockDim.x) {
             const int zc = i / N, iy = i - zc * N;
             out[(size_t)(z0 + zc) * N + iy] = L[zc * lsL + iy];
@@ -245,23 +254,23 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<R> *__restrict__ T2, FFTPlan p
     }
 }
 
-template <typename R>
+template <typename R, typename CT = R>
 __global__ void __launch_bounds__(kThreads)
-k_pass_b(cx<R> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__restrict__ vt,
+k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__restrict__ vt,
          const cx<R> *__restrict__ twg, int yc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = plan.N;
-    cx<R> *tw = reinterpret_cast<cx<R> *>(smem_raw);
-    cx<R> *L = tw + N;
+    cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
+    cx<CT> *L = tw + N;
     const int lsL = N + 1;
     const int y0 = blockIdx.x * yc, z = blockIdx.y, b = blockIdx.z;
     const int ny = min(yc, N - y0);
-    const cx<R> zero = mkc<R>(0, 0);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    const cx<CT> zero = mkc<CT>(0, 0);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = to_ct<CT>(twg[i]);
     for (int i = threadIdx.x; i < ny * lsL; i += blockDim.x) L[i] = zero;
     __syncthreads();
     const size_t NN = (size_t)N * N;
-    cx<R> *base = T2 + (size_t)b * Px * NN + (size_t)z * N + y0;
+    cx<CT> *base = T2 + (size_t)b * Px * NN + (size_t)z * N + y0;
     for (int i = threadIdx.x; i < Px * ny; i += blockDim.x) {
         const int px = i / ny, yy = i - px * ny;
         int ix = nx0m + px;
@@ -269,14 +278,14 @@ k_pass_b(cx<R> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__rest
         L[yy * lsL + ix] = base[(size_t)px * NN + yy];
     }
     __syncthreads();
-    fft_lines<R>(L, ny, lsL, 1, plan, tw, (R)1);
+    fft_lines<CT>(L, ny, lsL, 1, plan, tw, 1);
     const R *vz = vt + (size_t)z * NN + y0;
     for (int i = threadIdx.x; i < ny * N; i += blockDim.x) {
         const int ix = i / ny, yy = i - ix * ny;
-        L[yy * lsL + ix] = vz[(size_t)ix * N + yy] * L[yy * lsL + ix];
+        L[yy * lsL + ix] = (CT)vz[(size_t)ix * N + yy] * L[yy * lsL + ix];
     }
     __syncthreads();
-    fft_lines<R>(L, ny, lsL, 1, plan, tw, (R)-1);
+    fft_lines<CT>(L, ny, lsL, 1, plan, tw, -1);
     for (int i = threadIdx.x; i < Px * ny; i += blockDim.x) {
         const int px = i / ny, yy = i - px * ny;
         int ix = nx0m + px;
@@ -285,22 +294,22 @@ k_pass_b(cx<R> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__rest
     }
 }
 
-template <typename R>
+template <typename R, typename CT = R>
 __global__ void __launch_bounds__(kThreads)
-k_pass_c(const cx<R> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx<R> *__restrict__ X, int ldx,
+k_pass_c(const cx<CT> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx<R> *__restrict__ X, int ldx,
          const R *__restrict__ kin, FFTPlan plan, int Px, int Py, int ny0m, const int *__restrict__ plane_begin,
          const int2 *__restrict__ yrange, const int *__restrict__ gmap, const cx<R> *__restrict__ twg,
          int zc_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = plan.N;
-    cx<R> *tw = reinterpret_cast<cx<R> *>(smem_raw);
-    cx<R> *A = tw + N;
-    cx<R> *L = A + Py * N;
+    cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
+    cx<CT> *A = tw + N;
+    cx<CT> *L = A + Py * N;
     const int lsL = N + 1;
     const int px = blockIdx.x, b = blockIdx.y;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = to_ct<CT>(twg[i]);
     __syncthreads();
-    const cx<R> *in = T2 + ((size_t)b * Px + px) * (size_t)N * N;  // [z][y]
+    const cx<CT> *in = T2 + ((size_t)b * Px + px) * (size_t)N * N;  // [z][y]
     for (int z0 = 0; z0 < N; z0 += zc_max) {
         const int nz = min(zc_max, N - z0);
         for (int i = threadIdx.x; i < nz * N; i += blockDim.x) {
@@ -308,7 +317,7 @@ k_pass_c(const cx<R> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx<
             L[zc * lsL + iy] = in[(size_t)(z0 + zc) * N + iy];
         }
         __syncthreads();
-        fft_lines<R>(L, nz, lsL, 1, plan, tw, (R)-1);
+        fft_lines<CT>(L, nz, lsL, 1, plan, tw, -1);
         for (int i = threadIdx.x; i < nz * Py; i += blockDim.x) {
             const int zc = i % nz, py = i / nz;
             int iy = py + ny0m;
@@ -318,14 +327,15 @@ k_pass_c(const cx<R> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx<
         __syncthreads();
     }
     const int2 yr = yrange[px];
-    fft_lines<R>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, (R)-1);
+    fft_lines<CT>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, -1);
     const int g0 = plane_begin[px], g1 = plane_begin[px + 1];
     cx<R> *Yb = Y + (size_t)b * ldy;
     const cx<R> *Xb = X + (size_t)b * ldx;
     for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-        cx<R> v = A[gmap[g]];
-        if (kin) v = v + kin[g] * Xb[g];
-        Yb[g] = v;
+        cx<CT> v = A[gmap[g]];
+        if (kin) v = v + (CT)kin[g] * to_ct<CT>(Xb[g]);
+        if constexpr (std::is_same<CT, R>::value) Yb[g] = v;
+        else Yb[g] = mkc<R>((R)v.x, (R)v.y);
     }
 }
 
@@ -376,13 +386,12 @@ size_t fft_smem_need(const FFTGeom &g) {
     return zc ? smem_ac<R>(g, zc) : 0;
 }
 
-template <typename R>
-int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
-                   const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch, cudaStream_t s) {
-    if (nb <= 0) return LOBPCG_OK;
-    if constexpr (std::is_same<R, float>::value) {
-        if (fft_reg_supported(g.N)) return fft_reg_apply(g, X, ldx, Y, ldy, nb, kin, vt, T2, nbatch, s);
-    }
+namespace {
+
+// The three passes over batches of bands; CT is the compute type (see k_pass_a).
+template <typename R, typename CT>
+int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
+               const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
     const int N = g.N;
     const int zc = pick_zc<R>(g);
     if (zc == 0) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT grid too large for shared memory");
@@ -392,9 +401,9 @@ int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
     static std::atomic<bool> attr_set{false};
     if (!attr_set.load()) {
         const int lim = max_dyn_smem();
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_a<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_b<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_c<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_a<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_b<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_c<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         attr_set.store(true);
     }
     const int ny0m = ((g.ny0 % N) + N) % N;
@@ -403,22 +412,38 @@ int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
         const int nbb = std::min(nbatch, nb - b0);
         const cx<R> *Xb = X + (size_t)b0 * ldx;
         cx<R> *Yb = Y + (size_t)b0 * ldy;
-        k_pass_a<R><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
+        k_pass_a<R, CT><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
                                                              g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass A"));
-        k_pass_b<R><<<dim3((N + yc - 1) / yc, N, nbb), kThreads, sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
+        k_pass_b<R, CT><<<dim3((N + yc - 1) / yc, N, nbb), kThreads, sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
         LG_TRY(check_launch("fft pass B"));
-        k_pass_c<R><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
+        k_pass_c<R, CT><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
                                                              g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass C"));
     }
     return LOBPCG_OK;
 }
 
+}  // namespace
+
+template <typename R>
+int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
+                   const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch, cudaStream_t s, bool df) {
+    if (nb <= 0) return LOBPCG_OK;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fft_reg_supported(g.N)) return fft_reg_apply(g, X, ldx, Y, ldy, nb, kin, vt, T2, nbatch, s);
+    } else {
+        if (df)  // FP64 data transformed in double-FP32 (the half box holds pairs of floats)
+            return fft_passes<R, df64>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, reinterpret_cast<cx<df64> *>(T2),
+                                       nbatch, s);
+    }
+    return fft_passes<R, R>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+}
+
 template int fft_vloc_apply<float>(const FFTGeom &, const FFTPlan &, const c32 *, int, c32 *, int, int,
-                                   const float *, const float *, const c32 *, c32 *, int, cudaStream_t);
+                                   const float *, const float *, const c32 *, c32 *, int, cudaStream_t, bool);
 template int fft_vloc_apply<double>(const FFTGeom &, const FFTPlan &, const z64 *, int, z64 *, int, int,
-                                    const double *, const double *, const z64 *, z64 *, int, cudaStream_t);
+                                    const double *, const double *, const z64 *, z64 *, int, cudaStream_t, bool);
 template size_t fft_smem_need<float>(const FFTGeom &);
 template size_t fft_smem_need<double>(const FFTGeom &);
 

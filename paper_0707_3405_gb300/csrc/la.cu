@@ -43,13 +43,6 @@ template <> struct Lim<float> {
     static __device__ __forceinline__ float tiny() { return FLT_MIN; }
     static __device__ __forceinline__ float big() { return FLT_MAX; }
 };
-// double-FP32: 2^-46 covers a few units of the pair's 2^-48 per operation; the range is
-// FP32's, kept well inside it so that the low part does not underflow
-template <> struct Lim<df64> {
-    static __device__ __forceinline__ df64 eps() { return df64(1.4210854715202004e-14f); }
-    static __device__ __forceinline__ df64 tiny() { return df64(7.888609052210118e-31f); }
-    static __device__ __forceinline__ df64 big() { return df64(1.2676506002282294e30f); }
-};
 __device__ __forceinline__ z64 ldcg_cx(const z64 *p) {
     const double2 t = __ldcg(reinterpret_cast<const double2 *>(p));
     return mkc(t.x, t.y);
@@ -732,12 +725,33 @@ __device__ void tri_bounds(const RT *__restrict__ d, const RT *__restrict__ e, i
     hi += pad;
 }
 
-// One warp per eigenvalue index k < m, one warp per block so that the m warps
-// spread over the SMs (the FP64 divisions of the Sturm counts are the cost, and
-// this GPU has few FP64 units per SM): each round the 32 lanes evaluate Sturm
-// counts at 32 points inside the bracket and keep the 1/33 of it that holds
-// eigenvalue k (about 5 bits per round).
+// Multisection: each round the 32 lanes of a warp evaluate Sturm counts at 32
+// points inside the bracket and keep the 1/33 of it that holds eigenvalue k
+// (about 5 bits per round).  The FP64 divisions of the Sturm counts are the cost
+// (this GPU has few FP64 units per SM).
 constexpr int kMsLanes = 32;
+constexpr int kMsMaxN = 4096;  // FP32 pre-bracketing copies of d and e^2 (shared memory)
+// FP32 Sturm count on FP32 copies of d and e^2 (shared memory).
+__device__ __forceinline__ int sturm_count32(const float *__restrict__ d, const float *__restrict__ e2, int n, float x,
+                                             float pivmin) {
+    int c = 0;
+    float q = d[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += (q < 0.f);
+    for (int i = 1; i < n; ++i) {
+        q = d[i] - x - e2[i - 1] / q;
+        if (fabsf(q) < pivmin) q = -pivmin;
+        c += (q < 0.f);
+    }
+    return c;
+}
+
+// One warp per eigenvalue index k < m, one warp per block so that the m warps spread over
+// the SMs.  FP64 (RT = double): a few cheap FP32 rounds first narrow the bracket.  FP32
+// Sturm counts are exact for a matrix whose entries are within a few FP32 roundings of T
+// (Kahan; Demmel, Dhillon and Ren 1995), so the FP32 bracket widened by a margin well above
+// that perturbation still holds the eigenvalue; the first FP64 round checks it (its end
+// lanes evaluate the two bracket ends) and falls back to the Gershgorin bracket if not.
 template <typename RT>
 __global__ void __launch_bounds__(32)
 k_multisect(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, RT *__restrict__ theta) {
@@ -746,11 +760,54 @@ k_multisect(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, RT
     if (k >= m) return;
     RT lo, hi, tnorm, pivmin;
     tri_bounds(d, e, n, lo, hi, tnorm, pivmin);
-    for (int it = 0; it < 24; ++it) {
+    bool check = false;
+    const RT lo_g = lo, hi_g = hi;
+    if constexpr (sizeof(RT) == 8) {
+        __shared__ float ds[kMsMaxN], e2s[kMsMaxN];
+        if (n <= kMsMaxN) {
+            for (int i = sub; i < n; i += kMsLanes) {
+                ds[i] = (float)d[i];
+                e2s[i] = (i + 1 < n) ? (float)(e[i] * e[i]) : 0.f;
+            }
+            __syncwarp();
+            const float tn = (float)tnorm;
+            const float piv = FLT_MIN * fmaxf(1.f, tn * tn);
+            const float margin = 32.f * FLT_EPSILON * tn + 4.f * piv;
+            float l32 = (float)lo, h32 = (float)hi;
+            for (int it = 0; it < 8 && h32 - l32 > 4.f * margin; ++it) {  // warp-uniform
+                const float w = h32 - l32;
+                const float x = l32 + w * (float)(sub + 1) / (float)(kMsLanes + 1);
+                const int c = sturm_count32(ds, e2s, n, x, piv);
+                const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
+                const int T = __popc(mask) - 1;
+                const float xlo = __shfl_sync(0xffffffffu, x, T < 0 ? 0 : T);
+                const float xhi = __shfl_sync(0xffffffffu, x, T < kMsLanes - 1 ? T + 1 : kMsLanes - 1);
+                if (T >= 0) l32 = xlo;
+                if (T < kMsLanes - 1) h32 = xhi;
+            }
+            lo = fmax(lo_g, (RT)l32 - (RT)margin);
+            hi = fmin(hi_g, (RT)h32 + (RT)margin);
+            check = true;
+        }
+    }
+    for (int it = 0; it < 32; ++it) {
         const RT w = hi - lo;
         if (w <= 2.0 * Lim<RT>::eps() * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;  // warp-uniform
-        const RT x = lo + w * (RT)(sub + 1) / (RT)(kMsLanes + 1);
+        RT x;
+        if (check)  // bracket ends on the end lanes, 30 points between
+            x = (sub == 0) ? lo : (sub == kMsLanes - 1) ? hi : lo + w * (RT)sub / (RT)(kMsLanes - 1);
+        else
+            x = lo + w * (RT)(sub + 1) / (RT)(kMsLanes + 1);
         const int c = sturm_count(d, e, n, x, pivmin);
+        if (check) {
+            check = false;
+            const bool ok = __shfl_sync(0xffffffffu, c, 0) <= k && __shfl_sync(0xffffffffu, c, kMsLanes - 1) > k;
+            if (!ok) {  // the FP32 bracket missed (not expected): restart from Gershgorin
+                lo = lo_g;
+                hi = hi_g;
+                continue;
+            }
+        }
         const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
         const int T = __popc(mask) - 1;  // counts are monotone in sub: lanes 0..T have c <= k
         const RT xlo = __shfl_sync(0xffffffffu, x, T < 0 ? 0 : T);
@@ -774,15 +831,15 @@ __device__ __forceinline__ RT hash_uniform(unsigned int a, unsigned int b) {
 // LU of T - lambda I with partial pivoting and the solves (sequential recurrences,
 // kept in shared memory), from a pseudo-random start, three times; after each solve
 // the warp orthogonalises against the cluster's earlier vectors (modified
-// Gram-Schmidt) and normalises.  Dynamic shared memory: 5 n reals + n pivots.
+// Gram-Schmidt) and normalises.  Dynamic shared memory: 6 n reals + n pivots.
 template <typename RT>
 __global__ void __launch_bounds__(32)
 k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, const RT *__restrict__ theta,
           RT *Z) {
     extern __shared__ __align__(16) unsigned char smraw[];
     RT *dd = reinterpret_cast<RT *>(smraw);
-    RT *du = dd + n, *du2 = du + n, *dl = du2 + n, *z = dl + n;
-    signed char *pv = reinterpret_cast<signed char *>(z + n);
+    RT *du = dd + n, *du2 = du + n, *dl = du2 + n, *z = dl + n, *rdd = z + n;
+    signed char *pv = reinterpret_cast<signed char *>(rdd + n);
     const int k = blockIdx.x, lane = threadIdx.x;
     if (k >= m) return;
     RT lo, hi, tnorm, pivmin;
@@ -822,6 +879,9 @@ k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, cons
             }
             if (dd[n - 1] == 0.0) dd[n - 1] = pert;
         }
+        __syncwarp();
+        // reciprocal pivots, all lanes: the three solves below then multiply instead of divide
+        for (int i = lane; i < n; i += 32) rdd[i] = (RT)1.0 / dd[i];
         for (int i = lane; i < n; i += 32) z[i] = hash_uniform<RT>((unsigned)j, (unsigned)i);
         __syncwarp();
         for (int it = 0; it < 3; ++it) {
@@ -835,9 +895,9 @@ k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, cons
                         z[i + 1] = t - dl[i] * z[i];
                     }
                 }
-                z[n - 1] = z[n - 1] / dd[n - 1];
-                if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / dd[n - 2];
-                for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
+                z[n - 1] = z[n - 1] * rdd[n - 1];
+                if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) * rdd[n - 2];
+                for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) * rdd[i];
             }
             __syncwarp();
             for (int p = k; p < j; ++p) {
@@ -924,7 +984,6 @@ template <typename RT>
 int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT> *V, int ldv, cudaStream_t s) {
     if (n <= 0 || m <= 0) return LOBPCG_OK;
     if (m > n) return fail(LOBPCG_ERR_ARG, "heev: m > n");
-    const int nt = (n + 31) / 32;
     // workspace carve-up
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
@@ -1041,7 +1100,7 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     }
     k_multisect<RT><<<m, kMsLanes, 0, s>>>(n, m, dg, eg, theta);
     LG_TRY(check_launch("multisection"));
-    const size_t smem_ii = 5 * sizeof(RT) * (size_t)n + (size_t)n;
+    const size_t smem_ii = 6 * sizeof(RT) * (size_t)n + (size_t)n;
     if (smem_ii > 48 * 1024)
         LG_TRY(allow_max_dyn_smem((const void *)k_inviter<RT>));
     k_inviter<RT><<<m, 32, smem_ii, s>>>(n, m, dg, eg, theta, Z);

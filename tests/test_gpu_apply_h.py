@@ -3,6 +3,7 @@ CPU FP64 oracle, element by element, on seeded synthetic cells.
 
 Tolerances (relative to max |H x|):
   complex128 / FP64 FFT and GEMMs  1e-12
+  complex128 / double-FP32         5e-12  (~2^-47 per operation, same growth)
   complex64  / FP32 FFT and GEMMs  5e-6   (FP32 unit roundoff 6e-8 times the
                                          ~log2(N^3) + nproj-term growth)
 """
@@ -14,7 +15,7 @@ from tests._helpers import ensure_built, make_solver, oracle_for
 
 pytestmark = pytest.mark.gpu
 
-TOL64, TOL32 = 1e-12, 5e-6
+TOL64, TOL32, TOLDF = 1e-12, 5e-6, 5e-12
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,10 +34,10 @@ def _rand_block(seed, nb, npw):
     return (rng.standard_normal((nb, npw)) + 1j * rng.standard_normal((nb, npw))) / np.sqrt(2)
 
 
-def _compare(solver, H, k, X, dtype, tol):
+def _compare(solver, H, k, X, dtype, tol, df32=False):
     torch = _torch()
     Xt = torch.tensor(X.astype(dtype), device="cuda")
-    Yt = solver.apply_H(k, Xt)
+    Yt = solver.apply_H(k, Xt, df32=df32)
     torch.cuda.synchronize()
     Y = Yt.cpu().numpy().astype(np.complex128)
     ref = H.apply(X.astype(dtype).astype(np.complex128).T).T
@@ -58,7 +59,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"N{c['N']}_kb{int(c['kb'])}_k{c['kpt'][0]}")
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c128_df32"])
 def test_apply_h_matches_oracle_small(case, prec):
     w = synth.tiny_workload(**case)
     with make_solver(w, block_size=4) as s:
@@ -68,6 +69,8 @@ def test_apply_h_matches_oracle_small(case, prec):
         X = _rand_block(1, 37, s.npw())
         if prec == "c128":
             _compare(s, H, 0, X, np.complex128, TOL64)
+        elif prec == "c128_df32":
+            _compare(s, H, 0, X, np.complex128, TOLDF, df32=True)
         else:
             _compare(s, H, 0, X, np.complex64, TOL32)
 
@@ -122,7 +125,7 @@ def test_apply_h_translation_invariance_gpu():
         assert d < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c128_df32"])
 def test_apply_h_full_size_k96(prec):
     """The 96^3 / 57925 plane-wave cell with 256 KB projectors, k = (1/4,1/4,1/4):
     a ragged block of 19 bands against the oracle's FFT route."""
@@ -131,8 +134,8 @@ def test_apply_h_full_size_k96(prec):
         assert s.npw() == 57925
         H = oracle_for(w, s)
         X = _rand_block(5, 19, s.npw())
-        _compare(s, H, 0, X, np.complex128 if prec == "c128" else np.complex64,
-                 TOL64 if prec == "c128" else TOL32)
+        _compare(s, H, 0, X, np.complex64 if prec == "c64" else np.complex128,
+                 {"c128": TOL64, "c64": TOL32, "c128_df32": TOLDF}[prec], df32=prec == "c128_df32")
 
 
 def test_apply_h_multi_kpoint_uneven_spheres():
