@@ -110,9 +110,10 @@ typedef struct {
                             bands a gap to the unresolved spectrum. */
     double mixed_switch; /* MIXED only: a block whose smallest residual after the previous sweep is
                             below this (Ha) runs its iterations in FP64 (default 0 = never) */
-    double mixed_early;  /* MIXED only: while the largest residual of the previous sweep is above this
-                            (Ha), block starts and the sweep-end Rayleigh-Ritz use the FP32 copies and
-                            skip the FP64 H X refresh (default 1e-3; 0 = never) */
+    double mixed_early;  /* MIXED only: a block all of whose bands had residuals above this (Ha) in the
+                            previous sweep visits "early": its start and its X updates use the FP32
+                            copies, and its H X is not refreshed in FP64.  The sweep-end Rayleigh-Ritz
+                            does likewise when every block was early.  (default 1e-3; 0 = never) */
     int    fp64_gemm;    /* arithmetic of the FP64-class work limited by this GPU's FP64 units: the tall
                             GEMMs (Grams, constraint, Ritz updates, KB projections of FP64 H X) and, in
                             the Rayleigh-Ritz step, the Cholesky diagonal blocks, the tridiagonalisation's
@@ -151,6 +152,8 @@ typedef struct {
     long long block_visits_fp64;  /* block visits run entirely in FP64 */
     double    ph_ms_fp64[LOBPCG_PH_COUNT];     /* part of ph_ms spent in calls doing FP64 arithmetic */
     double    ph_bytes_fp64[LOBPCG_PH_COUNT];  /* part of ph_bytes moved by those calls */
+    long long block_visits_settled;  /* MIXED: block visits without inner iterations, the block's
+                                        residuals being all below tol / 100 after the previous sweep */
 } lobpcg_stats;
 
 /* Fill *opt with defaults: m = 64, nline = 4, max_sweeps = 100, FP64, tol = 1e-8. */

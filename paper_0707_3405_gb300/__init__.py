@@ -62,7 +62,8 @@ class Stats(ctypes.Structure):
                 ("ph_bytes", ctypes.c_double * NPH), ("ph_calls", ctypes.c_longlong * NPH),
                 ("ph_fp64_flops", ctypes.c_double * NPH),
                 ("block_visits_fp32", ctypes.c_longlong), ("block_visits_fp64", ctypes.c_longlong),
-                ("ph_ms_fp64", ctypes.c_double * NPH), ("ph_bytes_fp64", ctypes.c_double * NPH)]
+                ("ph_ms_fp64", ctypes.c_double * NPH), ("ph_bytes_fp64", ctypes.c_double * NPH),
+                ("block_visits_settled", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         out = {}

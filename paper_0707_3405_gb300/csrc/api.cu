@@ -600,7 +600,9 @@ struct Solver {
         return rayleigh_quotients(npw, m, Xb, npw, HXb, npw, theta, s);
     }
 
-    int block_mixed(int b) {
+    // nline: Algorithm 1 iterations after the block start (0 for a block already converged far
+    // below the tolerance, see solve_k)
+    int block_mixed(int b, int nline) {
         const int j0 = b * m;
         int cur = 0;
         z64 *Xb = Z[cur], *HXb = HZ[cur];
@@ -634,7 +636,7 @@ struct Solver {
         cur = 1 - cur;
         trace("mixed-start", b, -1, Z[cur], HZ[cur], m);
         int nP = 0;
-        for (int it = 0; it < c->opt.nline; ++it) {
+        for (int it = 0; it < nline; ++it) {
             Xb = Z[cur];
             HXb = HZ[cur];
             c32 *Q = Q32[cur], *HQ = HQ32[cur];
@@ -861,7 +863,12 @@ T *carve(lobpcg_ctx *c, DevBuf &b, size_t count, int &rc) {
     return reinterpret_cast<T *>(b.p);
 }
 
+// Mixed schedule: a block whose residuals after the previous sweep are all below this fraction of
+// the tolerance takes no inner iterations in the next sweep.
+constexpr double kSettledFrac = 1e-2;
+
 struct SolveCounters {
+    long long settled = 0;               // mixed block visits without inner iterations
     long long a64 = 0, a32 = 0;          // single-band H applications (FP64, FP32)
     long long visits32 = 0, visits64 = 0;  // block visits per precision
     int iters = 0;                       // Algorithm 1 iterations
@@ -933,19 +940,36 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     double maxr = 0.0;
     // residuals of the previous sweep choose each block's precision in a mixed solve
     std::vector<double> res_prev(M, HUGE_VAL);
-    double prev_max = HUGE_VAL;
+    // per block: H X_b holds FP64 accuracy (false after an early visit or an early sweep end)
+    std::vector<char> hx64(sv.nblk, 1);
     for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
-        const bool was_early = sv.early;
-        sv.early = sv.mixed && c->opt.mixed_early > 0.0 && prev_max > c->opt.mixed_early;
-        // First full sweep after early ones: H X carries the FP32 noise of the early sweeps
-        // (~1e-7 |H|), which dominates the residuals of well converged bands and makes their W
-        // nearly parallel; recompute it in FP64 from X first.
-        if (was_early && !sv.early) LG_TRY(sv.applyH64(X, sv.HX, M));
+        bool all_early = sv.mixed;
         for (int b = 0; b < sv.nblk; ++b) {
             double rmin = HUGE_VAL;
             for (int i = b * m; i < (b + 1) * m; ++i) rmin = std::min(rmin, res_prev[i]);
+            // Early visits (FP32 block start and X updates) only while every band of the block is
+            // above mixed_early: bands nearer the FP32 noise of H X (~1e-7 |H|) get W directions
+            // made of that noise, and their Rayleigh-Ritz steps then drop most of [W P] and lose
+            // the block (seen with 2048 bands, whose lowest blocks converge sweeps before the top).
+            sv.early = sv.mixed && c->opt.mixed_early > 0.0 && rmin > c->opt.mixed_early;
+            all_early = all_early && sv.early;
+            if (sv.mixed && !sv.early && !hx64[b]) {
+                // first full visit after early ones: H X_b in FP64 from X_b (its FP32 noise would
+                // dominate the residuals of well converged bands)
+                LG_TRY(sv.applyH64(sv.col(X, b * m), sv.col(sv.HX, b * m), m));
+                LG_TRY(sv.refresh32(b));
+            }
+            hx64[b] = !sv.early;
+            // A block whose bands all sit far below the tolerance keeps its block start (constraint
+            // and the block's Rayleigh-Ritz) but takes no inner iterations: its residuals, hence its
+            // W, are rounding noise there, and a Rayleigh-Ritz step on such a basis broke a
+            // converged block of the 2048-band cell (residual 3e-12 -> 1 Ha in one iteration).
+            double rmax = 0.0;
+            for (int i = b * m; i < (b + 1) * m; ++i) rmax = std::max(rmax, res_prev[i]);
+            const bool settled = sv.mixed && rmax < kSettledFrac * c->opt.tol;
             if (sv.mixed && !(rmin < c->opt.mixed_switch)) {
-                LG_TRY(sv.block_mixed(b));
+                LG_TRY(sv.block_mixed(b, settled ? 0 : c->opt.nline));
+                if (settled) ++cnt.settled;
                 ++cnt.visits32;
             } else {
                 LG_TRY(sv.block64(b));
@@ -953,6 +977,11 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
                 ++cnt.visits64;
             }
         }
+        // the sweep-end Rayleigh-Ritz runs on the FP32 copies only if every block was early; else
+        // it refreshes H X in FP64 first
+        sv.early = all_early;
+        if (all_early) std::fill(hx64.begin(), hx64.end(), 0);
+        else std::fill(hx64.begin(), hx64.end(), 1);
         LG_TRY(sv.final_rr(eig_h, res_h));
         if (prof) prof->collect();
         ++sweeps_done;
@@ -966,7 +995,6 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
         LG_TRY(tc_check_error());
         if (!finite) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite Ritz value or residual");
         std::copy(res_h, res_h + M, res_prev.begin());
-        prev_max = maxr;
         if (maxr <= c->opt.tol && !sv.early) break;
     }
     cnt.a64 += sv.applies64;
@@ -1319,6 +1347,7 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         cnt.a32 += cnts[l].a32;
         cnt.visits32 += cnts[l].visits32;
         cnt.visits64 += cnts[l].visits64;
+        cnt.settled += cnts[l].settled;
         cnt.iters += cnts[l].iters;
     }
     for (int k = 0; k < c->nk; ++k) {
@@ -1337,6 +1366,7 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         st->band_applies_fp32 = cnt.a32;
         st->block_visits_fp32 = cnt.visits32;
         st->block_visits_fp64 = cnt.visits64;
+        st->block_visits_settled = cnt.settled;
         st->kernel_launches = launch_count() - l0;
         for (int l = 0; l < nl; ++l)
             for (int p = 0; p < LOBPCG_PH_COUNT; ++p) {

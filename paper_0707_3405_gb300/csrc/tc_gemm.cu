@@ -61,11 +61,19 @@ __device__ __forceinline__ unsigned char *align1k(unsigned char *p) {
     return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
 }
 
-template <int STAGE>
-constexpr int n_stages() { return 3 * STAGE <= 200 * 1024 ? 3 : 2; }
+// Ring depth: NSF if given, else 3 stages when they fit in 200 KB, else 2.
+template <int STAGE, int NSF = 0>
+constexpr int n_stages() { return NSF ? NSF : (3 * STAGE <= 200 * 1024 ? 3 : 2); }
 
-template <int STAGE>
-constexpr size_t smem_bytes() { return (size_t)n_stages<STAGE>() * STAGE + 1024 + 64; }
+template <int STAGE, int NSF = 0>
+constexpr size_t smem_bytes() { return (size_t)n_stages<STAGE, NSF>() * STAGE + 1024 + 64; }
+
+// A B with 64 columns: a 2-stage ring (97 KB) lets two CTAs share an SM; the products of the
+// block iterations are tall and short (K = 64 .. 192), so a deeper ring never fills anyway.
+template <int NN>
+constexpr int nn_ring() { return NN == 64 ? 2 : 0; }
+template <int NN>
+constexpr int nn_ctas_per_sm() { return NN == 64 ? 2 : 1; }
 
 // Issue the 3xTF32 MMAs of one stage (4 K-steps of 8) and commit them to `bar`.
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t a_h, uint32_t a_l, uint32_t b_h, uint32_t b_l,
@@ -206,12 +214,12 @@ __global__ void k_tc_reduce(int m, int n, int nsplit, float alpha, const z64 *__
 // ------------------------------------------------------------------ D = alpha A B + beta C
 // CTA tile: 64 complex rows of A / D (128 real rows) x NN columns of B / D, full K.
 template <int NN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, nn_ctas_per_sm<NN>())
 k_tc_nn(int M, int n, int k, float alpha, const c32 *__restrict__ A, int lda, const c32 *__restrict__ B, int ldb,
         float beta, const c32 *C, int ldc, c32 *D, int ldd) {
     constexpr int A_BYTES = 128 * ROWB, B_BYTES = NN * ROWB;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    constexpr int NS = n_stages<STAGE>();
+    constexpr int NS = n_stages<STAGE, nn_ring<NN>()>();
     constexpr uint32_t IDESC = make_idesc_tf32(128, NN);
     extern __shared__ unsigned char smraw[];
     unsigned char *base = align1k(smraw);
@@ -371,7 +379,7 @@ template <int NN>
 int launch_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c32 *B, int ldb, float beta,
               const c32 *C, int ldc, c32 *D, int ldd, cudaStream_t s) {
     constexpr int STAGE = 2 * 128 * ROWB + 2 * NN * ROWB;
-    constexpr size_t SMEM = smem_bytes<STAGE>();
+    constexpr size_t SMEM = smem_bytes<STAGE, nn_ring<NN>()>();
     static std::atomic<bool> attr{false};
     LG_TRY(ensure_smem(k_tc_nn<NN>, SMEM, attr));
     const dim3 grid((M + 63) / 64, (n + NN - 1) / NN);
