@@ -169,7 +169,7 @@ __device__ __forceinline__ void df_norm(float &h, float &l) {
 }
 
 template <bool CA, bool CB, int T>
-__global__ void __launch_bounds__(TH)
+__global__ void __launch_bounds__(TH, 2)
 k_gemm_df(int m, int n, int K, int kchunk, double alpha, const z64 *__restrict__ A, int lda,
           const z64 *__restrict__ B, int ldb, double beta, const z64 *C, int ldc, z64 *D, int ldd,
           z64 *__restrict__ part, int lower) {

@@ -170,7 +170,8 @@ struct FFTPlan {
     int nstage = 0;
     int radix[12];
 };
-bool make_fft_plan(int N, FFTPlan &plan);
+// Mixed-radix plan of a length-N line (radices 8, 4, 2, 5, 3; allow8 = false leaves out 8).
+bool make_fft_plan(int N, FFTPlan &plan, bool allow8 = true);
 
 // Local-potential application Y = V_loc X (+ T X) for a block of bands on one k-point.
 //   X, Y: npw x nb column-major (ld = ldx / ldy) of cx<R>; T: npw kinetic (nullable)

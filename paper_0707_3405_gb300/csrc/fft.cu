@@ -28,13 +28,14 @@
 
 namespace lg {
 
-bool make_fft_plan(int N, FFTPlan &p) {
+bool make_fft_plan(int N, FFTPlan &p, bool allow8) {
     p.N = N;
     p.nstage = 0;
     int r = N;
     if (N < 2) return false;
     const int pref[5] = {8, 4, 2, 5, 3};
     for (int f : pref) {
+        if (f == 8 && !allow8) continue;
         while (r % f == 0) {
             if (p.nstage >= 12) return false;
             p.radix[p.nstage++] = f;
@@ -177,13 +178,20 @@ __device__ __forceinline__ void fft_stage(cx<R> *buf, int nlines, int ls, int es
     __syncthreads();
 }
 
-constexpr int kVPT = 8;
 constexpr int kThreads = 256;
+// Values per thread and stage: 8 (radix up to 8) for FP32 / FP64; the double-FP32 passes hold
+// 4 (radix up to 5, no radix-8 stage) so that their pair arithmetic fits in half the registers
+// and two blocks share an SM.
+template <typename CT>
+constexpr int vpt() { return sizeof(CT) == 8 && !std::is_same<CT, double>::value ? 4 : 8; }
+template <typename CT>
+constexpr bool radix8() { return vpt<CT>() == 8; }
 
 // In-place FFT of `nlines` lines (line stride ls, element stride es) by the whole block.
 // sg = -1: forward (e^{-i...}); sg = +1: inverse without 1/N.
 template <typename R>
 __device__ void fft_lines(cx<R> *buf, int nlines, int ls, int es, const FFTPlan &plan, const cx<R> *tw, int sg) {
+    constexpr int kVPT = vpt<R>();
     const int N = plan.N;
     int lpg = (int)(blockDim.x * kVPT) / N;
     if (lpg < 1) lpg = 1;
@@ -194,7 +202,9 @@ __device__ void fft_lines(cx<R> *buf, int nlines, int ls, int es, const FFTPlan 
         for (int s = 0; s < plan.nstage; ++s) {
             const int r = plan.radix[s];
             switch (r) {
-                case 8: fft_stage<R, 8, kVPT>(b, nl, ls, es, N, Ns, tw, sg); break;
+                case 8:
+                    if constexpr (radix8<R>()) fft_stage<R, 8, kVPT>(b, nl, ls, es, N, Ns, tw, sg);
+                    break;
                 case 4: fft_stage<R, 4, kVPT>(b, nl, ls, es, N, Ns, tw, sg); break;
                 case 2: fft_stage<R, 2, kVPT>(b, nl, ls, es, N, Ns, tw, sg); break;
                 case 5: fft_stage<R, 5, kVPT>(b, nl, ls, es, N, Ns, tw, sg); break;
@@ -433,9 +443,12 @@ int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
     if constexpr (std::is_same<R, float>::value) {
         if (fft_reg_supported(g.N)) return fft_reg_apply(g, X, ldx, Y, ldy, nb, kin, vt, T2, nbatch, s);
     } else {
-        if (df)  // FP64 data transformed in double-FP32 (the half box holds pairs of floats)
-            return fft_passes<R, df64>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, reinterpret_cast<cx<df64> *>(T2),
+        if (df) {  // FP64 data transformed in double-FP32 (the half box holds pairs of floats)
+            FFTPlan p4;
+            if (!make_fft_plan(g.N, p4, false)) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plan");
+            return fft_passes<R, df64>(g, p4, X, ldx, Y, ldy, nb, kin, vt, tw, reinterpret_cast<cx<df64> *>(T2),
                                        nbatch, s);
+        }
     }
     return fft_passes<R, R>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
 }
