@@ -100,8 +100,14 @@ typedef struct {
     int    gemm_split;   /* complex64 GEMM engine: 0 = auto (= 2), 2 = tensor cores with 3xTF32 split
                             operands for long reductions and tall products, 3 = CUDA cores only;
                             1 (BF16x3) is not built: ERR_UNSUPPORTED */
-    int    use_graph;    /* reserved (accepted, no effect yet) */
-    int    autotune;     /* reserved (accepted, no effect yet) */
+    int    use_graph;    /* 1: the FP32 H application of each block iteration (FFT passes + KB GEMMs,
+                            about ten kernels) is recorded once per buffer pair as a CUDA graph and
+                            replayed as one launch.  Ignored while options.timing is on and on the
+                            legacy default stream (which cannot be captured). */
+    int    autotune;     /* 1: the first lobpcg_solve of the handle times, per k-point, the FFT
+                            band-batch budget (32 .. 256 MB) of the FP32 and of the FP64-class H
+                            application and keeps the fastest; lobpcg_stats.ms_autotune reports
+                            the time it took (not included in ms_total). */
     double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */
     long long mem_cap;   /* 0: no cap; else maximum bytes the handle may allocate (ERR_OOM above it) */
     int    timing;       /* 1: time each phase of lobpcg_solve with CUDA events on the handle's stream */
@@ -154,6 +160,7 @@ typedef struct {
     double    ph_bytes_fp64[LOBPCG_PH_COUNT];  /* part of ph_bytes moved by those calls */
     long long block_visits_settled;  /* MIXED: block visits without inner iterations, the block's
                                         residuals being all below tol / 100 after the previous sweep */
+    double    ms_autotune;            /* wall time of the autotuner in this call (options.autotune) */
 } lobpcg_stats;
 
 /* Fill *opt with defaults: m = 64, nline = 4, max_sweeps = 100, FP64, tol = 1e-8. */

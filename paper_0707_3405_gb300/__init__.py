@@ -63,7 +63,7 @@ class Stats(ctypes.Structure):
                 ("ph_fp64_flops", ctypes.c_double * NPH),
                 ("block_visits_fp32", ctypes.c_longlong), ("block_visits_fp64", ctypes.c_longlong),
                 ("ph_ms_fp64", ctypes.c_double * NPH), ("ph_bytes_fp64", ctypes.c_double * NPH),
-                ("block_visits_settled", ctypes.c_longlong)]
+                ("block_visits_settled", ctypes.c_longlong), ("ms_autotune", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -181,7 +181,7 @@ class Solver:
                  block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
                  tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, nbuf: int = 0,
                  mixed_switch: float | None = None, mixed_early: float | None = None, stream=None,
-                 fp64_gemm: int = 0):
+                 fp64_gemm: int = 0, use_graph: bool = False, autotune: bool = False):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -193,7 +193,7 @@ class Solver:
         self.nproj = int(E.shape[0])
         self.nk = int(kp.shape[0])
         opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
-                            mixed_early, fp64_gemm)
+                            mixed_early, fp64_gemm, use_graph, autotune)
         cell = Cell(a, N, ecut)
         self._stream = stream
         rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
@@ -209,7 +209,7 @@ class Solver:
 
     @staticmethod
     def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False, nbuf=0,
-                 mixed_switch=None, mixed_early=None, fp64_gemm=0) -> Options:
+                 mixed_switch=None, mixed_early=None, fp64_gemm=0, use_graph=False, autotune=False) -> Options:
         o = default_options()
         o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -222,12 +222,15 @@ class Solver:
         if mixed_early is not None:
             o.mixed_early = mixed_early
         o.fp64_gemm = fp64_gemm
+        o.use_graph = 1 if use_graph else 0
+        o.autotune = 1 if autotune else 0
         return o
 
     def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0,
-                    timing=False, nbuf=0, mixed_switch=None, mixed_early=None, fp64_gemm=0):
+                    timing=False, nbuf=0, mixed_switch=None, mixed_early=None, fp64_gemm=0, use_graph=False,
+                    autotune=False):
         o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
-                          mixed_early, fp64_gemm)
+                          mixed_early, fp64_gemm, use_graph, autotune)
         _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
 
     def set_stream(self, stream):

@@ -11,8 +11,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 // ------------------------------------------------------------------ shared helpers
@@ -30,6 +32,8 @@ const char *global_error() { return g_last_fail.c_str(); }
 
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
+// Correct the count for kernels recorded into a CUDA graph (not run) or run from one.
+static void add_launches(long long d) { g_launches.fetch_add(d, std::memory_order_relaxed); }
 
 int check_launch(const char *what) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -151,6 +155,9 @@ struct KPoint {
     z64 *beta64 = nullptr;  // npw x nproj
     c32 *beta32 = nullptr;
     bool has_beta = false;
+    // FFT scratch budget per band batch (bytes; 0 = the handle default), chosen by the autotuner
+    size_t fft_budget32 = 0, fft_budget64 = 0;
+    bool tuned = false;
 };
 
 // Everything one k-point solve (or one apply_H call) writes: scratch, solver buffers and the
@@ -164,6 +171,19 @@ struct Lane {
     EigWork ew;
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
     DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32, E32;
+    // CUDA graphs of the FP32 H application on fixed buffers (options.use_graph), keyed by
+    // (k, X, Y, nb); a graph is only replayed while the scratch it recorded is still in place
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;
+        const void *t2 = nullptr, *nlb = nullptr, *part = nullptr;
+    };
+    std::map<std::tuple<int, const void *, void *, int>, Graph> graphs;
+    void clear_graphs() {
+        for (auto &g : graphs)
+            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+        graphs.clear();
+    }
     void bind(Allocator *a, CoopGate *g, int share) {
         gw.alloc = a;
         ew.alloc = a;
@@ -176,6 +196,7 @@ struct Lane {
                           &Tmp, &Gram, &Gram2, &Cbuf, &dtheta, &dres, &dwork, &Gc, &gw.part, &ew.buf, &ew.ibuf,
                           &ew.gw.part, &X32all, &HX32all, &Q32[0], &Q32[1], &HQ32[0], &HQ32[1], &D32, &Small32,
                           &Xext, &T32, &E32};
+        clear_graphs();
         for (DevBuf *b : bufs) a.release(*b);
         if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
@@ -339,7 +360,8 @@ int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y
     const bool f64 = sizeof(R) == 8;
     const size_t cb = sizeof(cx<R>);
     const size_t per_band = cb * (size_t)g.Px * g.N * g.N;
-    int nbatch = (int)std::max<size_t>(1, c->fft_budget / per_band);
+    const size_t kb = f64 ? K.fft_budget64 : K.fft_budget32;
+    int nbatch = (int)std::max<size_t>(1, (kb ? kb : c->fft_budget) / per_band);
     nbatch = std::min(std::min(nbatch, nb), 65535);
     LG_TRY(c->alloc.ensure(L.T2, per_band * nbatch));
     {
@@ -469,7 +491,55 @@ struct Solver {
     }
     int applyH32(const c32 *Xin, c32 *Yout, int nb) {
         applies32 += nb;
+        // (the legacy default stream cannot be captured)
+        if (c->opt.use_graph && !prof && s != nullptr && s != cudaStreamLegacy) return graph_apply32(Xin, Yout, nb);
         return apply_H_dev<float>(c, *L, k, Xin, npw, Yout, npw, nb, prof);
+    }
+    // H W through a CUDA graph: the FFT passes and KB GEMMs of one block application (about ten
+    // kernels) replay as one launch.  The first call on a buffer pair runs directly (allocating
+    // its scratch) and records the graph for the next ones.
+    int graph_apply32(const c32 *Xin, c32 *Yout, int nb) {
+        const auto key = std::make_tuple(k, (const void *)Xin, (void *)Yout, nb);
+        auto it = L->graphs.find(key);
+        if (it != L->graphs.end() && it->second.t2 == L->T2.p && it->second.nlb == L->nlB.p &&
+            it->second.part == L->gw.part.p) {
+            LG_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
+            add_launches(it->second.kernels);
+            return LOBPCG_OK;
+        }
+        if (it != L->graphs.end()) {  // scratch moved since it was recorded
+            cudaGraphExecDestroy(it->second.exec);
+            L->graphs.erase(it);
+        }
+        LG_TRY(apply_H_dev<float>(c, *L, k, Xin, npw, Yout, npw, nb, nullptr));
+        const long long l0 = launch_count();
+        cudaGraph_t g = nullptr;
+        LG_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = apply_H_dev<float>(c, *L, k, Xin, npw, Yout, npw, nb, nullptr);
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        add_launches(l0 - launch_count());  // recorded, not run
+        if (rc != LOBPCG_OK || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (rc != LOBPCG_OK) return rc;
+            LG_CUDA_TRY(ec);
+        }
+        Lane::Graph gr;
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++gr.kernels;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&gr.exec, g, 0ULL);
+        cudaGraphDestroy(g);
+        LG_CUDA_TRY(ei);
+        gr.t2 = L->T2.p;
+        gr.nlb = L->nlB.p;
+        gr.part = L->gw.part.p;
+        L->graphs[key] = gr;
+        return LOBPCG_OK;
     }
 
     // ---------------------------------------------------------- FP64 helpers
@@ -877,6 +947,7 @@ struct SolveCounters {
 // Solve one k-point for M bands of which the first Mreq must converge (the rest are buffer bands).
 int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h, int &sweeps_done,
             Prof *prof, SolveCounters &cnt) {
+    L.clear_graphs();  // buffers may have moved since an earlier solve
     Solver sv;
     sv.c = c;
     sv.L = &L;
@@ -1239,6 +1310,61 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
 // Concurrent k-point lanes of one solve (k-points are independent, Sec. 5.2).
 constexpr int kMaxLanes = 4;
 
+// Autotuner (options.autotune): for each k-point, the FFT scratch budget per band batch (which
+// sets how many bands one launch of the FFT passes covers) of the FP32 H application and of the
+// FP64-class one, timed with CUDA events on the lane's stream over candidates from 32 to 256 MB
+// with nb = the block size.  Once per k-point and handle; its time is reported apart.
+static int autotune_k(lobpcg_ctx *c, Lane &L, int k, bool df, int nb) {
+    KPoint &K = c->kp[k];
+    if (K.tuned) return LOBPCG_OK;
+    const int npw = K.npw;
+    DevBuf bx, by;
+    int rc = c->alloc.ensure(bx, sizeof(z64) * (size_t)npw * nb);
+    if (rc == LOBPCG_OK) rc = c->alloc.ensure(by, sizeof(z64) * (size_t)npw * nb);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == LOBPCG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = fail(LOBPCG_ERR_CUDA, "autotune: event creation failed");
+    if (rc == LOBPCG_OK && cudaMemsetAsync(bx.p, 0, sizeof(z64) * (size_t)npw * nb, L.stream) != cudaSuccess)
+        rc = fail(LOBPCG_ERR_CUDA, "autotune: memset failed");
+    const size_t cands[] = {(size_t)32 << 20, (size_t)64 << 20, (size_t)128 << 20, (size_t)256 << 20};
+    for (int pass = 0; pass < 2 && rc == LOBPCG_OK; ++pass) {
+        size_t &budget = pass == 0 ? K.fft_budget32 : K.fft_budget64;
+        float best = 0.f;
+        size_t best_b = 0;
+        for (size_t b : cands) {
+            budget = b;
+            auto run = [&]() {
+                if (pass == 0)
+                    return apply_H_dev<float>(c, L, k, static_cast<const c32 *>(bx.p), npw, static_cast<c32 *>(by.p),
+                                              npw, nb);
+                return apply_H_dev<double>(c, L, k, static_cast<const z64 *>(bx.p), npw, static_cast<z64 *>(by.p),
+                                           npw, nb, nullptr, df);
+            };
+            rc = run();  // warm-up (allocates the scratch)
+            if (rc != LOBPCG_OK) break;
+            cudaEventRecord(e0, L.stream);
+            for (int r = 0; r < 3 && rc == LOBPCG_OK; ++r) rc = run();
+            cudaEventRecord(e1, L.stream);
+            float ms = 0.f;
+            if (rc == LOBPCG_OK &&
+                (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = fail(LOBPCG_ERR_CUDA, "autotune: timing failed");
+            if (rc != LOBPCG_OK) break;
+            if (best_b == 0 || ms < best) {
+                best = ms;
+                best_b = b;
+            }
+        }
+        budget = best_b;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->alloc.release(bx);
+    c->alloc.release(by);
+    if (rc == LOBPCG_OK) K.tuned = true;
+    return rc;
+}
+
 // One k-point on one lane: stage host vectors, add buffer bands, solve, copy back.
 static int solve_one(lobpcg_ctx *c, Lane &L, int k, int M, int nbuf, void *Xk, double *eig_k, double *res_k,
                      int &sw, Prof *prof, SolveCounters &cnt) {
@@ -1286,6 +1412,23 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         if (M + nb_extra > c->kp[k].npw)
             return fail(LOBPCG_ERR_ARG, "nbands (plus buffer bands) exceeds the plane-wave count");
         if (c->nproj > 0 && !c->kp[k].has_beta) return fail(LOBPCG_ERR_ARG, "projectors missing for a k-point");
+    }
+    double ms_tune = 0.0;
+    bool untuned = false;
+    for (int k = 0; k < c->nk; ++k) untuned = untuned || !c->kp[k].tuned;
+    if (c->opt.autotune && untuned) {  // first solve of the handle: tune each k-point on lane 0, timed apart
+        const auto ta = std::chrono::steady_clock::now();
+        if (c->lanes.empty()) {
+            std::unique_ptr<Lane> L(new Lane());
+            c->lanes.push_back(std::move(L));
+        }
+        Lane &L0 = *c->lanes[0];
+        L0.bind(&c->alloc, nullptr, 1);
+        L0.stream = c->stream;
+        const bool mixed = c->opt.precision == LOBPCG_MIXED;
+        const bool df = c->opt.fp64_gemm == 2 || (c->opt.fp64_gemm == 0 && mixed);
+        for (int k = 0; k < c->nk; ++k) LG_TRY(autotune_k(c, L0, k, df, m));
+        ms_tune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
     }
     const auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launch_count();
@@ -1367,6 +1510,7 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         st->block_visits_fp32 = cnt.visits32;
         st->block_visits_fp64 = cnt.visits64;
         st->block_visits_settled = cnt.settled;
+        st->ms_autotune = ms_tune;
         st->kernel_launches = launch_count() - l0;
         for (int l = 0; l < nl; ++l)
             for (int p = 0; p < LOBPCG_PH_COUNT; ++p) {

@@ -78,6 +78,31 @@ def test_solve_fp64_gemm_engines(precision, fp64_gemm):
         _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_graphs_and_autotune(precision):
+    """options.use_graph (the FP32 H W of the block iterations replayed from CUDA graphs, on a
+    non-default stream) and options.autotune give the same eigenpairs; the autotuner runs in
+    the first solve only and its time is reported apart."""
+    import torch
+    w = synth.tiny_workload(a=6.0, N=12, natoms=2, kpt=(0.25, 0.125, -0.375))
+    ref = np.loadtxt(os.path.join(GOLDEN, "tiny_kb_eig.txt"))
+    st = torch.cuda.Stream()
+    with make_solver(w, block_size=8, nline=4, max_sweeps=200, precision=precision, tol=1e-8, use_graph=True,
+                     autotune=True, stream=st) as s:
+        X = _start(w, s, M=24)
+        torch.cuda.synchronize()
+        res = s.solve([X])
+        assert res.status == 0
+        assert res.stats["ms_autotune"] > 0
+        _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
+        X2 = _start(w, s, M=24)
+        torch.cuda.synchronize()
+        res2 = s.solve([X2])
+        assert res2.status == 0 and res2.stats["ms_autotune"] == 0
+        assert np.abs(res2.eig - res.eig).max() < 1e-12
+        _check_result(w, s, X2, res2, ref, orth=1e-12 if precision == "fp64" else 1e-10)
+
+
 def test_solve_free_electron_degenerate():
     """V = 0, no projectors: the closed-form spectrum 1/2|k+G|^2 with its degenerate shells."""
     a, N = 6.0, 12
