@@ -571,10 +571,10 @@ struct Solver {
     // Rayleigh-Ritz on the pencil in S, A.  `tol` is the dependence threshold on the squared
     // Cholesky pivot of the unit-diagonal Gram: a kept direction amplifies the Gram's rounding
     // by 1/pivot^2, so tol is ~1e3 x the Gram's unit roundoff (FP64 Grams 1e-12, FP32 Grams 1e-3).
-    int rr(int nz, int mm, double tol) {
+    int rr(int nz, int mm, double tol, int lead = 0) {
         const double n3 = (double)nz * nz * nz;
         PhaseScope ps(prof, LOBPCG_PH_RR, 8.0 * (3.0 * n3 + 2.0 * nz * (double)nz * mm), 0.0, true);
-        return rayleigh_ritz(L->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s);
+        return rayleigh_ritz(L->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s, lead);
     }
     template <typename Ro, typename Ri>
     int cast(int cols, const cx<Ri> *a, cx<Ro> *b) {
@@ -658,7 +658,9 @@ struct Solver {
     // Rayleigh-Ritz of the mixed schedule: FP32 Gram blocks assembled into an FP64 pencil,
     // solved in FP64; the coefficients also come back in FP32 for the FP32 updates.
     int rr_mixed(int nz, int mm) {
-        LG_TRY(rr(nz, mm, drop_tol32));
+        // the assembled pencil has S = I on the X block and no X-W / X-P overlap (see
+        // assemble_gram_mixed): its Cholesky starts after that block
+        LG_TRY(rr(nz, mm, drop_tol32, m));
         // a Ritz vector's phase is free: make C's X-diagonal real positive, so that a step which
         // barely moves X_b has C_X close to I (see near_identity)
         LG_TRY(fix_phases(nz, mm, C, nz, s));

@@ -286,8 +286,10 @@ struct EigWork {
     bool df = false;
 };
 // Rayleigh-Ritz: lowest m pairs of A c = theta S c (n x n, ld n). See lobpcg_k_rayleigh_ritz.
+// lead (a multiple of 32): the first lead columns of S are known to be the identity's (an
+// orthonormal block orthogonal to the rest), so their factorisation is skipped.
 int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,
-                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s);
+                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s, int lead = 0);
 // The same Rayleigh-Ritz in FP32 arithmetic (complex64 pencil, float Ritz values).
 int rayleigh_ritz32(EigWork &w, int n, int m, const c32 *S, int lds, const c32 *A, int lda, double drop_tol,
                     float *theta, c32 *C, int ldc, int *ndropped, cudaStream_t s);

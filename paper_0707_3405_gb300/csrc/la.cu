@@ -215,6 +215,19 @@ k_chol_panel(int n, int k0, int kb, cx<RT> *__restrict__ L, const cx<RT> *__rest
     }
 }
 
+// Leading identity block (a basis whose first `lead` vectors are orthonormal and orthogonal to the
+// rest, as [X W P] of a mixed block iteration): its Cholesky factor and inverse are the identity.
+template <typename RT>
+__global__ void k_lead_identity(int n, int lead, cx<RT> *__restrict__ L, cx<RT> *__restrict__ Linv,
+                                int *__restrict__ dropped) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= n) return;
+    const cx<RT> v = mkc<RT>(i == j ? 1.0 : 0.0, 0.0);
+    L[(size_t)j * n + i] = v;
+    if (i < lead) Linv[(size_t)j * n + i] = v;
+    if (i == 0) dropped[j] = 0;
+}
+
 template <typename RT>
 __global__ void k_zero_dropped_rows(int n, cx<RT> *__restrict__ L, const int *__restrict__ dropped) {
     const int j = blockIdx.x;
@@ -623,10 +636,11 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
         for (int r = i + 1 + tid; r < n; r += blockDim.x)
             x[r] = ldcg_cx(cb + r) - mul_conj(w[r], vi1) - mul_conj(v[r], wi1);
         __syncthreads();
-        if (g == 0) {
-            for (int r = i + 1 + tid; r < n; r += blockDim.x) Hv[(size_t)i * n + r] = as_store<RT>(v[r]);
+        if (g == 0) {  // reflectors kept in the compute type (read by the back-transformation)
+            cx<CT> *HvC = reinterpret_cast<cx<CT> *>(Hv);
+            for (int r = i + 1 + tid; r < n; r += blockDim.x) HvC[(size_t)i * n + r] = v[r];
             if (tid == 0) {
-                taus[i] = as_store<RT>(R.tau);
+                reinterpret_cast<cx<CT> *>(taus)[i] = R.tau;
                 eg[i] = (RT)R.beta;
                 dg[i + 1] = (RT)x[i + 1].x;
             }
@@ -953,6 +967,48 @@ k_backtransform(int n, int m, const cx<RT> *__restrict__ Hv, const cx<RT> *__res
     for (int r = lane; r < n; r += 32) V[(size_t)j * ldv + r] = z[r];
 }
 
+// The same in double-FP32 for reflectors stored as pairs (the double-FP32 tridiagonalisation),
+// four warps per vector: one SM's FP64 units bound the one-warp FP64 version, while the pair
+// arithmetic spreads over the four FP32 sub-partitions.  Dot products: warp shuffles, then the
+// four warp sums in a fixed order (reproducible).
+template <typename RT>
+__global__ void __launch_bounds__(128)
+k_backtransform_df(int n, int m, const cx<df64> *__restrict__ Hv, const cx<df64> *__restrict__ taus,
+                   const RT *__restrict__ Z, cx<RT> *__restrict__ V, int ldv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<df64> *z = reinterpret_cast<cx<df64> *>(smraw);
+    __shared__ df64 red[2][4];
+    const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    if (j >= m) return;
+    for (int r = tid; r < n; r += 128) z[r] = mkc<df64>((df64)Z[(size_t)j * n + r], df64(0.f));
+    __syncthreads();
+    for (int i = n - 2; i >= 0; --i) {
+        const cx<df64> tau = taus[i];
+        if (tau.x == df64(0.f) && tau.y == df64(0.f)) continue;  // uniform
+        const int L = n - i - 1;
+        const cx<df64> *v = Hv + (size_t)i * n + i + 1;
+        df64 sre(0.f), sim(0.f);
+        for (int r = tid; r < L; r += 128) {
+            const cx<df64> a = v[r], b = z[i + 1 + r];
+            sre += a.x * b.x + a.y * b.y;
+            sim += a.x * b.y - a.y * b.x;
+        }
+        sre = warp_sum(sre);
+        sim = warp_sum(sim);
+        if (lane == 0) {
+            red[0][wp] = sre;
+            red[1][wp] = sim;
+        }
+        __syncthreads();
+        sre = ((red[0][0] + red[0][1]) + red[0][2]) + red[0][3];
+        sim = ((red[1][0] + red[1][1]) + red[1][2]) + red[1][3];
+        const cx<df64> ts = tau * mkc<df64>(sre, sim);
+        for (int r = tid; r < L; r += 128) z[i + 1 + r] = z[i + 1 + r] - ts * v[r];
+        __syncthreads();
+    }
+    for (int r = tid; r < n; r += 128) V[(size_t)j * ldv + r] = mkc<RT>((RT)z[r].x, (RT)z[r].y);
+}
+
 template <typename RT>
 __global__ void k_scale_rows_copy(int n, int m, const RT *__restrict__ d, const cx<RT> *__restrict__ T, int ldt,
                                   cx<RT> *__restrict__ C, int ldc) {
@@ -1007,7 +1063,7 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     unsigned int *cnt = reinterpret_cast<unsigned int *>(base + o_cnt);
     LG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n, s));
     LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(cx<RT>) * n, s));
-    bool coop_done = false;
+    bool coop_done = false, hv_df = false;
     if (n >= 2) {
         // fused version: tiles resident in shared memory, one grid barrier per column; 16 x 16
         // tiles for small matrices (more SMs share a column's FP64 work), else 32 x 32
@@ -1028,9 +1084,12 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
         const size_t static_sm = sizeof(RT) * 32 + sizeof(cx<RT>) * 16 * 33 + 64;
         int *err = device_wait_flag();
         const void *fn = small_tiles ? (const void *)k_tri_fused<RT, 16> : (const void *)k_tri_fused<RT, 32>;
+        bool fn_df = false;
         if constexpr (std::is_same<RT, double>::value) {
-            if (w.df)  // the column's vector work in double-FP32 (this GPU has few FP64 units per SM)
+            if (w.df) {  // the column's vector work in double-FP32 (this GPU has few FP64 units per SM)
                 fn = small_tiles ? (const void *)k_tri_fused<RT, 16, df64> : (const void *)k_tri_fused<RT, 32, df64>;
+                fn_df = true;
+            }
         }
         if (coop && err && dsm + static_sm <= (size_t)smem_max) {
             LG_TRY(allow_max_dyn_smem(fn));
@@ -1053,6 +1112,7 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
                 }
                 LG_TRY(check_launch("tridiagonalisation (fused cooperative)"));
                 coop_done = true;
+                hv_df = fn_df;  // reflectors stored as pairs
             }
         }
     }
@@ -1109,6 +1169,14 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     if (smem > 48 * 1024) {
         LG_TRY(allow_max_dyn_smem((const void *)k_backtransform<RT>));
     }
+    if constexpr (sizeof(cx<RT>) == sizeof(cx<df64>)) {
+        if (hv_df) {
+            if (smem > 48 * 1024) LG_TRY(allow_max_dyn_smem((const void *)k_backtransform_df<RT>));
+            k_backtransform_df<RT><<<m, 128, smem, s>>>(n, m, reinterpret_cast<const cx<df64> *>(Hv),
+                                                        reinterpret_cast<const cx<df64> *>(taus), Z, V, ldv);
+            return check_launch("back-transform (double-FP32)");
+        }
+    }
     k_backtransform<RT><<<m, 32, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
     return check_launch("back-transform");
 }
@@ -1122,7 +1190,7 @@ int hermitize_lower_t(EigWork &w, int n, cx<RT> *A, cudaStream_t s) {
 
 template <typename RT>
 int rayleigh_ritz_t(EigWork &w, int n, int m, const cx<RT> *S, int lds, const cx<RT> *A, int lda, double drop_tol,
-                    RT *theta, cx<RT> *C, int ldc, int *ndropped, cudaStream_t s) {
+                    RT *theta, cx<RT> *C, int ldc, int *ndropped, cudaStream_t s, int lead = 0) {
     if (n <= 0 || m <= 0) return LOBPCG_OK;
     if (m > n) return fail(LOBPCG_ERR_ARG, "rayleigh_ritz: m > n");
     if (n > 4096) return fail(LOBPCG_ERR_ARG, "rayleigh_ritz: n > 4096");
@@ -1155,8 +1223,13 @@ int rayleigh_ritz_t(EigWork &w, int n, int m, const cx<RT> *S, int lds, const cx
     LG_CUDA_TRY(cudaMemsetAsync(Li, 0, sizeof(cx<RT>) * (size_t)n * n, s));
     k_scale_gram<RT><<<dim3((n + 127) / 128, n), 128, 0, s>>>(n, S, lds, A, lda, Ss, As, d);
     LG_TRY(check_launch("scale gram"));
-    // blocked Cholesky with dropping (L overwrites Ss)
-    for (int k0 = 0; k0 < n; k0 += NBK) {
+    if (lead % NBK != 0 || lead > n || lead < 0) lead = 0;
+    if (lead > 0) {
+        k_lead_identity<RT><<<dim3((n + 127) / 128, lead), 128, 0, s>>>(n, lead, Ss, Li, dr);
+        LG_TRY(check_launch("leading identity"));
+    }
+    // blocked Cholesky with dropping (L overwrites Ss), after the leading identity columns
+    for (int k0 = lead; k0 < n; k0 += NBK) {
         const int kb = std::min(NBK, n - k0);
         bool chol_done = false;
         if constexpr (std::is_same<RT, double>::value) {
@@ -1210,8 +1283,8 @@ int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V
 }
 int hermitize_lower(EigWork &w, int n, z64 *A, cudaStream_t s) { return hermitize_lower_t<double>(w, n, A, s); }
 int rayleigh_ritz(EigWork &w, int n, int m, const z64 *S, int lds, const z64 *A, int lda, double drop_tol,
-                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s) {
-    return rayleigh_ritz_t<double>(w, n, m, S, lds, A, lda, drop_tol, theta, C, ldc, ndropped, s);
+                  double *theta, z64 *C, int ldc, int *ndropped, cudaStream_t s, int lead) {
+    return rayleigh_ritz_t<double>(w, n, m, S, lds, A, lda, drop_tol, theta, C, ldc, ndropped, s, lead);
 }
 int rayleigh_ritz32(EigWork &w, int n, int m, const c32 *S, int lds, const c32 *A, int lda, double drop_tol,
                     float *theta, c32 *C, int ldc, int *ndropped, cudaStream_t s) {
