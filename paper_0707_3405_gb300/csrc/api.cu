@@ -439,6 +439,7 @@ struct Solver {
     int k, npw, M, m, nblk;
     bool mixed;
     bool df = false;  // FP64-class tall GEMMs in double-FP32 arithmetic
+    double *part = nullptr;  // scratch of the per-column reductions (colsum_part_elems(nzmax))
     cudaStream_t s;
     z64 *X, *HX;             // all bands, FP64 (X is the caller's buffer)
     z64 *Z[2], *HZ[2];       // FP64 block bases [X W P] (mixed: only the X part)
@@ -468,7 +469,7 @@ struct Solver {
         if (verbose < 2) return;
         dbg.assign(2 * nb + 1, 0.0);
         double *dres = res;
-        column_resid_norms(npw, nb, Xb, npw, HXb, npw, theta, dres, s);
+        column_resid_norms(npw, nb, Xb, npw, HXb, npw, theta, dres, part, s);
         cudaMemcpyAsync(dbg.data(), dres, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(dbg.data() + nb, theta, sizeof(double) * nb, cudaMemcpyDeviceToHost, s);
         int nd = 0;
@@ -630,7 +631,7 @@ struct Solver {
             z64 *W = col(Zc, m), *HW = col(HZc, m);
             {   // steps 2-3: R = HX - X Upsilon, W = K(R)
                 PhaseScope ps(prof, LOBPCG_PH_UPDATE, 20.0 * npw * m, cbytes64(3.0 * m), true);
-                LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, c->kp[k].kin64, W, npw, work, s));
+                LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, c->kp[k].kin64, W, npw, work, part, s));
             }
             LG_TRY(constrain64(W, m, b * m));
             LG_TRY(applyH64(W, HW, m));
@@ -669,7 +670,7 @@ struct Solver {
     }
     int ritz_values(const z64 *Xb, const z64 *HXb) {
         PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * m, cbytes64(2.0 * m), true);
-        return rayleigh_quotients(npw, m, Xb, npw, HXb, npw, theta, s);
+        return rayleigh_quotients(npw, m, Xb, npw, HXb, npw, theta, part, s);
     }
 
     // nline: Algorithm 1 iterations after the block start (0 for a block already converged far
@@ -725,7 +726,7 @@ struct Solver {
             LG_TRY(constrain32(R32, m, X32, m, LOBPCG_PH_UPDATE));
             {   // step 3: W = K(R)
                 PhaseScope ps(prof, LOBPCG_PH_UPDATE, 10.0 * npw * m, cbytes64(m) + 2.0 * cbytes32(m), false);
-                LG_TRY(precond32(npw, m, Xb, npw, c->kp[k].kin64, R32, npw, W32, npw, work, s));
+                LG_TRY(precond32(npw, m, Xb, npw, c->kp[k].kin64, R32, npw, W32, npw, work, part, s));
             }
             LG_TRY(constrain32(W32, m, X32all, j0, LOBPCG_PH_CONSTRAINT));
             LG_TRY(constrain32(W32, m, X32, m, LOBPCG_PH_UPDATE));
@@ -815,7 +816,7 @@ struct Solver {
         {
             PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * m, cbytes64(2.0 * m), true);
             LG_TRY(assemble_gram_mixed(m, 0, S32, m, A32, m, nullptr, S, A, s));
-            LG_TRY(diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, s));
+            LG_TRY(diag_pencil(npw, m, Xb, npw, HXb, npw, S, A, part, s));
         }
         LG_TRY(rr(m, m, drop_tol32));
         {
@@ -889,7 +890,7 @@ struct Solver {
         }
         {
             PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * M, cbytes64(2.0 * M), true);
-            LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
+            LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, part, s));
         }
         if (mixed) {
             LG_TRY(cast<float, double>(M, X, X32all));
@@ -908,7 +909,7 @@ struct Solver {
         {
             PhaseScope ps(prof, LOBPCG_PH_RR, 16.0 * npw * M, cbytes64(2.0 * M), true);
             LG_TRY(assemble_gram_mixed(M, 0, S32, M, A32, M, nullptr, S, A, s));
-            LG_TRY(diag_pencil(npw, M, X, npw, HX, npw, S, A, s));
+            LG_TRY(diag_pencil(npw, M, X, npw, HX, npw, S, A, part, s));
         }
         LG_TRY(rr(M, M, drop_tol32));
         {
@@ -923,7 +924,7 @@ struct Solver {
         LG_TRY(copy32(HX32all, T32, M));
         {
             PhaseScope ps(prof, LOBPCG_PH_UPDATE, 8.0 * npw * M, cbytes64(2.0 * M), true);
-            LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, s));
+            LG_TRY(column_resid_norms(npw, M, X, npw, HX, npw, theta, res, part, s));
         }
         return fetch_results(eig_h, res_h);
     }
@@ -983,9 +984,10 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     sv.G = carve<z64>(c, L.Gc, (size_t)M * m, rc); LG_TRY(rc);
     sv.theta = carve<double>(c, L.dtheta, nzmax, rc); LG_TRY(rc);
     sv.res = carve<double>(c, L.dres, nzmax, rc); LG_TRY(rc);
-    double *w = carve<double>(c, L.dwork, 4 * (size_t)nzmax + 64, rc); LG_TRY(rc);
+    double *w = carve<double>(c, L.dwork, 4 * (size_t)nzmax + 64 + colsum_part_elems(nzmax), rc); LG_TRY(rc);
     sv.work = w;
     sv.ndrop = reinterpret_cast<int *>(w + 4 * (size_t)nzmax);
+    sv.part = w + 4 * (size_t)nzmax + 64;  // partial sums of the per-column reductions
     if (sv.mixed) {
         sv.X32all = carve<c32>(c, L.X32all, (size_t)npw * M, rc); LG_TRY(rc);
         sv.HX32all = carve<c32>(c, L.HX32all, (size_t)npw * M, rc); LG_TRY(rc);

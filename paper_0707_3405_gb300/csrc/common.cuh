@@ -301,25 +301,27 @@ int heev_lowest(EigWork &w, int n, int m, z64 *A, int lda, double *theta, z64 *V
 // ------------------------------------------------------------------ vector kernels
 template <typename R>
 int residual_precond(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
-                     const double *kin, cx<R> *W, int ldw, double *work, cudaStream_t s);
+                     const double *kin, cx<R> *W, int ldw, double *work, double *part, cudaStream_t s);
 // Mixed schedule: R = HX - X theta (FP64) stored in FP32, and W = K(R) in FP32.
 int residual_precond_mixed(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
-                           const double *kin, c32 *R, c32 *W, int ld, double *work, cudaStream_t s);
+                           const double *kin, c32 *R, c32 *W, int ld, double *work, double *part, cudaStream_t s);
 // V += alpha D (FP64 columns).
 int axpy_cols(int rows, int cols, double alpha, const z64 *D, int ldd, z64 *V, int ldv, cudaStream_t s);
 // Assemble the FP64 Rayleigh-Ritz pencil of the mixed schedule (see api.cu).
 int assemble_gram_mixed(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
                         z64 *S, z64 *A, cudaStream_t s);
 // Overwrite diag(S) = diag(X^H X), diag(A) = diag(X^H HX) in FP64 (m x m, ld m).
-int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, cudaStream_t s);
+int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, double *part,
+                cudaStream_t s);
 // Deterministic pseudo-random complex entries in [-1, 1) (buffer-band start vectors).
 int fill_random(int rows, int cols, z64 *X, int ldx, unsigned seed, cudaStream_t s);
 int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
-                       double *out, cudaStream_t s);
+                       double *out, double *part, cudaStream_t s);
 // FP32-output pencil assembly, FP64 Rayleigh quotients, FP32 residual and preconditioner (mixed schedule).
 int assemble_gram_mixed32(int nz, int mx, const c32 *S32, int lds32, const c32 *A32, int lda32, const double *theta,
                           c32 *S, c32 *A, cudaStream_t s);
-int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, cudaStream_t s);
+int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, double *part,
+                       cudaStream_t s);
 // E = C - I (leading rows x cols, FP32) and its largest component magnitude on the host (synchronises).
 int near_identity32(int rows, int cols, const z64 *C, int ldc, c32 *E, int lde, unsigned int *dmax, float *hmax,
                     cudaStream_t s);
@@ -330,7 +332,11 @@ int add_cast(int rows, int cols, const z64 *A, int lda, const c32 *T, int ldt, z
 int residual32(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta, c32 *R, int ldr,
                cudaStream_t s);
 int precond32(int npw, int m, const z64 *X, int ldx, const double *kin, const c32 *R, int ldr, c32 *W, int ldw,
-              double *work, cudaStream_t s);
+              double *work, double *part, cudaStream_t s);
+// Per-column sums (kinetic energies, Rayleigh quotients, pencil diagonals, residual norms) take a
+// scratch `part` of colsum_part_elems(m) doubles: their rows are split over many blocks and the
+// partials added in a fixed order.  part = NULL: one block per column.
+size_t colsum_part_elems(int m);
 template <typename Ro, typename Ri>
 int copy_cast(int rows, int cols, const cx<Ri> *A, int lda, cx<Ro> *B, int ldb, cudaStream_t s);
 int scale_rows_real(int rows, int cols, const double *d, z64 *A, int lda, cudaStream_t s);

@@ -34,6 +34,84 @@ __device__ void block_sum2(double &a, double &b) {
     b = tb;
 }
 
+// ------------------------------------------------------------------ per-column sums
+// Two sums per column over the plane waves, split over chunks of rows so that the FP64 work of
+// a few columns spreads over the whole GPU (one block per column would leave it to that block's
+// SM, whose FP64 units are few); the chunk partials are added in a fixed order (reproducible).
+enum ColOp { kEkin = 0, kRayleigh = 1, kDiag = 2, kResid = 3 };
+constexpr int kMaxChunks = 32;
+
+template <int OP>
+__global__ void __launch_bounds__(256)
+k_colsum2(int npw, int chunk, const z64 *__restrict__ X, int ldx, const z64 *__restrict__ HX, int ldhx,
+          const double *__restrict__ kin, const double *__restrict__ theta, double *__restrict__ part) {
+    const int c = blockIdx.x, j = blockIdx.y, nch = gridDim.x;
+    const int g0 = c * chunk, g1 = min(npw, g0 + chunk);
+    const z64 *x = X + (size_t)j * ldx;
+    const z64 *h = (OP == kEkin) ? nullptr : HX + (size_t)j * ldhx;
+    const double th = (OP == kResid) ? theta[j] : 0.0;
+    double a = 0.0, b = 0.0;
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        const z64 xv = x[g];
+        const double xx = abs2(xv);
+        if (OP == kEkin) {
+            a += kin[g] * xx;
+            b += xx;
+        } else if (OP == kResid) {
+            const z64 hv = h[g];
+            const double p = hv.x - th * xv.x, q = hv.y - th * xv.y;
+            a += p * p + q * q;
+            b += xx;
+        } else {
+            const z64 hv = h[g];
+            a += xx;
+            b += xv.x * hv.x + xv.y * hv.y;
+        }
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        part[((size_t)j * nch + c) * 2] = a;
+        part[((size_t)j * nch + c) * 2 + 1] = b;
+    }
+}
+
+template <int OP>
+__global__ void k_colsum2_finish(int m, int nch, const double *__restrict__ part, double *__restrict__ out,
+                                 z64 *__restrict__ S, z64 *__restrict__ A, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c < nch; ++c) {
+        a += part[((size_t)j * nch + c) * 2];
+        b += part[((size_t)j * nch + c) * 2 + 1];
+    }
+    if (OP == kEkin) out[j] = b > 0.0 ? a / b : 1.0;
+    else if (OP == kRayleigh) out[j] = a > 0.0 ? b / a : 0.0;
+    else if (OP == kDiag) {
+        S[(size_t)j * n + j] = mkc(a, 0.0);
+        A[(size_t)j * n + j] = mkc(b, 0.0);
+    } else out[j] = b > 0.0 ? sqrt(a / b) : 0.0;
+}
+
+// Chunks per column for m columns of npw rows: about four blocks per SM in all, at least 2048 rows
+// per chunk.
+int col_chunks(int npw, int m) {
+    int nch = (4 * 152 + m - 1) / std::max(1, m);
+    nch = std::min(nch, (npw + 2047) / 2048);
+    return std::max(1, std::min(nch, kMaxChunks));
+}
+
+template <int OP>
+int colsum2(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *kin, const double *theta,
+            double *part, double *out, z64 *S, z64 *A, int n, cudaStream_t s) {
+    const int nch = col_chunks(npw, m);
+    const int chunk = (npw + nch - 1) / nch;
+    k_colsum2<OP><<<dim3(nch, m), 256, 0, s>>>(npw, chunk, X, ldx, HX, ldhx, kin, theta, part);
+    LG_TRY(check_launch("column sums"));
+    k_colsum2_finish<OP><<<(m + 127) / 128, 128, 0, s>>>(m, nch, part, out, S, A, n);
+    return check_launch("column sums (finish)");
+}
+
 // Kinetic energy of each band, Ekin_i = sum T |x|^2 / sum |x|^2 (one block per column).
 __global__ void __launch_bounds__(256)
 k_ekin(int npw, const z64 *__restrict__ X, int ldx, const double *__restrict__ kin, double *__restrict__ ekin) {
@@ -241,22 +319,30 @@ int grid_for(size_t n, int threads) {
 
 }  // namespace
 
+size_t colsum_part_elems(int m) { return 2 * (size_t)std::max(m, 1) * kMaxChunks; }
+
+// Ekin of each column into ekin[0..m)
+static int ekin_cols(int npw, int m, const z64 *X, int ldx, const double *kin, double *ekin, double *part,
+                     cudaStream_t s) {
+    if (part) return colsum2<kEkin>(npw, m, X, ldx, nullptr, 0, kin, nullptr, part, ekin, nullptr, nullptr, 0, s);
+    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, ekin);
+    return check_launch("ekin");
+}
+
 template <typename R>
 int residual_precond(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
-                     const double *kin, cx<R> *W, int ldw, double *work, cudaStream_t s) {
+                     const double *kin, cx<R> *W, int ldw, double *work, double *part, cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
-    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, work);
-    LG_TRY(check_launch("ekin"));
+    LG_TRY(ekin_cols(npw, m, X, ldx, kin, work, part, s));
     const int gx = std::max(1, std::min((npw + 255) / 256, 64));
     k_resid_precond<R><<<dim3(gx, m), 256, 0, s>>>(npw, m, X, ldx, HX, ldhx, theta, kin, work, W, ldw);
     return check_launch("residual/preconditioner");
 }
 
 int residual_precond_mixed(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
-                           const double *kin, c32 *R, c32 *W, int ld, double *work, cudaStream_t s) {
+                           const double *kin, c32 *R, c32 *W, int ld, double *work, double *part, cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
-    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, work);
-    LG_TRY(check_launch("ekin"));
+    LG_TRY(ekin_cols(npw, m, X, ldx, kin, work, part, s));
     const int gx = std::max(1, std::min((npw + 255) / 256, 64));
     k_resid_precond_mixed<<<dim3(gx, m), 256, 0, s>>>(npw, m, X, ldx, HX, ldhx, theta, kin, work, R, W, ld);
     return check_launch("residual/preconditioner (mixed)");
@@ -280,8 +366,10 @@ int assemble_gram_mixed32(int nz, int mx, const c32 *S32, int lds32, const c32 *
     return check_launch("assemble gram (fp32)");
 }
 
-int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, cudaStream_t s) {
+int rayleigh_quotients(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, double *theta, double *part,
+                       cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
+    if (part) return colsum2<kRayleigh>(npw, m, X, ldx, HX, ldhx, nullptr, nullptr, part, theta, nullptr, nullptr, 0, s);
     k_rayleigh_quotients<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, theta);
     return check_launch("rayleigh quotients");
 }
@@ -295,17 +383,18 @@ int residual32(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, c
 }
 
 int precond32(int npw, int m, const z64 *X, int ldx, const double *kin, const c32 *R, int ldr, c32 *W, int ldw,
-              double *work, cudaStream_t s) {
+              double *work, double *part, cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
-    k_ekin<<<m, 256, 0, s>>>(npw, X, ldx, kin, work);
-    LG_TRY(check_launch("ekin"));
+    LG_TRY(ekin_cols(npw, m, X, ldx, kin, work, part, s));
     const int gx = std::max(1, std::min((npw + 255) / 256, 64));
     k_precond32<<<dim3(gx, m), 256, 0, s>>>(npw, R, ldr, kin, work, W, ldw);
     return check_launch("preconditioner (fp32)");
 }
 
-int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, cudaStream_t s) {
+int diag_pencil(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, z64 *S, z64 *A, double *part,
+                cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
+    if (part) return colsum2<kDiag>(npw, m, X, ldx, HX, ldhx, nullptr, nullptr, part, nullptr, S, A, m, s);
     k_diag_pencil<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, S, A, m);
     return check_launch("diagonal of the pencil");
 }
@@ -329,8 +418,9 @@ int fill_random(int rows, int cols, z64 *X, int ldx, unsigned seed, cudaStream_t
 }
 
 int column_resid_norms(int npw, int m, const z64 *X, int ldx, const z64 *HX, int ldhx, const double *theta,
-                       double *out, cudaStream_t s) {
+                       double *out, double *part, cudaStream_t s) {
     if (m <= 0) return LOBPCG_OK;
+    if (part) return colsum2<kResid>(npw, m, X, ldx, HX, ldhx, nullptr, theta, part, out, nullptr, nullptr, 0, s);
     k_resid_norm<<<m, 256, 0, s>>>(npw, X, ldx, HX, ldhx, theta, out);
     return check_launch("residual norms");
 }
@@ -426,9 +516,9 @@ int add_cast(int rows, int cols, const z64 *A, int lda, const c32 *T, int ldt, z
 }
 
 template int residual_precond<double>(int, int, const z64 *, int, const z64 *, int, const double *, const double *,
-                                      z64 *, int, double *, cudaStream_t);
+                                      z64 *, int, double *, double *, cudaStream_t);
 template int residual_precond<float>(int, int, const z64 *, int, const z64 *, int, const double *, const double *,
-                                     c32 *, int, double *, cudaStream_t);
+                                     c32 *, int, double *, double *, cudaStream_t);
 template int copy_cast<double, double>(int, int, const z64 *, int, z64 *, int, cudaStream_t);
 template int copy_cast<float, double>(int, int, const z64 *, int, c32 *, int, cudaStream_t);
 template int copy_cast<double, float>(int, int, const c32 *, int, z64 *, int, cudaStream_t);
