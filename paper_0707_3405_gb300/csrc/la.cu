@@ -167,19 +167,32 @@ k_chol_diag(int n, int k0, int kb, cx<RT> *__restrict__ L, cx<RT> *__restrict__ 
         if (c < r && dflag[r]) T[r][c] = mkc<CT>(0.0, 0.0);
     }
     __syncthreads();
-    // inverse of the lower-triangular block (real positive diagonal), row by row:
-    // I[r][c] = -(1 / T[r][r]) sum_{l=c}^{r-1} T[r][l] I[l][c], thread c for column c
-    for (int r = 0; r < kb; ++r) {
-        if (tid < r) {
-            const int c = tid;
-            cx<CT> s = mkc<CT>(0.0, 0.0);
-            for (int l = c; l < r; ++l) s = s + T[r][l] * I[l][c];
-            I[r][c] = ((CT)(-1.0) / T[r][r].x) * s;
-        } else if (tid == r) {
-            I[r][r] = mkc<CT>((CT)1.0 / T[r][r].x, 0.0);
+    // inverse of the lower-triangular block (real positive diagonal) by forward substitution,
+    // column c on the 8 lanes of one warp segment: I[r][c] = -(1 / T[r][r]) sum_{l=c}^{r-1} T[r][l] I[l][c],
+    // each lane taking every 8th l, the segment adding its partial sums by shuffles (fixed order)
+    __shared__ CT rdiag[NBK];
+    if (tid < kb) rdiag[tid] = (CT)1.0 / T[tid][tid].x;
+    __syncthreads();
+    {
+        const int c = tid >> 3, sub = tid & 7;
+        const bool on = c < kb;
+        for (int r = 0; r < kb; ++r) {
+            cx<CT> sacc = mkc<CT>(0.0, 0.0);
+            if (on && c < r)
+                for (int l = c + sub; l < r; l += 8) sacc = sacc + T[r][l] * I[l][c];
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+                sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+            }
+            if (on && sub == 0) {
+                if (c < r) I[r][c] = (-rdiag[r]) * sacc;
+                else if (c == r) I[r][r] = mkc<CT>(rdiag[r], 0.0);
+            }
+            __syncwarp();
         }
-        __syncthreads();
     }
+    __syncthreads();
     for (int e = tid; e < kb * kb; e += blockDim.x) {
         const int r = e % kb, c = e / kb;
         L[(size_t)(k0 + c) * n + k0 + r] = (r >= c) ? as_store<RT>(T[r][c]) : mkc<RT>(0.0, 0.0);
