@@ -179,6 +179,23 @@ struct Lane {
         const void *t2 = nullptr, *nlb = nullptr, *part = nullptr;
     };
     std::map<std::tuple<int, const void *, void *, int>, Graph> graphs;
+    // Beside a full mixed sweep, each block's FP64-class H X is recomputed on a side stream with its
+    // own scratch (side) into HXr, overlapping the latency-bound Rayleigh-Ritz steps of the later
+    // blocks; the sweep end swaps it in.
+    DevBuf HXr;
+    std::unique_ptr<Lane> side;
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+    int make_side(Allocator *a) {
+        if (!side) {
+            side.reset(new Lane());
+            LG_CUDA_TRY(cudaStreamCreateWithFlags(&side->stream, cudaStreamNonBlocking));
+            side->own_stream = true;
+        }
+        side->bind(a, nullptr, 1);
+        if (!ev_main) LG_CUDA_TRY(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
+        if (!ev_side) LG_CUDA_TRY(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
+        return LOBPCG_OK;
+    }
     void clear_graphs() {
         for (auto &g : graphs)
             if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
@@ -198,6 +215,15 @@ struct Lane {
                           &Xext, &T32, &E32};
         clear_graphs();
         for (DevBuf *b : bufs) a.release(*b);
+        a.release(HXr);
+        if (side) {
+            if (side->stream) cudaStreamSynchronize(side->stream);
+            side->release(a);
+            side.reset();
+        }
+        if (ev_main) cudaEventDestroy(ev_main);
+        if (ev_side) cudaEventDestroy(ev_side);
+        ev_main = ev_side = nullptr;
         if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
     }
@@ -442,6 +468,8 @@ struct Solver {
     double *part = nullptr;  // scratch of the per-column reductions (colsum_part_elems(nzmax))
     cudaStream_t s;
     z64 *X, *HX;             // all bands, FP64 (X is the caller's buffer)
+    z64 *HXr = nullptr;      // side-stream H X of the current full sweep (see Lane::side)
+    bool hxr_ready = false;  // every block's side refresh of this sweep is queued
     z64 *Z[2], *HZ[2];       // FP64 block bases [X W P] (mixed: only the X part)
     z64 *Tmp;                // npw x max(M, m) FP64 scratch
     z64 *S, *A, *C;          // Gram / projected / coefficient matrices, FP64
@@ -863,9 +891,25 @@ struct Solver {
         return LOBPCG_OK;
     }
     // Rayleigh-Ritz over all M bands closing a sweep (Sec. 3.2), then FP64 residuals.
+    // After block b's visit (X_b final for this sweep): H X_b on the side stream into HXr.
+    int side_refresh(int b) {
+        Lane &R = *L->side;
+        LG_CUDA_TRY(cudaEventRecord(L->ev_main, s));
+        LG_CUDA_TRY(cudaStreamWaitEvent(R.stream, L->ev_main, 0));
+        applies64 += m;
+        return apply_H_dev<double>(c, R, k, col(X, b * m), npw, col(HXr, b * m), npw, m, nullptr, df);
+    }
     int final_rr(double *eig_h, double *res_h) {
         if (early) return final_rr_early(eig_h, res_h);
-        if (mixed) LG_TRY(applyH64(X, HX, M));  // FP64 H X for the residual test
+        if (mixed && hxr_ready) {
+            // FP64 H X for the residual test: the side stream's, computed block by block
+            LG_CUDA_TRY(cudaEventRecord(L->ev_side, L->side->stream));
+            LG_CUDA_TRY(cudaStreamWaitEvent(s, L->ev_side, 0));
+            std::swap(HX, HXr);
+            hxr_ready = false;
+        } else if (mixed) {
+            LG_TRY(applyH64(X, HX, M));
+        }
         LG_TRY(gram64(M, X, X, S));
         LG_TRY(gram64(M, X, HX, A));
         LG_TRY(rr(M, M, drop_tol));
@@ -951,6 +995,13 @@ struct SolveCounters {
 int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h, int &sweeps_done,
             Prof *prof, SolveCounters &cnt) {
     L.clear_graphs();  // buffers may have moved since an earlier solve
+    // whatever way this returns, no side-stream work (reading X) outlives it
+    struct SideSync {
+        Lane &L;
+        ~SideSync() {
+            if (L.side && L.side->stream) cudaStreamSynchronize(L.side->stream);
+        }
+    } side_sync{L};
     Solver sv;
     sv.c = c;
     sv.L = &L;
@@ -977,6 +1028,10 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
         sv.HZ[i] = carve<z64>(c, L.HZb[i], (size_t)npw * zcols, rc); LG_TRY(rc);
     }
     sv.HX = carve<z64>(c, L.HXall, (size_t)npw * M, rc); LG_TRY(rc);
+    if (c->opt.precision == LOBPCG_MIXED) {
+        sv.HXr = carve<z64>(c, L.HXr, (size_t)npw * M, rc); LG_TRY(rc);
+        LG_TRY(L.make_side(&c->alloc));
+    }
     sv.Tmp = carve<z64>(c, L.Tmp, (size_t)npw * M, rc); LG_TRY(rc);
     sv.S = carve<z64>(c, L.Gram, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
     sv.A = carve<z64>(c, L.Gram2, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
@@ -1018,16 +1073,24 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     // per block: H X_b holds FP64 accuracy (false after an early visit or an early sweep end)
     std::vector<char> hx64(sv.nblk, 1);
     for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
+        // Early visits (FP32 block start and X updates) only while every band of the block is
+        // above mixed_early: bands nearer the FP32 noise of H X (~1e-7 |H|) get W directions
+        // made of that noise, and their Rayleigh-Ritz steps then drop most of [W P] and lose
+        // the block (seen with 2048 bands, whose lowest blocks converge sweeps before the top).
+        std::vector<char> early_b(sv.nblk, 0);
         bool all_early = sv.mixed;
         for (int b = 0; b < sv.nblk; ++b) {
             double rmin = HUGE_VAL;
             for (int i = b * m; i < (b + 1) * m; ++i) rmin = std::min(rmin, res_prev[i]);
-            // Early visits (FP32 block start and X updates) only while every band of the block is
-            // above mixed_early: bands nearer the FP32 noise of H X (~1e-7 |H|) get W directions
-            // made of that noise, and their Rayleigh-Ritz steps then drop most of [W P] and lose
-            // the block (seen with 2048 bands, whose lowest blocks converge sweeps before the top).
-            sv.early = sv.mixed && c->opt.mixed_early > 0.0 && rmin > c->opt.mixed_early;
-            all_early = all_early && sv.early;
+            early_b[b] = sv.mixed && c->opt.mixed_early > 0.0 && rmin > c->opt.mixed_early;
+            all_early = all_early && early_b[b];
+        }
+        // a full sweep end needs H X of every block in FP64 class: computed beside the sweep
+        const bool side = sv.mixed && !all_early;
+        for (int b = 0; b < sv.nblk; ++b) {
+            double rmin = HUGE_VAL;
+            for (int i = b * m; i < (b + 1) * m; ++i) rmin = std::min(rmin, res_prev[i]);
+            sv.early = early_b[b] != 0;
             if (sv.mixed && !sv.early && !hx64[b]) {
                 // first full visit after early ones: H X_b in FP64 from X_b (its FP32 noise would
                 // dominate the residuals of well converged bands)
@@ -1051,9 +1114,11 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
                 if (sv.mixed) LG_TRY(sv.refresh32(b));
                 ++cnt.visits64;
             }
+            if (side) LG_TRY(sv.side_refresh(b));
         }
+        sv.hxr_ready = side;
         // the sweep-end Rayleigh-Ritz runs on the FP32 copies only if every block was early; else
-        // it refreshes H X in FP64 first
+        // it takes the FP64 H X computed beside the sweep
         sv.early = all_early;
         if (all_early) std::fill(hx64.begin(), hx64.end(), 0);
         else std::fill(hx64.begin(), hx64.end(), 1);
