@@ -184,11 +184,15 @@ struct Lane {
     // blocks; the sweep end swaps it in.
     DevBuf HXr;
     std::unique_ptr<Lane> side;
+    cudaStream_t solve_stream = nullptr;  // lane 0's own high-priority stream during a solve
     cudaEvent_t ev_main = nullptr, ev_side = nullptr;
     int make_side(Allocator *a) {
         if (!side) {
+            // lowest priority: its blocks fill the gaps the solve's own kernels leave
+            int least = 0, greatest = 0;
+            LG_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
             side.reset(new Lane());
-            LG_CUDA_TRY(cudaStreamCreateWithFlags(&side->stream, cudaStreamNonBlocking));
+            LG_CUDA_TRY(cudaStreamCreateWithPriority(&side->stream, cudaStreamNonBlocking, least));
             side->own_stream = true;
         }
         side->bind(a, nullptr, 1);
@@ -224,6 +228,8 @@ struct Lane {
         if (ev_main) cudaEventDestroy(ev_main);
         if (ev_side) cudaEventDestroy(ev_side);
         ev_main = ev_side = nullptr;
+        if (solve_stream) cudaStreamDestroy(solve_stream);
+        solve_stream = nullptr;
         if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
     }
@@ -1502,22 +1508,33 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
     const auto t0 = std::chrono::steady_clock::now();
     const long long l0 = launch_count();
     const int nbuf = c->opt.nbuf > 0 ? ((c->opt.nbuf + m - 1) / m) * m : 0;
-    // lanes: lane 0 is the handle's stream; more lanes (own streams) for a multi-k solve
+    // lanes: one per concurrent k-point, each on its own high-priority stream (so that the
+    // low-priority side streams of the H X refresh only fill the gaps), all ordered after the work
+    // already queued on the handle's stream; lane 0 returns to the handle's stream afterwards
     const int nl = std::max(1, std::min(c->nk, kMaxLanes));
+    int least = 0, greatest = 0;
+    LG_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    if (c->lanes.empty()) c->lanes.push_back(std::unique_ptr<Lane>(new Lane()));
     while ((int)c->lanes.size() < nl) {
         std::unique_ptr<Lane> L(new Lane());
-        LG_CUDA_TRY(cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking));
+        LG_CUDA_TRY(cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking, greatest));
         L->own_stream = true;
         c->lanes.push_back(std::move(L));
     }
+    if (!c->lanes[0]->solve_stream)
+        LG_CUDA_TRY(cudaStreamCreateWithPriority(&c->lanes[0]->solve_stream, cudaStreamNonBlocking, greatest));
     for (int l = 0; l < nl; ++l) c->lanes[l]->bind(&c->alloc, nl > 1 ? &c->gate : nullptr, nl);
-    c->lanes[0]->stream = c->stream;
+    c->lanes[0]->stream = c->lanes[0]->solve_stream;
+    struct Lane0Back {  // lane 0 serves lobpcg_apply_H on the handle's stream
+        lobpcg_ctx *c;
+        ~Lane0Back() {
+            cudaStreamSynchronize(c->lanes[0]->solve_stream);
+            c->lanes[0]->stream = c->stream;
+        }
+    } lane0_back{c};
     c->gate.used = false;
-    if (nl > 1) {
-        // the other lanes start after the work already queued on the handle's stream
-        LG_CUDA_TRY(cudaEventRecord(c->gate.ev, c->stream));
-        for (int l = 1; l < nl; ++l) LG_CUDA_TRY(cudaStreamWaitEvent(c->lanes[l]->stream, c->gate.ev, 0));
-    }
+    LG_CUDA_TRY(cudaEventRecord(c->gate.ev, c->stream));
+    for (int l = 0; l < nl; ++l) LG_CUDA_TRY(cudaStreamWaitEvent(c->lanes[l]->stream, c->gate.ev, 0));
     std::vector<Prof> profs(nl);
     std::vector<SolveCounters> cnts(nl);
     std::vector<int> sweeps_k(c->nk, 0), rc_k(c->nk, LOBPCG_OK);
