@@ -39,9 +39,11 @@
  * Ownership and streams
  *   - The library copies the potential, projectors and energies at create
  *     and owns every device buffer it allocates; it never frees caller memory.
- *   - All device work is enqueued on the CUDA stream given at create
- *     (lobpcg_set_stream changes it); calls return after enqueueing unless
- *     stated otherwise.
+ *   - lobpcg_apply_H enqueues on the CUDA stream given at create
+ *     (lobpcg_set_stream changes it) and returns after enqueueing.
+ *     lobpcg_solve runs after the work already queued on that stream, on
+ *     library streams (one per concurrent k-point, high priority, plus
+ *     low-priority side streams), and returns synchronised.
  *   - A handle is not thread-safe: one host thread at a time per handle.
  *
  * Errors
@@ -110,7 +112,7 @@ typedef struct {
                             the time it took (not included in ms_total). */
     double tol;          /* convergence: max_i ||H x_i - theta_i x_i||_2 <= tol (Ha), ||x_i|| = 1 */
     long long mem_cap;   /* 0: no cap; else maximum bytes the handle may allocate (ERR_OOM above it) */
-    int    timing;       /* 1: time each phase of lobpcg_solve with CUDA events on the handle's stream */
+    int    timing;       /* 1: time each phase of lobpcg_solve with CUDA events on its lane streams */
     int    nbuf;         /* extra buffer bands iterated above the M requested ones but not required to
                             converge (rounded up to whole blocks; 0 = none).  They give the top wanted
                             bands a gap to the unresolved spectrum. */
@@ -149,7 +151,7 @@ typedef struct {
     long long band_applies_fp32;  /* single-band H applications done in FP32 */
     long long kernel_launches;    /* kernels launched by the solve */
     /* per phase (index LOBPCG_PH_*), filled when options.timing = 1: */
-    double    ph_ms[LOBPCG_PH_COUNT];      /* device time, CUDA events on the handle's stream */
+    double    ph_ms[LOBPCG_PH_COUNT];      /* device time, CUDA events on the lane streams (summed) */
     double    ph_flops[LOBPCG_PH_COUNT];   /* algorithmic floating-point operations */
     double    ph_bytes[LOBPCG_PH_COUNT];   /* algorithmic DRAM bytes */
     long long ph_calls[LOBPCG_PH_COUNT];   /* timed calls */
