@@ -56,8 +56,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the warm-up and timed steps of --mode, no other legs")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply"],
-                    help="with --ncu: LOBPCG sweeps, full solves to --tol, or standalone apply_H on all bands")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply", "apply_df32"],
+                    help="with --ncu: LOBPCG sweeps, full solves to --tol, standalone apply_H, or the "
+                         "double-FP32 apply_H of the FP64-class H X")
+    ap.add_argument("--nb", type=int, default=0, help="with --ncu and an apply mode: bands (0 = all)")
     return ap.parse_args()
 
 
@@ -74,6 +76,8 @@ def ncu_run(args):
     else:
         s = solver_for(w, args.precision, timing=False, max_sweeps=1, tol=1e-30, nbuf=args.nbuf)
     X = start_block(w, s)
+    if args.mode.startswith("apply") and args.nb > 0:
+        X = X[:args.nb].contiguous()
     if args.mode == "apply" and args.precision == "mixed":
         X = X.to(torch.complex64)
     Y = torch.empty_like(X)
@@ -83,7 +87,7 @@ def ncu_run(args):
         if args.mode in ("sweep", "solve"):
             s.solve([X.clone()] if args.mode == "solve" else [X])
         else:
-            s.apply_H(0, X, Y)
+            s.apply_H(0, X, Y, df32=args.mode == "apply_df32")
     torch.cuda.synchronize()
     print(json.dumps({"ncu_run": True, "mode": args.mode, "precision": args.precision, "workload": w.name,
                       "launches": lg.launch_count(), "s": time.perf_counter() - t0}))
