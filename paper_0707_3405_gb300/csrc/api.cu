@@ -161,8 +161,9 @@ struct KPoint {
 };
 
 // Everything one k-point solve (or one apply_H call) writes: scratch, solver buffers and the
-// stream it runs on.  Lane 0 runs on the handle's stream; a multi-k solve adds lanes with their
-// own streams so that k-points proceed concurrently.
+// stream it runs on.  Lane 0 serves apply_H on the handle's stream and runs a solve on its own
+// high-priority stream; a multi-k solve adds lanes with their own streams so that k-points
+// proceed concurrently.
 struct Lane {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -255,7 +256,7 @@ struct lobpcg_ctx {
     float *E32 = nullptr;
     size_t fft_budget = (size_t)128 << 20;
     int device = 0;
-    std::vector<std::unique_ptr<Lane>> lanes;  // lanes[0]: the handle's stream
+    std::vector<std::unique_ptr<Lane>> lanes;  // lanes[0]: apply_H on the handle's stream
     CoopGate gate;
     std::string err;
 };
