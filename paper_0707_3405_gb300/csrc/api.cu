@@ -1384,6 +1384,7 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
 }
 
 // Concurrent k-point lanes of one solve (k-points are independent, Sec. 5.2).
+// (10 lanes for the 10-k-point cell measured slower than 4: 3.1 s against 2.65 s.)
 constexpr int kMaxLanes = 4;
 
 // Autotuner (options.autotune): for each k-point, the FFT scratch budget per band batch (which
@@ -1512,7 +1513,20 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
     // lanes: one per concurrent k-point, each on its own high-priority stream (so that the
     // low-priority side streams of the H X refresh only fill the gaps), all ordered after the work
     // already queued on the handle's stream; lane 0 returns to the handle's stream afterwards
-    const int nl = std::max(1, std::min(c->nk, kMaxLanes));
+    // as many lanes as k-points (up to kMaxLanes) while their buffers fit: about ten npw x (M +
+    // buffer bands) complex128 arrays per lane, against the free memory (2 lanes for two 268k
+    // plane-wave k-points of 2304 bands)
+    int nl = std::max(1, std::min(c->nk, kMaxLanes));
+    {
+        size_t free_b = 0, total_b = 0;
+        int npw_max = 1;
+        for (int k = 0; k < c->nk; ++k) npw_max = std::max(npw_max, c->kp[k].npw);
+        const double per_lane = 10.0 * 16.0 * npw_max * (double)(M + nbuf);
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && per_lane > 0.0) {
+            const int fit = (int)std::max(1.0, std::floor(0.9 * (double)free_b / per_lane));
+            nl = std::max(1, std::min(nl, fit));
+        }
+    }
     int least = 0, greatest = 0;
     LG_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     if (c->lanes.empty()) c->lanes.push_back(std::unique_ptr<Lane>(new Lane()));
