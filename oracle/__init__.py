@@ -26,5 +26,6 @@ What it computes (Bottin, Leroux, Knyazev, Zerah 2007):
 Pins (tests/test_oracle_*.py): V=0 closed form, constant-V shift, rank-one KB
 secular equation, direct DFT vs analytic Fourier coefficients, Hermiticity,
 translation invariance, time reversal, Jacobi vs LAPACK, Courant-Fischer
-bounds, LOBPCG vs dense diagonalisation.
+bounds, LOBPCG vs dense diagonalisation, the Teter-Payne-Allan ratio's small-
+and large-x expansions and the band kinetic energy it is scaled by.
 """

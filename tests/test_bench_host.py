@@ -1,0 +1,117 @@
+"""Host-side logic of bench.py, on CPU: the replica aggregation at world size 2 over gloo, the
+reference arm's JSON line (rank 0 only under a multi-rank launch) and the choice of roofline."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _replica_worker(rank, ws, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    # rank r did (r + 1) * 100 band-applies in (r + 1) * 2 s
+    rate, t_max = bench.whole_job_rate(100.0 * (rank + 1), 2.0 * (rank + 1), ws)
+    mx = bench.max_over_ranks(float(rank), ws)
+    sm = bench.sum_over_ranks(float(rank + 1), ws)
+    with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+        json.dump({"rate": rate, "t_max": t_max, "max": mx, "sum": sm}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_world_size_2_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    ws = 2
+    mp.spawn(_replica_worker, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True)
+    res = [json.load(open(tmp_path / f"r{r}.json")) for r in range(ws)]
+    for r in res:
+        # whole job: (100 + 200) applies over the slowest rank's 4 s
+        assert r["rate"] == pytest.approx(75.0)
+        assert r["t_max"] == pytest.approx(4.0)
+        assert r["max"] == 1.0 and r["sum"] == 3.0
+
+
+def test_single_rank_aggregation_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.whole_job_rate(300.0, 1.5, 1) == (200.0, 1.5)
+    assert bench.dist_init(1) == (0, 1)
+
+
+def _run_reference(env_extra):
+    env = dict(os.environ)
+    env.update(env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                           "--workload", "gamma24", "--steps", "1", "--warmup", "0"],
+                          capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+
+
+def test_reference_arm_prints_one_contract_line():
+    p = _run_reference({"RANK": "0", "WORLD_SIZE": "1"})
+    assert p.returncode == 0, p.stderr
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference"
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "gamma24"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    p = _run_reference({"RANK": "1", "WORLD_SIZE": "2"})
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
+
+
+def _phases(**ms):
+    names = ("fft", "nonlocal", "gram", "constraint", "rr", "update")
+    return {p: float(ms.get(p, 0.0)) for p in names}
+
+
+def test_roofline_picks_the_longest_segment():
+    sys.path.insert(0, ROOT)
+    import bench
+    pk = {"hbm_gbs": 6000.0, "bf16_tflops": 1900.0}
+    # FFT phase dominant, FP32: HBM-bound, achieved = bytes / time
+    ms = _phases(fft=100.0, rr=10.0)
+    zero = _phases()
+    by = _phases(fft=300e9, rr=1e9)
+    fl = _phases(fft=0.0, rr=1e10)
+    roof = bench.roofline_of(ms, zero, fl, zero, by, zero, _phases(fft=4, rr=2), 2, pk, "measured")
+    assert roof["bound"] == "hbm" and roof["phase"] == "fft" and roof["precision"] == "fp32"
+    assert roof["achieved"] == pytest.approx(300e9 / 0.1 / 1e9)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 6000.0)
+    assert roof["calls_per_step"] == 2.0
+    assert roof["phase_share"] == pytest.approx(100.0 / 110.0)
+    # Rayleigh-Ritz in FP64-class arithmetic dominant: FP64 ALU roofline
+    ms = _phases(fft=10.0, rr=200.0)
+    ms64 = _phases(rr=150.0)
+    fl = _phases(rr=2e11)
+    fl64 = _phases(rr=1.5e11)
+    by = _phases(fft=1e9, rr=1e9)
+    roof = bench.roofline_of(ms, ms64, fl, fl64, by, zero, _phases(fft=1, rr=1), 1, pk, "measured")
+    assert roof["bound"] == "alu" and roof["alu"] == "fp64" and roof["phase"] == "rr"
+    assert roof["achieved"] == pytest.approx(1.5e11 / 0.15 / 1e12)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / bench.FP64_PEAK_TFLOPS)

@@ -133,3 +133,38 @@ def test_golden_files_reproduce():
     t = synth.tiny_workload(a=6.0, N=12, natoms=2, kpt=(0.25, 0.125, -0.375))
     ev = np.linalg.eigvalsh(hamiltonian.for_workload(t).dense())[:24]
     assert np.abs(np.loadtxt(os.path.join(here, "tiny_kb_eig.txt")) - ev).max() < 1e-12
+
+
+def test_teter_preconditioner_limits_and_shape():
+    """The Teter-Payne-Allan ratio K(x) passes low-energy components unchanged to fourth order,
+    K = 1 - (16/27) x^4 + (32/81) x^5 + O(x^6), and acts like the inverse kinetic energy at high
+    energy, 1/K = 2x - 2 + O(1/x); in between it decreases monotonically inside (0, 1]."""
+    K = lobpcg.teter
+    assert K(np.array([0.0]))[0] == 1.0
+    for x in (0.01, 0.02):
+        lead = (1.0 - K(np.array([x]))[0]) / x ** 4
+        assert lead == pytest.approx(16.0 / 27.0 - 32.0 / 81.0 * x, abs=1e-6)
+    for x in (1e3, 1e4):
+        inv = 1.0 / K(np.array([x]))[0]
+        assert inv - 2.0 * x == pytest.approx(-2.0, abs=10.0 / x)
+    xs = np.linspace(0.0, 200.0, 20001)
+    k = K(xs)
+    assert np.all(k > 0.0) and np.all(k <= 1.0)
+    assert np.all(np.diff(k[1:]) < 0.0)
+
+
+def test_precondition_uses_the_band_kinetic_energy():
+    """W = K(T / Ekin) R column by column, Ekin the kinetic expectation of the band: a band made
+    of two plane waves has Ekin = (T_a + T_b) / 2 whatever its norm and phases."""
+    rng = np.random.default_rng(5)
+    T = np.abs(rng.standard_normal(12)) * 3.0
+    X = np.zeros((12, 2), complex)
+    X[[2, 7], 0] = 2.5 * np.exp(1j * np.array([0.3, -1.1]))    # two plane waves, equal weight
+    X[4, 1] = -0.7j                                           # one plane wave
+    R = rng.standard_normal((12, 2)) + 1j * rng.standard_normal((12, 2))
+    W = lobpcg.precondition(R, X, T)
+    e0 = 0.5 * (T[2] + T[7])
+    np.testing.assert_allclose(W[:, 0], lobpcg.teter(T / e0) * R[:, 0], rtol=1e-14)
+    np.testing.assert_allclose(W[:, 1], lobpcg.teter(T / T[4]) * R[:, 1], rtol=1e-14)
+    # at the band's own plane wave the ratio is K(1) = 65/81
+    assert W[4, 1] / R[4, 1] == pytest.approx(65.0 / 81.0, rel=1e-14)
