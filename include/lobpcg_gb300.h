@@ -183,7 +183,9 @@ int lobpcg_default_options(lobpcg_options *opt);
  *   opt       options (NULL = defaults).
  *   stream    cudaStream_t to enqueue on (NULL = legacy default stream).
  * On success *out receives a handle.  Errors: ERR_ARG, ERR_UNSUPPORTED,
- * ERR_OOM, ERR_CUDA (then *out is NULL).
+ * ERR_OOM, ERR_CUDA (then *out is NULL).  The options, the cell, N and every
+ * host value (potential, k-points, energies: all finite) are checked before
+ * the first device call, so ERR_ARG and ERR_UNSUPPORTED need no GPU.
  */
 int lobpcg_create(lobpcg_ctx **out, const lobpcg_cell *cell, int nk, const double *kpts,
                   const double *vloc_r, int nproj, const double *proj_E,

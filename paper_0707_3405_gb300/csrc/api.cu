@@ -1200,13 +1200,20 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
     if (nproj < 0 || (nproj > 0 && !proj_E)) return fail(LOBPCG_ERR_ARG, "bad projector arguments");
     if (cell->N < 4 || cell->N > 256 || !make_fft_plan(cell->N, c->plan))
         return fail(LOBPCG_ERR_UNSUPPORTED, "N must be a product of 2, 3 and 5 in [4, 256]");
+    const int N = cell->N;
+    const size_t N3 = (size_t)N * N * N;
+    // every argument is checked before the first device call
+    for (size_t i = 0; i < N3; ++i)
+        if (!std::isfinite(vloc_r[i])) return fail(LOBPCG_ERR_ARG, "vloc_r has non-finite values");
+    for (int i = 0; i < 3 * nk; ++i)
+        if (!std::isfinite(kpts[i])) return fail(LOBPCG_ERR_ARG, "non-finite k-point");
+    for (int p = 0; p < nproj; ++p)
+        if (!std::isfinite(proj_E[p])) return fail(LOBPCG_ERR_ARG, "proj_E has non-finite values");
     c->cell = *cell;
     c->nk = nk;
     c->nproj = nproj;
-    const int N = cell->N;
     // potential: [x][y][z] -> [z][x][y] (FP32 register FFT: [y][x][z]), scaled by 1/N^3
     // (the forward FFT's normalisation)
-    const size_t N3 = (size_t)N * N * N;
     std::vector<double> vt(N3);
     std::vector<float> vt32(N3);
     const double inv = 1.0 / (double)N3;
@@ -1216,7 +1223,6 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
         for (int y = 0; y < N; ++y)
             for (int z = 0; z < N; ++z) {
                 const double v = vloc_r[((size_t)x * N + y) * N + z] * inv;
-                if (!std::isfinite(v)) return fail(LOBPCG_ERR_ARG, "vloc_r has non-finite values");
                 vt[((size_t)z * N + x) * N + y] = v;
                 vt32[reg32 ? ((size_t)y * N + x) * N + z : ((size_t)z * N + x) * N + y] = (float)v;
             }
@@ -1239,10 +1245,7 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
     }
     c->kp.resize(nk);
     for (int k = 0; k < nk; ++k) {
-        for (int d = 0; d < 3; ++d) {
-            c->kp[k].k[d] = kpts[3 * k + d];
-            if (!std::isfinite(kpts[3 * k + d])) return fail(LOBPCG_ERR_ARG, "non-finite k-point");
-        }
+        for (int d = 0; d < 3; ++d) c->kp[k].k[d] = kpts[3 * k + d];
         LG_TRY(build_basis(c, c->kp[k]));
     }
     LG_CUDA_TRY(cudaGetDevice(&c->device));

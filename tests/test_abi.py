@@ -31,3 +31,77 @@ def test_default_options_without_gpu():
     o = lg.default_options()
     assert o.block_size == 64 and o.nline == 4 and o.precision == lg.FP64 and abs(o.tol - 1e-8) < 1e-20
     assert o.fp64_gemm == 0 and abs(o.mixed_early - 1e-3) < 1e-20
+
+
+def _raw_create(lib, lg, cell=True, a=10.0, N=16, ecut=5.0, nk=1, kpts=None, vloc=None, nproj=0, proj_E=None,
+                opt=None):
+    import numpy as np
+    h = ctypes.c_void_p(12345)
+    kp = np.zeros((max(nk, 1), 3)) if kpts is None else np.ascontiguousarray(kpts, dtype=np.float64)
+    v = np.zeros((N, N, N)) if vloc is None else np.ascontiguousarray(vloc, dtype=np.float64)
+    E = None if proj_E is None else np.ascontiguousarray(proj_E, dtype=np.float64)
+    c = lg.Cell(a, N, ecut)
+    rc = lib.lobpcg_create(ctypes.byref(h), ctypes.byref(c) if cell else None, nk, kp.ctypes.data,
+                           v.ctypes.data, nproj, None if E is None else E.ctypes.data, None,
+                           ctypes.byref(opt) if opt is not None else None, None)
+    msg = (lib.lobpcg_last_error(None) or b"").decode()
+    return rc, h.value, msg
+
+
+def test_create_rejects_bad_arguments_before_any_device_call():
+    """Argument errors come back as status codes with a message and a NULL handle, before the
+    library touches a device (this runs without a GPU)."""
+    import numpy as np
+    import paper_0707_3405_gb300 as lg
+    ensure_built()
+    lib = lg.load()
+    ERR_ARG, ERR_UNSUPPORTED = -1, -6
+
+    def bad_opt(**kw):
+        o = lg.default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    cases = [
+        (dict(cell=False), ERR_ARG, "must not be NULL"),
+        (dict(a=0.0), ERR_ARG, "a and ecut"),
+        (dict(ecut=-1.0), ERR_ARG, "a and ecut"),
+        (dict(nk=0), ERR_ARG, "nk must be"),
+        (dict(nproj=3), ERR_ARG, "projector"),
+        (dict(N=7), ERR_UNSUPPORTED, "product of 2, 3 and 5"),
+        (dict(N=512), ERR_UNSUPPORTED, "product of 2, 3 and 5"),
+        (dict(vloc=np.full((16, 16, 16), np.nan)), ERR_ARG, "vloc_r"),
+        (dict(kpts=np.array([[0.0, np.inf, 0.0]])), ERR_ARG, "k-point"),
+        (dict(nproj=2, proj_E=np.array([1.0, np.nan])), ERR_ARG, "proj_E"),
+        (dict(opt=bad_opt(block_size=0)), ERR_ARG, "block_size"),
+        (dict(opt=bad_opt(block_size=2000)), ERR_ARG, "block_size too large"),
+        (dict(opt=bad_opt(nline=0)), ERR_ARG, "nline"),
+        (dict(opt=bad_opt(precision=7)), ERR_ARG, "precision"),
+        (dict(opt=bad_opt(tol=0.0)), ERR_ARG, "tol"),
+        (dict(opt=bad_opt(tol=float("nan"))), ERR_ARG, "tol"),
+        (dict(opt=bad_opt(nbuf=-1)), ERR_ARG, "nbuf"),
+        (dict(opt=bad_opt(gemm_split=1)), ERR_UNSUPPORTED, "BF16x3"),
+        (dict(opt=bad_opt(gemm_split=5)), ERR_ARG, "gemm_split"),
+        (dict(opt=bad_opt(mixed_early=-1.0)), ERR_ARG, "mixed_early"),
+        (dict(opt=bad_opt(fp64_gemm=3)), ERR_ARG, "fp64_gemm"),
+    ]
+    for kw, code, text in cases:
+        rc, handle, msg = _raw_create(lib, lg, **kw)
+        assert rc == code, (kw, rc, msg)
+        assert handle is None, kw
+        assert text in msg, (kw, msg)
+    assert lib.lobpcg_create(None, None, 1, None, None, 0, None, None, None, None) == ERR_ARG
+
+
+def test_handle_calls_reject_null_handle():
+    import paper_0707_3405_gb300 as lg
+    ensure_built()
+    lib = lg.load()
+    assert lib.lobpcg_npw(None, 0) == -1
+    assert lib.lobpcg_set_stream(None, None) == -1
+    assert lib.lobpcg_set_options(None, None) == -1
+    assert lib.lobpcg_set_projectors(None, 0, None) == -1
+    assert lib.lobpcg_solve(None, 64, None, None, None, None) == -1
+    assert lib.lobpcg_apply_H(None, 0, None, None, 1, 0) == -1
+    lib.lobpcg_destroy(None)
