@@ -104,15 +104,19 @@ Prof::~Prof() {
 int Allocator::alloc(void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return LOBPCG_OK;
-    if (cap > 0 && used.load() + (long long)bytes > cap)
+    // reserve first, so that concurrent lanes cannot pass the cap check together
+    const long long before = used.fetch_add((long long)bytes);
+    if (cap > 0 && before + (long long)bytes > cap) {
+        used -= (long long)bytes;
         return fail(LOBPCG_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes exceeds the memory cap");
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
+        used -= (long long)bytes;
         cudaGetLastError();
         *p = nullptr;
         return fail(LOBPCG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
     }
-    used += (long long)bytes;
     return LOBPCG_OK;
 }
 
