@@ -23,9 +23,26 @@ What it computes (Bottin, Leroux, Knyazev, Zerah 2007):
 * ``checks``      -- residual norms, orthonormality and cluster-projector
                      distances used to compare any solver against the oracle.
 
+For the next rows of the path (no GPU counterpart yet):
+
+* ``density``     -- rho(r) = sum_n f_n |psi_n(r)|^2 on the grid (first step
+                     of the SC loop, Sec. 2.1; by FFT, Sec. 2.2 item iii),
+                     as a plain sum and by the inverse FFT.
+* ``gamma``       -- the Gamma-point real-wavefunction form: half-sphere
+                     storage, its inner products, H in a real orthonormal
+                     basis, and the LOBPCG sweeps in real arithmetic.
+* ``pcg``         -- band-by-band PCG with exact line minimisation (the
+                     method Sec. 3.3 compares LOBPCG with).  Its conjugacy
+                     coefficient changes the speed, not the converged result,
+                     so it is pinned only through convergence.
+
 Pins (tests/test_oracle_*.py): V=0 closed form, constant-V shift, rank-one KB
 secular equation, direct DFT vs analytic Fourier coefficients, Hermiticity,
 translation invariance, time reversal, Jacobi vs LAPACK, Courant-Fischer
 bounds, LOBPCG vs dense diagonalisation, the Teter-Payne-Allan ratio's small-
-and large-x expansions and the band kinetic energy it is scaled by.
+and large-x expansions and the band kinetic energy it is scaled by
+(tests/test_oracle_next.py: density Parseval, plane-wave closed forms,
+translation and unitary invariance; real form unitary, real, same spectrum;
+PCG line minimum vs brute force, exact two-plane-wave step, monotone
+Rayleigh quotient, dense and free-electron limits).
 """

@@ -130,13 +130,15 @@ def block_lobpcg(H, X: np.ndarray, T: np.ndarray, Y: np.ndarray | None, nline: i
 
 
 def solve(H, X0: np.ndarray, block: int, nline: int = 4, tol: float = 1e-10, max_sweeps: int = 200,
-          nblocks_only: int | None = None, keep_trace: bool = False) -> Result:
+          nblocks_only: int | None = None, keep_trace: bool = False, real: bool = False) -> Result:
     """Lowest M = X0.shape[1] eigenpairs of H by block-by-block LOBPCG sweeps.
 
     ``nblocks_only`` restricts the run to the first blocks (their result does
     not depend on later blocks, which are constrained to be orthogonal to them).
+    ``real``: H is a real symmetric operator on real vectors (the Gamma-point real
+    form); the same steps then run in real arithmetic.
     """
-    X = np.array(X0, dtype=np.complex128)
+    X = np.array(X0, dtype=np.float64 if real else np.complex128)
     M = X.shape[1]
     if M % block:
         raise ValueError("number of bands must be a multiple of the block size")
