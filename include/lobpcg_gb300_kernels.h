@@ -19,7 +19,10 @@
  *     (cudaStream_t, NULL = legacy default stream) and the call returns
  *     without synchronising, except where noted.
  *   - Return LOBPCG_OK or a negative LOBPCG_ERR_* code (header lobpcg_gb300.h);
- *     lobpcg_k_last_error() gives the message of the last failure.
+ *     lobpcg_k_last_error() gives the message of the last failure.  The
+ *     precision, the sizes, NULL pointers and leading dimensions are checked
+ *     before any device work (ERR_ARG); a GEMM with an empty output (m, n or
+ *     M = 0) is a no-op that returns LOBPCG_OK.
  *   - Scratch memory the kernels need is allocated by the library and kept
  *     for later calls (one pool per device).
  */

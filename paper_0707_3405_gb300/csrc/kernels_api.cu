@@ -36,6 +36,8 @@ extern "C" {
 
 int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A, int lda, const void *B, int ldb,
                      double beta, void *C, int ldc, void *stream) {
+    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C64)
+        return fail(LOBPCG_ERR_ARG, "unknown precision");
     if (m < 0 || n < 0 || K < 0) return fail(LOBPCG_ERR_ARG, "negative size");
     if (m == 0 || n == 0) return LOBPCG_OK;
     if (!A || !B || !C || lda < K || ldb < K || ldc < m) return fail(LOBPCG_ERR_ARG, "bad pointer or leading dimension");
@@ -67,6 +69,8 @@ int lobpcg_k_gram_lower(int prec, int n, int K, const void *A, int lda, const vo
 
 int lobpcg_k_gemm_nn(int prec, int M, int n, int k, double alpha, const void *A, int lda, const void *B, int ldb,
                      double beta, const void *C, int ldc, void *D, int ldd, void *stream) {
+    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C64)
+        return fail(LOBPCG_ERR_ARG, "unknown precision");
     if (M < 0 || n < 0 || k < 0) return fail(LOBPCG_ERR_ARG, "negative size");
     if (M == 0 || n == 0) return LOBPCG_OK;
     if (!A || !B || !D || lda < M || ldb < k || ldd < M || (beta != 0.0 && (!C || ldc < M)))

@@ -105,3 +105,39 @@ def test_handle_calls_reject_null_handle():
     assert lib.lobpcg_solve(None, 64, None, None, None, None) == -1
     assert lib.lobpcg_apply_H(None, 0, None, None, 1, 0) == -1
     lib.lobpcg_destroy(None)
+
+
+def test_kernel_entry_points_check_arguments_without_a_device():
+    """The lobpcg_k_* calls reject bad precisions, sizes, pointers and leading dimensions
+    with ERR_ARG before any device work; empty GEMM outputs are no-ops."""
+    import paper_0707_3405_gb300 as lg
+    ensure_built()
+    lib = lg.load()
+    C128, DF32, C64, ERR_ARG = 0, 2, 1, -1
+    p = ctypes.c_void_p(0x1000)   # never dereferenced: every call below fails or returns first
+
+    def msg():
+        return (lib.lobpcg_k_last_error() or b"").decode()
+
+    assert lib.lobpcg_k_gemm_cn(9, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None) == ERR_ARG and "precision" in msg()
+    assert lib.lobpcg_k_gemm_cn(9, 0, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None) == ERR_ARG
+    assert lib.lobpcg_k_gemm_cn(C128, -1, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None) == ERR_ARG and "negative" in msg()
+    assert lib.lobpcg_k_gemm_cn(C64, 4, 4, 8, 1.0, p, 7, p, 8, 0.0, p, 4, None) == ERR_ARG and "leading" in msg()
+    assert lib.lobpcg_k_gemm_cn(DF32, 4, 4, 8, 1.0, None, 8, p, 8, 0.0, p, 4, None) == ERR_ARG
+    assert lib.lobpcg_k_gemm_cn(C128, 0, 4, 8, 1.0, None, 0, None, 0, 0.0, None, 0, None) == 0
+    assert lib.lobpcg_k_gram_lower(C64, 4, 8, p, 8, p, 8, p, 4, None) == ERR_ARG and "precision" in msg()
+    assert lib.lobpcg_k_gram_lower(C128, 4, 8, p, 8, p, 8, p, 3, None) == ERR_ARG
+    assert lib.lobpcg_k_gram_lower(DF32, 0, 8, None, 8, None, 8, None, 0, None) == 0
+    assert lib.lobpcg_k_gemm_nn(9, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, None, 0, p, 4, None) == ERR_ARG
+    assert lib.lobpcg_k_gemm_nn(C128, 4, 4, 4, 1.0, p, 4, p, 4, 1.0, None, 0, p, 4, None) == ERR_ARG
+    assert lib.lobpcg_k_gemm_nn(C64, 8, 4, 4, 1.0, p, 7, p, 4, 0.0, None, 0, p, 8, None) == ERR_ARG
+    assert lib.lobpcg_k_gemm_nn(DF32, 8, 0, 4, 1.0, None, 0, None, 0, 0.0, None, 0, None, 0, None) == 0
+    th = ctypes.c_void_p(0x2000)
+    for fn in (lib.lobpcg_k_rayleigh_ritz, lib.lobpcg_k_rayleigh_ritz_df32, lib.lobpcg_k_rayleigh_ritz32):
+        assert fn(4, 5, p, p, 1e-12, th, p, None, None) == ERR_ARG and "m <= n" in msg()
+        assert fn(5000, 5, p, p, 1e-12, th, p, None, None) == ERR_ARG
+        assert fn(4, 2, None, p, 1e-12, th, p, None, None) == ERR_ARG and "NULL" in msg()
+    assert lib.lobpcg_k_heev(0, p, th, p, None) == ERR_ARG
+    assert lib.lobpcg_k_heev(4, p, None, p, None) == ERR_ARG
+    assert lib.lobpcg_k_set_gemm_mode(1) == ERR_ARG and "gemm mode" in msg()
+    assert lib.lobpcg_k_set_gemm_mode(7) == ERR_ARG
