@@ -462,13 +462,18 @@ bool is_device_ptr(const void *p) {
 //   * the Gram blocks of W and P are FP32 tensor-core GEMMs, the Rayleigh-Ritz
 //     solve is FP64;
 //   * X_b <- X_b C_X + P and H X_b <- H X_b C_X + H P are FP64;
-//   * every sweep ends with an FP64 H X refresh, the FP64 all-band Rayleigh-Ritz
-//     step and FP64 residual norms, which decide convergence;
-//   * early sweeps (largest residual of the previous sweep above opt.mixed_early):
-//     block starts and the sweep-end Rayleigh-Ritz run on the FP32 copies (tensor
-//     cores, FP64 diagonals and eigensolve) and H X is not refreshed; X and H X then
-//     carry FP32 accuracy, far below the residuals of those sweeps.  Convergence is
-//     only ever declared after a full (non-early) sweep.
+//   * every sweep ends with an FP64-class H X refresh (computed block by block on a
+//     low-priority side stream while the later blocks run), the FP64-class all-band
+//     Rayleigh-Ritz step and FP64 residual norms, which decide convergence;
+//   * early visits (every band of the block above opt.mixed_early in the previous
+//     sweep): the block start and the block's X updates run on the FP32 copies
+//     (tensor cores, FP64 diagonals and eigensolve) and H X_b is not refreshed; X_b
+//     and H X_b then carry FP32 accuracy, far below the residuals of such a block.
+//     The first full visit of a block after early ones recomputes H X_b first;
+//   * settled blocks (every band below tol/100 after the previous sweep) keep their
+//     block start but take no inner iterations;
+//   * the sweep-end Rayleigh-Ritz runs on the FP32 copies only when every block was
+//     early, and convergence is only ever declared after a sweep that was not.
 struct Solver {
     lobpcg_ctx *c;
     Lane *L = nullptr;
