@@ -1,6 +1,6 @@
 """Host-side logic of bench.py, on CPU: the replica aggregation at world size 2 over gloo, the
 reference arm's JSON line (rank 0 only under a multi-rank launch), the choice of roofline and
-the per-phase roofline table."""
+the per-phase rates."""
 import json
 import os
 import socket
@@ -118,24 +118,19 @@ def test_roofline_picks_the_longest_segment():
     assert roof["frac"] == pytest.approx(roof["achieved"] / bench.FP64_PEAK_TFLOPS)
 
 
-def test_phase_rooflines_each_segment_against_its_ceiling():
+def test_phase_rates_split_native_fp64_from_the_rest():
     sys.path.insert(0, ROOT)
     import bench
-    pk = {"hbm_gbs": 6000.0, "bf16_tflops": 2250.0}
     ms = _phases(fft=50.0, gram=20.0, rr=10.0)
     ms64 = _phases(gram=5.0, rr=10.0)
     fl = _phases(fft=1e12, gram=4e12, rr=1e10)
     fl64 = _phases(gram=1e11, rr=1e10)
     by = _phases(fft=120e9, gram=1e9)
     by64 = _phases(gram=0.5e9)
-    out = bench.phase_rooflines(ms, ms64, fl, fl64, by, by64, 2, pk)
-    assert set(out) == {"fft/fp32", "gram/fp32", "gram/fp64", "rr/fp64"}
-    f = out["fft/fp32"]
-    assert f["bound"] == "hbm" and f["achieved"] == pytest.approx(120e9 / 0.05 / 1e9)
-    assert f["frac"] == pytest.approx(f["achieved"] / 6000.0) and f["ms_per_step"] == 25.0
-    g = out["gram/fp32"]
-    assert g["bound"] == "tensor" and g["peak"] == pytest.approx(1100.0)
-    assert g["achieved"] == pytest.approx(3 * (4e12 - 1e11) / 0.015 / 1e12)
-    r = out["rr/fp64"]
-    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(1e10 / 0.01 / 1e12)
-    assert r["peak"] == bench.FP64_PEAK_TFLOPS
+    out = bench.phase_rates(ms, ms64, fl, fl64, by, by64, 2)
+    assert set(out) == {"fft/other", "gram/other", "gram/fp64", "rr/fp64"}
+    assert out["fft/other"]["gbs"] == pytest.approx(120e9 / 0.05 / 1e9)
+    assert out["fft/other"]["ms_per_step"] == 25.0
+    assert out["gram/other"]["tflops"] == pytest.approx((4e12 - 1e11) / 0.015 / 1e12)
+    assert out["gram/fp64"]["gbs"] == pytest.approx(0.5e9 / 0.005 / 1e9)
+    assert out["rr/fp64"]["tflops"] == pytest.approx(1e10 / 0.01 / 1e12)
