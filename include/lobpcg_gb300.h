@@ -191,20 +191,30 @@ int lobpcg_create(lobpcg_ctx **out, const lobpcg_cell *cell, int nk, const doubl
                   const double *vloc_r, int nproj, const double *proj_E,
                   const void *const *beta, const lobpcg_options *opt, void *stream);
 
-/* Upload (or replace) the projectors of k-point k: host npw_k x nproj complex128,
- * column-major, G order.  Synchronous with respect to the host buffer. */
+/* Upload (or replace) the Kleinman-Bylander projectors of k-point k (the v_nl
+ * term of Sec. 2.2 item iv and Sec. 4.3): beta_k is host npw_k x nproj
+ * complex128, column-major, rows in G order.  The library copies it; the call
+ * returns once the host buffer may be reused.  nproj = 0: a no-op.
+ * Errors: ERR_ARG (ctx or beta_k NULL, k out of range), ERR_OOM, ERR_CUDA. */
 int lobpcg_set_projectors(lobpcg_ctx *ctx, int k, const void *beta_k);
 
-/* Change the stream later calls enqueue on. */
+/* Change the CUDA stream (cudaStream_t; NULL = legacy default stream) that
+ * later calls enqueue on and that lobpcg_solve orders its work after.
+ * Errors: ERR_ARG (ctx NULL). */
 int lobpcg_set_stream(lobpcg_ctx *ctx, void *stream);
 
-/* Replace the options of an existing handle (block size, tolerance, precision ...). */
+/* Replace the options of an existing handle (block size, tolerance,
+ * precision ...); they apply from the next call.  The options are checked as
+ * at create: ERR_ARG or ERR_UNSUPPORTED leaves the old ones in place. */
 int lobpcg_set_options(lobpcg_ctx *ctx, const lobpcg_options *opt);
 
-/* Number of plane waves npw_k of k-point k (>= 1), or a negative error code. */
+/* Number of plane waves npw_k of k-point k (the sphere of Sec. 2.1, >= 1), or
+ * ERR_ARG (ctx NULL, k out of range). */
 int lobpcg_npw(const lobpcg_ctx *ctx, int k);
 
-/* Write the G order of k-point k: miller is host int32 npw_k x 3 (row g = (n_x, n_y, n_z)). */
+/* Write the G order of k-point k: miller is host int32 npw_k x 3, caller-owned
+ * (row g = (n_x, n_y, n_z), sorted by n_x, then n_y, then n_z).
+ * Errors: ERR_ARG (ctx or miller NULL, k out of range). */
 int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller);
 
 /*
