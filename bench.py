@@ -332,6 +332,71 @@ def phase_rates(ph_ms, ph_ms64, ph_fl, ph_fl64, ph_by, ph_by64, steps):
     return out
 
 
+# FP32 instruction rate: SMs x FP32 lanes x max SM clock; a double-FP32 complex multiply-add
+# costs about 48 FP32 instructions (split operands, TwoProd by FMA, TwoSum accumulation)
+FP32_INSTR_PER_S = 152 * 128 * 2.07e9
+DF32_INSTR_PER_CMAC = 48.0
+
+
+def kernel_rooflines(npw, nbands, block, pk, reps=5):
+    """Standalone CUDA-event timing of the two contraction kernels that dominate the solve,
+    at the solve's shapes, each against its own ceiling:
+
+    * the double-FP32 A B (``k_gemm_df``; the sweep-end rotation X C, npw x nbands x nbands):
+      FP64-class flops 8 M n k against the FP32 instruction rate / 48 per complex
+      multiply-add (ALU bound);
+    * the 3xTF32 tensor-core A^H B Gram of a block's [R W P] (``k_tc_cn``, 3m x 3m x npw):
+      tensor flops 3 x 8 m n K against the TF32 tensor rate (the measured BF16 rate x the
+      nominal 1.1 / 2.25 ratio).
+
+    Operands are larger than L2 (for the Gram: two distinct npw x 3m complex64 blocks)."""
+    import torch
+    import paper_0707_3405_gb300 as lg
+    out = {}
+
+    def timed(fn):
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    try:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1234)
+        M, n, k = npw, nbands, nbands
+        A = torch.randn((k, M), dtype=torch.complex128, device="cuda", generator=g)
+        B = torch.randn((n, k), dtype=torch.complex128, device="cuda", generator=g)
+        D = torch.empty((n, M), dtype=torch.complex128, device="cuda")
+        t = timed(lambda: lg.gemm_nn(A, B, D=D, df32=True))
+        fl = 8.0 * M * n * k
+        peak = FP32_INSTR_PER_S / DF32_INSTR_PER_CMAC * 8.0 / 1e12
+        out["k_gemm_df"] = {"shape": [M, n, k], "bound": "alu", "unit": "TFLOP/s", "ms": t * 1e3,
+                            "achieved": fl / t / 1e12, "peak": peak, "frac": fl / t / 1e12 / peak,
+                            "peak_source": "FP32 lanes x max clock / 48 instructions per complex multiply-add"}
+        del A, B, D
+        m3 = 3 * block
+        A = torch.randn((m3, npw), dtype=torch.complex64, device="cuda", generator=g)
+        B = torch.randn((m3, npw), dtype=torch.complex64, device="cuda", generator=g)
+        C = torch.empty((m3, m3), dtype=torch.complex64, device="cuda")
+        t = timed(lambda: lg.gemm_cn(A, B, C=C))
+        fl = 3.0 * 8.0 * m3 * m3 * npw
+        peak = pk.get("bf16_tflops", FALLBACK["bf16_tflops"]) * 1.1 / 2.25
+        out["k_tc_cn"] = {"shape": [m3, m3, npw], "bound": "tensor", "unit": "TFLOP/s", "ms": t * 1e3,
+                          "achieved": fl / t / 1e12, "peak": peak, "frac": fl / t / 1e12 / peak,
+                          "peak_source": "measured BF16 x nominal TF32/BF16 ratio 1.1/2.25 (3xTF32 flops)"}
+        del A, B, C
+    except Exception as e:  # a failed side measurement must not cost the bench line
+        out["error"] = f"{type(e).__name__}: {e}"
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -435,6 +500,8 @@ def main():
         torch.cuda.synchronize()
         applyh[f"{name}_band_applies_per_s"] = reps * w.nbands / (a0.elapsed_time(a1) / 1e3)
     s.close()
+    del Xa, Ya
+    kroof = kernel_rooflines(npw, w.nbands + args.nbuf, w.block, pk)
 
     # the FP64-only path on the same problem from the same start
     fp64 = None
@@ -488,6 +555,7 @@ def main():
             "fp64_path": fp64,
             "phases_ms_per_step": {p: acc["ph_ms"][p] / args.steps for p in lg.PHASES},
             "phase_rates": prl,
+            "kernel_rooflines": kroof,
         }
         print(json.dumps(line))
     if ws > 1:

@@ -134,3 +134,15 @@ def test_phase_rates_split_native_fp64_from_the_rest():
     assert out["gram/other"]["tflops"] == pytest.approx((4e12 - 1e11) / 0.015 / 1e12)
     assert out["gram/fp64"]["gbs"] == pytest.approx(0.5e9 / 0.005 / 1e9)
     assert out["rr/fp64"]["tflops"] == pytest.approx(1e10 / 0.01 / 1e12)
+
+
+def test_kernel_rooflines_never_raise():
+    """Without a GPU the side measurement reports its error instead of raising, so a failed
+    kernel timing cannot cost the bench line."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("CPU-only check")
+    out = bench.kernel_rooflines(1000, 8, 4, {"hbm_gbs": 1.0, "bf16_tflops": 1.0})
+    assert set(out) == {"error"}
