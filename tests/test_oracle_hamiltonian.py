@@ -164,3 +164,20 @@ def test_projector_normalisation():
     miller = basis.sphere(a, N, synth.default_ecut(a, N), [0, 0, 0])
     beta = synth.kb_beta(miller, [0, 0, 0], a, np.array([[0.0, 0.0, 0.0]]))
     assert abs(np.sum(np.abs(beta[:, 0]) ** 2) - 1.0) < 1e-3
+
+
+def test_free_electron_shells_of_the_cubic_lattice():
+    """V = 0 in a cell of side 2 pi (reciprocal lattice = integers, Ha units): at Gamma the
+    lowest levels are 0, 1/2, 1, 3/2, 2, 5/2 with the numbers of ways to write 0..5 as a sum of
+    three squares, 1, 6, 12, 8, 6, 24; at k = (1/2, 0, 0) they are 1/8 (twice) and 5/8 (8 times)."""
+    a, N = 2 * math.pi, 16
+    H = hamiltonian.Hamiltonian(a, N, np.zeros(3), basis.sphere(a, N, 3.0, np.zeros(3)), np.zeros((N, N, N)))
+    ev = np.linalg.eigvalsh(H.dense())
+    levels, counts = np.unique(np.round(ev[ev < 2.75], 12), return_counts=True)
+    assert np.allclose(levels, [0.0, 0.5, 1.0, 1.5, 2.0, 2.5], atol=1e-12)
+    assert list(counts) == [1, 6, 12, 8, 6, 24]
+    k = np.array([0.5, 0.0, 0.0])
+    H = hamiltonian.Hamiltonian(a, N, k, basis.sphere(a, N, 3.0, k), np.zeros((N, N, N)))
+    ev = np.linalg.eigvalsh(H.dense())
+    assert np.allclose(ev[:2], 0.125, atol=1e-12) and np.allclose(ev[2:10], 0.625, atol=1e-12)
+    assert ev[10] > 0.625 + 0.1
