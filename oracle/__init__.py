@@ -36,7 +36,7 @@ For the next rows of the path (no GPU counterpart yet):
                      coefficient changes the speed, not the converged result,
                      so it is pinned only through convergence.
 
-Pins (tests/test_oracle_*.py): V=0 closed form, constant-V shift, rank-one KB
+Pins (tests/test_oracle_*.py): V=0 closed form and cubic-lattice shell counts, constant-V shift, rank-one KB
 secular equation, direct DFT vs analytic Fourier coefficients, Hermiticity,
 translation invariance, time reversal, Jacobi vs LAPACK, Courant-Fischer
 bounds, LOBPCG vs dense diagonalisation, the Teter-Payne-Allan ratio's small-
