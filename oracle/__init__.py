@@ -36,13 +36,14 @@ For the next rows of the path (no GPU counterpart yet):
                      coefficient changes the speed, not the converged result,
                      so it is pinned only through convergence.
 
-Pins (tests/test_oracle_*.py): V=0 closed form and cubic-lattice shell counts, constant-V shift, rank-one KB
-secular equation, direct DFT vs analytic Fourier coefficients, Hermiticity,
-translation invariance, time reversal, Jacobi vs LAPACK, Courant-Fischer
-bounds, LOBPCG vs dense diagonalisation, the Teter-Payne-Allan ratio's small-
-and large-x expansions and the band kinetic energy it is scaled by
-(tests/test_oracle_next.py: density Parseval, plane-wave closed forms,
-translation and unitary invariance; real form unitary, real, same spectrum;
-PCG line minimum vs brute force, exact two-plane-wave step, monotone
-Rayleigh quotient, dense and free-electron limits).
+Pins (tests/test_oracle_*.py): V=0 closed form and cubic-lattice shell counts,
+constant-V shift, rank-one KB secular equation, direct DFT vs analytic Fourier
+coefficients, Hermiticity, translation invariance, time reversal, Jacobi vs
+LAPACK, Courant-Fischer bounds, LOBPCG vs dense diagonalisation, the
+Teter-Payne-Allan ratio's small- and large-x expansions and the band kinetic
+energy it is scaled by (tests/test_oracle_next.py: density Parseval,
+plane-wave closed forms, translation and unitary invariance; real form
+unitary, real, same spectrum; PCG line minimum vs brute force, exact
+two-plane-wave step, monotone Rayleigh quotient, dense and free-electron
+limits).
 """
