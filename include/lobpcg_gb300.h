@@ -271,6 +271,11 @@ int lobpcg_apply_local_noalloc(lobpcg_ctx *ctx, int k, const void *X, void *Y, i
 int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid,
                  lobpcg_stats *stats);
 
+/* Sizes in bytes of lobpcg_cell, lobpcg_options and lobpcg_stats as this library
+ * was compiled, so that a binding can check its own layouts against them (any
+ * pointer may be NULL).  Always LOBPCG_OK; needs no device. */
+int lobpcg_struct_sizes(int64_t *cell, int64_t *options, int64_t *stats);
+
 /* Number of kernels the library has launched in this process so far (all handles). */
 long long lobpcg_launch_count(void);
 

@@ -31,7 +31,7 @@ FP64, MIXED = 0, 1
 EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
-    "lobpcg_last_error", "lobpcg_destroy", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
+    "lobpcg_last_error", "lobpcg_destroy", "lobpcg_struct_sizes", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
     "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz_df32", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
     "lobpcg_k_set_gemm_mode", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
@@ -107,6 +107,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_solve": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Stats)]),
         "lobpcg_last_error": (ctypes.c_char_p, [vp]),
         "lobpcg_destroy": (None, [vp]),
+        "lobpcg_struct_sizes": (i, [ctypes.POINTER(ctypes.c_int64)] * 3),
         "lobpcg_launch_count": (ctypes.c_longlong, []),
         "lobpcg_apply_local_noalloc": (i, [vp, i, vp, vp, i, i]),
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
@@ -125,6 +126,13 @@ def load() -> ctypes.CDLL:
         f.restype = res
         f.argtypes = args
     _ = ll
+    # the structures above must match the library's layout exactly (the library writes them)
+    sizes = [ctypes.c_int64() for _ in range(3)]
+    lib.lobpcg_struct_sizes(*[ctypes.byref(x) for x in sizes])
+    mine = (ctypes.sizeof(Cell), ctypes.sizeof(Options), ctypes.sizeof(Stats))
+    if tuple(x.value for x in sizes) != mine:
+        raise RuntimeError(f"binding and library disagree on struct sizes (cell, options, stats): "
+                           f"{mine} here, {tuple(x.value for x in sizes)} in {LIB_PATH}")
     _lib = lib
     return lib
 

@@ -1646,6 +1646,13 @@ int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, doubl
     return ret(ctx, solve_impl(ctx, nbands, X, eig, resid, stats));
 }
 
+int lobpcg_struct_sizes(int64_t *cell, int64_t *options, int64_t *stats) {
+    if (cell) *cell = (int64_t)sizeof(lobpcg_cell);
+    if (options) *options = (int64_t)sizeof(lobpcg_options);
+    if (stats) *stats = (int64_t)sizeof(lobpcg_stats);
+    return LOBPCG_OK;
+}
+
 long long lobpcg_launch_count(void) { return launch_count(); }
 
 const char *lobpcg_last_error(const lobpcg_ctx *ctx) {

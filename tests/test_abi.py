@@ -141,3 +141,16 @@ def test_kernel_entry_points_check_arguments_without_a_device():
     assert lib.lobpcg_k_heev(4, p, None, p, None) == ERR_ARG
     assert lib.lobpcg_k_set_gemm_mode(1) == ERR_ARG and "gemm mode" in msg()
     assert lib.lobpcg_k_set_gemm_mode(7) == ERR_ARG
+
+
+def test_binding_structs_match_the_library_layout():
+    """lobpcg_cell, lobpcg_options and lobpcg_stats as compiled have the sizes of the binding's
+    ctypes structures (load() refuses a library that disagrees)."""
+    import paper_0707_3405_gb300 as lg
+    ensure_built()
+    lib = lg.load()
+    sizes = [ctypes.c_int64() for _ in range(3)]
+    assert lib.lobpcg_struct_sizes(*[ctypes.byref(x) for x in sizes]) == 0
+    assert [x.value for x in sizes] == [ctypes.sizeof(lg.Cell), ctypes.sizeof(lg.Options),
+                                        ctypes.sizeof(lg.Stats)]
+    assert lib.lobpcg_struct_sizes(None, None, None) == 0
