@@ -130,13 +130,17 @@ def block_lobpcg(H, X: np.ndarray, T: np.ndarray, Y: np.ndarray | None, nline: i
 
 
 def solve(H, X0: np.ndarray, block: int, nline: int = 4, tol: float = 1e-10, max_sweeps: int = 200,
-          nblocks_only: int | None = None, keep_trace: bool = False, real: bool = False) -> Result:
+          nblocks_only: int | None = None, keep_trace: bool = False, real: bool = False,
+          nconv: int | None = None) -> Result:
     """Lowest M = X0.shape[1] eigenpairs of H by block-by-block LOBPCG sweeps.
 
     ``nblocks_only`` restricts the run to the first blocks (their result does
     not depend on later blocks, which are constrained to be orthogonal to them).
     ``real``: H is a real symmetric operator on real vectors (the Gamma-point real
     form); the same steps then run in real arithmetic.
+    ``nconv``: only the lowest ``nconv`` bands must meet ``tol`` (the rest are
+    buffer bands iterated along to give the top wanted bands a gap to the
+    unresolved spectrum; the paper is silent on them).  Default: all bands.
     """
     X = np.array(X0, dtype=np.float64 if real else np.complex128)
     M = X.shape[1]
@@ -162,9 +166,10 @@ def solve(H, X0: np.ndarray, block: int, nline: int = 4, tol: float = 1e-10, max
         nrm = np.linalg.norm(X, axis=0)
         X, HX = X / nrm[None, :], HX / nrm[None, :]
         r = np.linalg.norm(HX - X * theta[None, :], axis=0)
-        res.history.append(float(r.max()))
+        rc = r if nconv is None else r[:nconv]
+        res.history.append(float(rc.max()))
         res.eig, res.X, res.resid, res.sweeps = theta, X, r, sweep
-        if r.max() <= tol:
+        if rc.max() <= tol:
             res.converged = True
             break
     return res
