@@ -245,10 +245,13 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
  *   limit      one band's half-box, Px * N^2 complex numbers (Px = x-planes the
  *              sphere occupies, about N/2 + 1), must fit in 32 MiB, else
  *              LOBPCG_ERR_ARG; bands are processed in batches that fit.
- * The first call on each device looks up the array's device address (host code
- * cannot use the array's name as an address), so make that first call before
- * any stream capture.  All calls share the array: calls that overlap on the GPU
- * race on it.  Errors: ERR_ARG, ERR_CUDA; the message is lobpcg_last_error(NULL).
+ * lobpcg_create looks up the array's device address on the handle's device
+ * (host code cannot use the array's name as an address; the lookup also loads
+ * the device module that holds the array, which is when CUDA reserves its
+ * 32 MiB), so the call itself does no set-up; the handle's device must be the
+ * current device (else ERR_ARG).  All calls share the array: calls that
+ * overlap on the GPU race on it.  Errors: ERR_ARG, ERR_CUDA; the message is
+ * lobpcg_last_error(NULL).
  */
 int lobpcg_apply_local_noalloc(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int precision);
 

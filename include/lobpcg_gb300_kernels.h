@@ -124,8 +124,11 @@ int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double 
 int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream);
 
 /*
- * Engine of the complex64 (LOBPCG_C64) GEMMs, process-wide; lobpcg_solve and
- * lobpcg_apply_H set it from lobpcg_options.gemm_split on entry.
+ * Engine of the complex64 (LOBPCG_C64) GEMMs issued by the calling host
+ * thread (a per-thread setting); lobpcg_solve and lobpcg_apply_H set it from
+ * their handle's lobpcg_options.gemm_split on entry, and every k-point lane
+ * thread of a solve does likewise, so handles with different engines used
+ * from different threads do not interfere.
  *   0 (auto) or 2: 5th-generation tensor cores (tcgen05, accumulators in TMEM)
  *      with 3xTF32 split operands and FP32 accumulation (relative error about
  *      1e-6 of sum |a||b|) for long reductions (A^H B with K >= 1024) and tall
@@ -134,6 +137,19 @@ int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream);
  * Returns ERR_ARG for other values (1, BF16x3, is not built).
  */
 int lobpcg_k_set_gemm_mode(int mode);
+
+/*
+ * Poll limit of the waits inside the tensor-core GEMMs on the current device:
+ * before a CTA refills a shared-memory stage it waits, at most `polls` times,
+ * for the MMAs that read it.  polls < 0 restores the default (2^26 polls,
+ * seconds).  A wait that runs out makes the CTA stop issuing, wait (with the
+ * default limit) for the MMAs it already issued, free its tensor memory and
+ * return with a device flag set, which lobpcg_k_check_timeouts and every
+ * solve sweep turn into LOBPCG_ERR_TIMEOUT.  This exists so that tests can
+ * drive the timeout path (polls = 0) without hanging or faulting the GPU.
+ * Errors: ERR_CUDA.
+ */
+int lobpcg_k_set_spin_limit(long long polls);
 
 /*
  * Synchronises the device, then returns LOBPCG_ERR_TIMEOUT if a tensor-core

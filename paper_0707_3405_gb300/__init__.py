@@ -33,7 +33,7 @@ EXPORTED = (
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_struct_sizes", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
     "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz_df32", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
-    "lobpcg_k_set_gemm_mode", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
+    "lobpcg_k_set_gemm_mode", "lobpcg_k_set_spin_limit", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
 
 
@@ -118,6 +118,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_k_rayleigh_ritz32": (i, [i, i, vp, vp, d, vp, vp, vp, vp]),
         "lobpcg_k_heev": (i, [i, vp, vp, vp, vp]),
         "lobpcg_k_set_gemm_mode": (i, [i]),
+        "lobpcg_k_set_spin_limit": (i, [ll]),
         "lobpcg_k_check_timeouts": (i, []),
         "lobpcg_k_last_error": (ctypes.c_char_p, []),
     }
@@ -125,7 +126,6 @@ def load() -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _ = ll
     # the structures above must match the library's layout exactly (the library writes them)
     sizes = [ctypes.c_int64() for _ in range(3)]
     lib.lobpcg_struct_sizes(*[ctypes.byref(x) for x in sizes])
@@ -295,6 +295,14 @@ class Solver:
         32 MiB scratch array holds the FFT half-box).  X and Y are (nb, npw)
         CUDA tensors, complex128 or complex64."""
         import torch
+        if X.dtype not in (torch.complex128, torch.complex64):
+            raise TypeError("X must be complex64 or complex128")
+        if not (isinstance(Y, torch.Tensor) and Y.dtype == X.dtype and tuple(Y.shape) == tuple(X.shape)):
+            raise TypeError("Y must be a tensor with the shape and dtype of X")
+        if X.dim() != 2 or not X.is_contiguous() or not Y.is_contiguous():
+            raise ValueError("X and Y must be contiguous (nb, npw_k) blocks")
+        if X.shape[0] and X.shape[1] != self.npw(k):
+            raise ValueError("X must have shape (nb, npw_k)")
         prec = C128 if X.dtype == torch.complex128 else C64
         rc = self._lib.lobpcg_apply_local_noalloc(self.handle, k, _ptr(X), _ptr(Y), int(X.shape[0]), prec)
         if rc < 0:
@@ -343,9 +351,15 @@ def launch_count() -> int:
 
 # ---------------------------------------------------------------- dense building blocks
 def set_gemm_mode(mode: int):
-    """Complex64 GEMM engine, process-wide: 0 or 2 = tensor cores (3xTF32) for long
+    """Complex64 GEMM engine of the calling thread: 0 or 2 = tensor cores (3xTF32) for long
     reductions and tall products, 3 = CUDA cores only."""
     _check(load().lobpcg_k_set_gemm_mode(int(mode)), None, kernels=True)
+
+
+def set_spin_limit(polls: int):
+    """Poll limit of the tensor-core GEMMs' ring waits (< 0: default); for tests of the
+    timeout path."""
+    _check(load().lobpcg_k_set_spin_limit(int(polls)), None, kernels=True)
 
 
 def check_timeouts():

@@ -901,6 +901,8 @@ struct Solver {
         LG_CUDA_TRY(cudaMemcpyAsync(res_h, res, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
         LG_CUDA_TRY(cudaMemcpyAsync(&nd_h, ndrop, sizeof(int), cudaMemcpyDeviceToHost, s));
         LG_CUDA_TRY(cudaStreamSynchronize(s));
+        // a device wait that gave up leaves its outputs undefined: report it before judging them
+        LG_TRY(tc_check_error());
         if (nd_h > 0)
             return fail(LOBPCG_ERR_BREAKDOWN, "the bands lost linear independence (" + std::to_string(nd_h) +
                                                   " dropped in the all-band Rayleigh-Ritz step)");
@@ -1258,6 +1260,7 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
         LG_TRY(build_basis(c, c->kp[k]));
     }
     LG_CUDA_TRY(cudaGetDevice(&c->device));
+    LG_TRY(noalloc_prepare());
     LG_CUDA_TRY(cudaEventCreateWithFlags(&c->gate.ev, cudaEventDisableTiming));
     c->lanes.emplace_back(new Lane());
     c->lanes[0]->stream = c->stream;
@@ -1345,6 +1348,7 @@ int ctx_local_view(const lobpcg_ctx *c, int k, LocalView *v) {
     v->tw64 = c->tw64;
     v->tw32 = c->tw32;
     v->stream = c->stream;
+    v->device = c->device;
     return LOBPCG_OK;
 }
 bool is_device_pointer(const void *p) { return is_device_ptr(p); }
@@ -1569,6 +1573,7 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
     std::vector<std::string> lane_err(nl);
     auto run_lane = [&](int l) {
         if (l > 0) cudaSetDevice(c->device);
+        set_gemm_mode(c->opt.gemm_split);  // the engine choice is per host thread
         Prof &pr = profs[l];
         pr.on = c->opt.timing != 0;
         pr.s = c->lanes[l]->stream;

@@ -357,7 +357,9 @@ int launch_gemm(GemmWork *w, int m, int n, int K, R alpha, const cx<R> *A, int l
 }  // namespace
 
 namespace {
-int g_gemm_mode = 0;
+// per host thread: each handle call (and each k-point lane thread of a solve) sets it from its
+// own options, so handles with different engines on different threads do not interfere
+thread_local int g_gemm_mode = 0;
 // tensor-core thresholds: a long reduction (A^H B) or a tall product (A B)
 constexpr int kTcMinK = 1024, kTcMinM = 1024;
 }  // namespace

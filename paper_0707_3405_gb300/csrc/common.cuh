@@ -212,7 +212,11 @@ struct LocalView {
     const z64 *tw64 = nullptr;
     const c32 *tw32 = nullptr;
     cudaStream_t stream = nullptr;
+    int device = 0;
 };
+// Looks up the allocation-free entry point's scratch address on the current device
+// (loading the module that holds it); lobpcg_create calls it on the handle's device.
+int noalloc_prepare();
 }  // namespace lg
 struct lobpcg_ctx;
 namespace lg {
@@ -246,6 +250,8 @@ int zgemm_nn_df(int M, int n, int k, double alpha, const z64 *A, int lda, const 
 // reductions / tall products unless the GEMM mode says otherwise.
 int tc_gemm_cn(GemmWork &w, int m, int n, int K, float alpha, const c32 *A, int lda, const c32 *B, int ldb,
                float beta, c32 *C, int ldc, cudaStream_t s);
+// Poll limit of the tensor-core GEMMs' ring waits on the current device (< 0: the default).
+int tc_set_spin_limit(long long polls);
 int tc_gemm_nn(int M, int n, int k, float alpha, const c32 *A, int lda, const c32 *B, int ldb, float beta,
                const c32 *C, int ldc, c32 *D, int ldd, cudaStream_t s);
 int tc_check_error();   // LOBPCG_ERR_TIMEOUT if a bounded device wait ran out (clears the flag)

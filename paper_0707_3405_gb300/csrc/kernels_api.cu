@@ -146,6 +146,8 @@ int lobpcg_k_set_gemm_mode(int mode) {
     return LOBPCG_OK;
 }
 
+int lobpcg_k_set_spin_limit(long long polls) { return tc_set_spin_limit(polls); }
+
 int lobpcg_k_check_timeouts(void) {
     LG_CUDA_TRY(cudaDeviceSynchronize());
     return tc_check_error();

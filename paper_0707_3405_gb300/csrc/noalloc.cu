@@ -11,9 +11,14 @@
 //
 // The array is kNoAllocScratchBytes (32 MiB) per device, held by every GPU
 // that loads the library until the process exits.  Host code cannot use the
-// array's name as a device address, so the first call on each device, with
-// that device current, looks the address up with cudaGetSymbolAddress and
-// keeps it; that first call should therefore come before any stream capture.
+// array's name as a device address: lobpcg_create, with the handle's device
+// current, looks the address up once per device with cudaGetSymbolAddress and
+// keeps it.  That lookup is also what loads this file's device module (the
+// library is built without relocatable device code, so each source file is a
+// module of its own, and CUDA loads modules lazily), i.e. where the 32 MiB are
+// actually reserved; doing it at create keeps that reservation out of the
+// allocation-free call.  A call therefore needs the handle's device to be the
+// current one (else LOBPCG_ERR_ARG).
 // All calls share the array: calls that overlap on the GPU (different
 // streams, or different handles at once) race on it.  Every element of the
 // half-box is written before it is read within a call, so nothing carried
@@ -50,6 +55,15 @@ int scratch_address(void **out) {
 
 }  // namespace
 
+namespace lg {
+// Called by lobpcg_create on the handle's device: loads this module and records the
+// scratch address, so that lobpcg_apply_local_noalloc itself does no set-up.
+int noalloc_prepare() {
+    void *p = nullptr;
+    return scratch_address(&p);
+}
+}  // namespace lg
+
 using namespace lg;
 
 extern "C" {
@@ -62,6 +76,11 @@ int lobpcg_apply_local_noalloc(lobpcg_ctx *ctx, int k, const void *X, void *Y, i
     if (nb == 0) return LOBPCG_OK;
     if (!X || !Y) return fail(LOBPCG_ERR_ARG, "X and Y must not be NULL");
     if (precision != LOBPCG_C128 && precision != LOBPCG_C64) return fail(LOBPCG_ERR_ARG, "unknown precision");
+    int dev = -1;
+    LG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != v.device)
+        return fail(LOBPCG_ERR_ARG, "the current device is not the handle's device (" + std::to_string(dev) +
+                                        " vs " + std::to_string(v.device) + ")");
     if (!is_device_pointer(X) || !is_device_pointer(Y))
         return fail(LOBPCG_ERR_ARG, "X and Y must be device pointers (no staging without allocation)");
     const size_t esz = precision == LOBPCG_C128 ? sizeof(z64) : sizeof(c32);

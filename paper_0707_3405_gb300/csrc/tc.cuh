@@ -109,10 +109,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, int count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait for phase `parity` of the mbarrier to complete; bounded.  Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// Wait for phase `parity` of the mbarrier to complete; at most `limit` polls.  Returns false
+// on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long limit = kSpinLimit) {
     const uint32_t a = smem_u32(mbar);
-    for (long long it = 0; it < kSpinLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -45,6 +45,10 @@ constexpr int KBC = 16;     // complex K per stage: 32 floats = one 128-byte sha
 constexpr int ROWB = 128;   // bytes per shared row
 
 __device__ int g_tc_err = 0;
+// Poll limit of the ring waits (a stage's MMAs done before its refill); the drain wait for the
+// MMAs a CTA has issued always takes the full kSpinLimit, so a CTA that gave up never frees
+// TMEM or returns while its own MMAs may still run.  Lowered only by tests of the timeout path.
+__device__ long long g_tc_spin = kSpinLimit;
 
 // Byte offset of complex element kc (0..15) of row r in a 128-byte-swizzled K-major tile.
 __device__ __forceinline__ uint32_t swz(int r, int kc) {
@@ -141,7 +145,7 @@ k_tc_cn(int m, int n, int K, int kchunk, const c32 *__restrict__ A, int lda, con
     if (nkb > 0) load(0);
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % NS;
-        if (kb >= NS && !mbar_wait(&bar[s], (uint32_t)((kb / NS - 1) & 1))) bad = 1;
+        if (kb >= NS && !mbar_wait(&bar[s], (uint32_t)((kb / NS - 1) & 1), g_tc_spin)) bad = 1;
         unsigned char *sAh = base + s * STAGE, *sAl = sAh + A_BYTES, *sBh = sAl + A_BYTES, *sBl = sBh + B_BYTES;
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
@@ -262,7 +266,7 @@ k_tc_nn(int M, int n, int k, float alpha, const c32 *__restrict__ A, int lda, co
     if (nkb > 0) load(0);
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % NS;
-        if (kb >= NS && !mbar_wait(&bar[s], (uint32_t)((kb / NS - 1) & 1))) bad = 1;
+        if (kb >= NS && !mbar_wait(&bar[s], (uint32_t)((kb / NS - 1) & 1), g_tc_spin)) bad = 1;
         unsigned char *sAh = base + s * STAGE, *sAl = sAh + A_BYTES, *sBh = sAl + A_BYTES, *sBl = sBh + B_BYTES;
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
@@ -417,6 +421,12 @@ int *device_wait_flag() {
         cached.store(p);
     }
     return p;
+}
+
+int tc_set_spin_limit(long long polls) {
+    const long long v = polls < 0 ? kSpinLimit : polls;
+    LG_CUDA_TRY(cudaMemcpyToSymbol(g_tc_spin, &v, sizeof(v)));
+    return LOBPCG_OK;
 }
 
 int tc_check_error() {
