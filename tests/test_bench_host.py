@@ -1,6 +1,6 @@
 """Host-side logic of bench.py, on CPU: the replica aggregation at world size 2 over gloo, the
-reference arm's JSON line (rank 0 only under a multi-rank launch), the choice of roofline and
-the per-phase rates."""
+reference arm's JSON line (rank 0 only under a multi-rank launch), the roofline object of the
+dominant kernel, the oracle extrapolation and the per-phase rates."""
 import json
 import os
 import socket
@@ -72,7 +72,7 @@ def test_reference_arm_prints_one_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference"
-    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["higher_is_better"] is False and d["unit"] == "s"
     assert d["config"]["workload"] == "gamma24"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
@@ -91,31 +91,30 @@ def _phases(**ms):
     return {p: float(ms.get(p, 0.0)) for p in names}
 
 
-def test_roofline_picks_the_longest_segment():
+def test_roofline_reports_the_dominant_kernel():
     sys.path.insert(0, ROOT)
     import bench
-    pk = {"hbm_gbs": 6000.0, "bf16_tflops": 1900.0}
-    # FFT phase dominant, FP32: HBM-bound, achieved = bytes / time
-    ms = _phases(fft=100.0, rr=10.0)
-    zero = _phases()
-    by = _phases(fft=300e9, rr=1e9)
-    fl = _phases(fft=0.0, rr=1e10)
-    roof = bench.roofline_of(ms, zero, fl, zero, by, zero, _phases(fft=4, rr=2), 2, pk, "measured")
-    assert roof["bound"] == "hbm" and roof["phase"] == "fft" and roof["precision"] == "fp32"
-    assert roof["achieved"] == pytest.approx(300e9 / 0.1 / 1e9)
-    assert roof["frac"] == pytest.approx(roof["achieved"] / 6000.0)
-    assert roof["calls_per_step"] == 2.0
-    assert roof["phase_share"] == pytest.approx(100.0 / 110.0)
-    # Rayleigh-Ritz in FP64-class arithmetic dominant: FP64 ALU roofline
-    ms = _phases(fft=10.0, rr=200.0)
-    ms64 = _phases(rr=150.0)
-    fl = _phases(rr=2e11)
-    fl64 = _phases(rr=1.5e11)
-    by = _phases(fft=1e9, rr=1e9)
-    roof = bench.roofline_of(ms, ms64, fl, fl64, by, zero, _phases(fft=1, rr=1), 1, pk, "measured")
-    assert roof["bound"] == "alu" and roof["alu"] == "fp64" and roof["phase"] == "rr"
-    assert roof["achieved"] == pytest.approx(1.5e11 / 0.15 / 1e12)
-    assert roof["frac"] == pytest.approx(roof["achieved"] / bench.FP64_PEAK_TFLOPS)
+    kr = {"fp64class_gemm": {"kernel": "k", "shape": [1, 2, 3], "bound": "tensor", "unit": "TFLOP/s",
+                             "ms": 2.0, "achieved": 40.0, "peak": 80.0, "frac": 0.5, "work_per_launch": "x",
+                             "peak_source": "MEASURED_PEAKS.json bf16_tflops"},
+          "fft_c64": {"error": "boom"}}
+    roof = bench.roofline_of(kr)
+    assert roof["bound"] == "tensor" and roof["frac"] == 0.5 and roof["achieved"] == 40.0
+    assert roof["traffic"] is None and "of measured" in roof["peak_source"]
+    bad = bench.roofline_of(kr, "fft_c64")
+    assert bad["frac"] is None and bad["error"] == "boom"
+
+
+def test_oracle_extrapolation_counts_every_block_visit():
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    w = synth.make_workload("gamma120")
+    # 9 sweeps x (1024 + 128) / 128 blocks x 1 k-point visits of 20 s
+    assert bench.oracle_s_to_tol(w, 20.0, 128) == pytest.approx(9 * 9 * 20.0)
+    w4 = synth.make_workload("mp72x10")
+    assert bench.oracle_s_to_tol(w4, 1.0, 64) == pytest.approx(6 * 3 * 10)
+    assert bench.nbuf_of(w, -1) == 128 and bench.nbuf_of(w, 0) == 0
 
 
 def test_phase_rates_split_native_fp64_from_the_rest():
@@ -137,12 +136,15 @@ def test_phase_rates_split_native_fp64_from_the_rest():
 
 
 def test_kernel_rooflines_never_raise():
-    """Without a GPU the side measurement reports its error instead of raising, so a failed
+    """Without a GPU each side measurement reports its error instead of raising, so a failed
     kernel timing cannot cost the bench line."""
     sys.path.insert(0, ROOT)
     import bench
+    import synth
     import torch
     if torch.cuda.is_available():
         pytest.skip("CPU-only check")
-    out = bench.kernel_rooflines(1000, 8, 4, {"hbm_gbs": 1.0, "bf16_tflops": 1.0})
-    assert set(out) == {"error"}
+    out = bench.kernel_rooflines(synth.make_workload("gamma24"), 925, 16, {"hbm_gbs": 1.0, "bf16_tflops": 1.0})
+    assert set(out) == {"fp64class_gemm", "gram_3xtf32", "fft_c64"}
+    assert all("error" in v for v in out.values())
+    assert bench.roofline_of(out)["frac"] is None
