@@ -78,6 +78,12 @@ extern "C" {
                                        pairs of FP32 numbers, error-free TwoSum / TwoProd steps,
                                        about 2^-47 relative per operation (FP64 class) at several
                                        times this GPU's FP64 rate */
+#define LOBPCG_C128_TC 3            /* complex128 in/out, FFT in double-FP32 arithmetic and GEMMs
+                                       on the tensor cores: each real value split exactly into six
+                                       8-bit BF16 digits with one power-of-two scale per 64 terms of
+                                       the reduction, digit products summed exactly in FP32 per
+                                       64 terms, partial sums in double-FP32 (error about 2^-44 of
+                                       sum |a||b|, FP64 class) */
 
 /* Precision schedule of lobpcg_solve (lobpcg_options.precision). */
 #define LOBPCG_FP64  0              /* every step in FP64 */
@@ -125,10 +131,13 @@ typedef struct {
     int    fp64_gemm;    /* arithmetic of the FP64-class work limited by this GPU's FP64 units: the tall
                             GEMMs (Grams, constraint, Ritz updates, KB projections of FP64 H X) and, in
                             the Rayleigh-Ritz step, the Cholesky diagonal blocks, the tridiagonalisation's
-                            column work and the small products.  0 = auto (MIXED: double-FP32 on the FP32
-                            units, about 2^-47 relative per operation; FP64: native FP64), 1 = native
-                            FP64, 2 = double-FP32 on both schedules.  The serial recurrences
-                            (multisection, inverse iteration, back-transformation) stay FP64. */
+                            column work and the small products.  0 = auto (MIXED: tall GEMMs on the
+                            tensor cores as in 3, the rest double-FP32; FP64: native FP64), 1 = native
+                            FP64, 2 = double-FP32 on the FP32 units (about 2^-47 relative per operation)
+                            on both schedules, 3 = like 2 but the tall GEMMs on the tensor cores with
+                            exact BF16 digit slices (the LOBPCG_C128_TC arithmetic).  The serial
+                            recurrences (multisection, inverse iteration, back-transformation) stay
+                            FP64. */
 } lobpcg_options;
 
 /* Phases of a solve, for the per-phase timers of lobpcg_stats. */
@@ -220,7 +229,7 @@ int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller);
 /*
  * Y = H X for nb bands of k-point k (Sec. 2.2 items iii and iv).
  *   X, Y       npw_k x nb, column-major (ld = npw_k), complex128 when
- *              precision = LOBPCG_C128 or LOBPCG_C128_DF32, complex64 when
+ *              precision = LOBPCG_C128, LOBPCG_C128_DF32 or LOBPCG_C128_TC, complex64 when
  *              LOBPCG_C64.  Device
  *              pointers run fully asynchronously on the handle's stream; host
  *              pointers are staged through device buffers and the call returns

@@ -14,7 +14,13 @@
  *     every operand split into two FP32 parts, exact FP32 products by FMA
  *     (Dekker's TwoProd) and pair accumulators (Knuth's TwoSum), about 2^-47
  *     relative per product, run on the FP32 units (FP64 class, several
- *     times the FP64 rate of this GPU).
+ *     times the FP64 rate of this GPU), or LOBPCG_C128_TC complex128 on the
+ *     tensor cores: each real value split exactly into six 8-bit BF16
+ *     digits with a power-of-two scale per 64 terms of the reduction, the
+ *     digit products of equal weight summed exactly in FP32 per 64 terms,
+ *     those sums added in double-FP32 (error about 2^-44 of sum |a||b|,
+ *     FP64 class; error-free slicing after Ozaki, Ogita, Oishi and Rump,
+ *     Numer. Algorithms 2012).
  *   - Pointers are device pointers; work is enqueued on `stream`
  *     (cudaStream_t, NULL = legacy default stream) and the call returns
  *     without synchronising, except where noted.
@@ -50,15 +56,16 @@ int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A,
                      const void *B, int ldb, double beta, void *C, int ldc, void *stream);
 
 /*
- * Lower triangle of C = A^H B, complex128 (prec = LOBPCG_C128 or
- * LOBPCG_C128_DF32): the FP64-class Gram matrices of
+ * Lower triangle of C = A^H B, complex128 (prec = LOBPCG_C128,
+ * LOBPCG_C128_DF32 or LOBPCG_C128_TC): the FP64-class Gram matrices of
  * Algorithm 1, step 4 and of the all-band Rayleigh-Ritz closing a sweep
  * (Sec. 3.2).  Both Grams of the Rayleigh-Ritz pencil are Hermitian and the
  * pencil solver reads only their lower triangles, so 64 x 64 output tiles
  * strictly above the diagonal are skipped: about half the work for n >> 64.
  *   A and B are K x n (lda, ldb >= K), C is n x n (ldc >= n).  Every element
  *   C(i, j) with i >= j is written; tiles strictly above the diagonal are
- *   left untouched, and the rest of the upper triangle holds A^H B values.
+ *   left untouched, and the rest of the upper triangle holds A^H B values
+ *   (LOBPCG_C128_TC writes the entries with i >= j only).
  *   Same split and fixed summation order as lobpcg_k_gemm_cn.
  */
 int lobpcg_k_gram_lower(int prec, int n, int K, const void *A, int lda, const void *B, int ldb, void *C,

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblobpcg_gb300.so")
 
 OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BREAKDOWN, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-C128, C64, C128_DF32 = 0, 1, 2
+C128, C64, C128_DF32, C128_TC = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
 EXPORTED = (
@@ -260,10 +260,11 @@ class Solver:
         colmajor = np.ascontiguousarray(b.T)
         _check(self._lib.lobpcg_set_projectors(self.handle, k, colmajor.ctypes.data), self.handle)
 
-    def apply_H(self, k: int, X, Y=None, df32: bool = False):
+    def apply_H(self, k: int, X, Y=None, df32: bool = False, tc: bool = False):
         """Y = H X for a (nb, npw) block: torch CUDA tensor (asynchronous on the
         handle's stream) or numpy array (staged, synchronous).  complex128 runs
-        in FP64 (or double-FP32 with df32=True), complex64 in FP32."""
+        in FP64 (or double-FP32 with df32=True, or double-FP32 FFT with the KB
+        products on the tensor cores with tc=True), complex64 in FP32."""
         import torch
         if isinstance(X, np.ndarray):
             prec = C128 if X.dtype == np.complex128 else C64
@@ -283,10 +284,10 @@ class Solver:
         nb = 0 if X.shape[0] == 0 else int(X.shape[0])
         if nb and X.shape[-1] != self.npw(k):
             raise ValueError("X must have shape (nb, npw_k)")
-        if df32:
+        if df32 or tc:
             if prec != C128:
-                raise ValueError("df32 needs complex128 vectors")
-            prec = C128_DF32
+                raise ValueError("df32 / tc need complex128 vectors")
+            prec = C128_TC if tc else C128_DF32
         _check(self._lib.lobpcg_apply_H(self.handle, k, _ptr(X), _ptr(Y), nb, prec), self.handle)
         return Y
 
@@ -367,17 +368,24 @@ def check_timeouts():
     _check(load().lobpcg_k_check_timeouts(), None, kernels=True)
 
 
-def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None, df32=False):
+def _prec128(dtype, df32, tc):
+    import torch
+    prec = C128 if dtype == torch.complex128 else C64
+    if df32 or tc:
+        if prec != C128:
+            raise ValueError("df32 / tc need complex128 operands")
+        prec = C128_TC if tc else C128_DF32
+    return prec
+
+
+def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None, df32=False, tc=False):
     """C = alpha A^H B + beta C for torch CUDA tensors given as (cols, rows) row-major
     (i.e. column-major matrices): A is (m, K), B is (n, K), C is (n, m).  df32=True
-    (complex128 only) runs the double-FP32 engine instead of FP64 arithmetic."""
+    (complex128 only) runs the double-FP32 engine instead of FP64 arithmetic, tc=True
+    the FP64-class tensor-core engine (exact BF16 digit slices)."""
     import torch
     lib = load()
-    prec = C128 if A.dtype == torch.complex128 else C64
-    if df32:
-        if prec != C128:
-            raise ValueError("df32 needs complex128 operands")
-        prec = C128_DF32
+    prec = _prec128(A.dtype, df32, tc)
     m, K = A.shape
     n = B.shape[0]
     if C is None:
@@ -387,10 +395,11 @@ def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None, df32=False):
     return C
 
 
-def gram_lower(A, B, C=None, stream=None, df32=False):
+def gram_lower(A, B, C=None, stream=None, df32=False, tc=False):
     """Lower triangle of C = A^H B (complex128), column-major as in gemm_cn: A and B are
     (n, K), C is (n, n).  Tiles of C strictly above the diagonal are left untouched.
-    df32=True runs the double-FP32 engine instead of FP64 arithmetic."""
+    df32=True runs the double-FP32 engine instead of FP64 arithmetic, tc=True the
+    tensor-core engine (which writes only the entries i >= j)."""
     import torch
     lib = load()
     n, K = A.shape
@@ -398,21 +407,17 @@ def gram_lower(A, B, C=None, stream=None, df32=False):
         raise ValueError("gram_lower: A and B must be complex128 of the same shape")
     if C is None:
         C = torch.zeros((n, n), dtype=A.dtype, device=A.device)
-    _check(lib.lobpcg_k_gram_lower(C128_DF32 if df32 else C128, n, K, _ptr(A), K, _ptr(B), K, _ptr(C), n,
+    _check(lib.lobpcg_k_gram_lower(C128_TC if tc else (C128_DF32 if df32 else C128), n, K, _ptr(A), K, _ptr(B), K, _ptr(C), n,
                                    _stream_handle(stream)), None, kernels=True)
     return C
 
 
-def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None, df32=False):
+def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None, df32=False, tc=False):
     """D = alpha A B + beta C, column-major stored as transposed torch tensors:
-    A is (k, M), B is (n, k), C and D are (n, M).  df32=True as in gemm_cn."""
+    A is (k, M), B is (n, k), C and D are (n, M).  df32 and tc as in gemm_cn."""
     import torch
     lib = load()
-    prec = C128 if A.dtype == torch.complex128 else C64
-    if df32:
-        if prec != C128:
-            raise ValueError("df32 needs complex128 operands")
-        prec = C128_DF32
+    prec = _prec128(A.dtype, df32, tc)
     k, M = A.shape
     n = B.shape[0]
     if D is None:

@@ -422,7 +422,8 @@ int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y
             if (df) {  // double-FP32 projections (FP64 class)
                 LG_TRY(zgemm_cn_df(L.gw, c->nproj, nb, K.npw, 1.0, beta, K.npw, X, ldx, 0.0, B, c->nproj, L.stream));
                 LG_TRY(scale_rows<R>(c->nproj, nb, Tables<R>::E(c), B, c->nproj, L.stream));
-                return zgemm_nn_df(K.npw, nb, c->nproj, 1.0, beta, K.npw, B, c->nproj, 1.0, Y, ldy, Y, ldy, L.stream);
+                return zgemm_nn_df(&L.gw, K.npw, nb, c->nproj, 1.0, beta, K.npw, B, c->nproj, 1.0, Y, ldy, Y, ldy,
+                                   L.stream);
             }
         }
         LG_TRY(gemm_cn<R>(L.gw, c->nproj, nb, K.npw, (R)1, beta, K.npw, X, ldx, (R)0, B, c->nproj, L.stream));
@@ -601,7 +602,7 @@ struct Solver {
     int gemm_nn64(int ph, int nn, int kk, double alpha, const z64 *Aa, const z64 *Bb, int ldb, double beta,
                   const z64 *Cc, z64 *Dd) {
         PhaseScope ps(prof, ph, 8.0 * nn * kk * (double)npw, cbytes64(kk + nn * (beta != 0.0 ? 2 : 1)), !df);
-        if (df) return zgemm_nn_df(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
+        if (df) return zgemm_nn_df(&L->gw, npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
         return gemm_nn<double>(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
     }
     int gemm_cn32(int ph, int mm, int nn, const c32 *Aa, const c32 *Bb, c32 *Cc, int ldc) {
@@ -1030,8 +1031,11 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     sv.m = c->opt.block_size;
     sv.nblk = M / sv.m;
     sv.mixed = c->opt.precision == LOBPCG_MIXED;
-    sv.df = c->opt.fp64_gemm == 2 || (c->opt.fp64_gemm == 0 && sv.mixed);
+    sv.df = c->opt.fp64_gemm >= 2 || (c->opt.fp64_gemm == 0 && sv.mixed);
     L.ew.df = sv.df;  // the Rayleigh-Ritz step's FP64-unit-bound parts likewise
+    // the tall FP64-class GEMMs on the tensor cores (exact digit slices); the side lane of the
+    // H X refresh follows (its KB projections)
+    L.gw.oz = c->opt.fp64_gemm == 3 || (c->opt.fp64_gemm == 0 && sv.mixed);
     sv.X = X;
     sv.s = L.stream;
     sv.drop_tol = 1e-12;
@@ -1049,6 +1053,7 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     if (c->opt.precision == LOBPCG_MIXED) {
         sv.HXr = carve<z64>(c, L.HXr, (size_t)npw * M, rc); LG_TRY(rc);
         LG_TRY(L.make_side(&c->alloc));
+        L.side->gw.oz = L.gw.oz;
     }
     sv.Tmp = carve<z64>(c, L.Tmp, (size_t)npw * M, rc); LG_TRY(rc);
     sv.S = carve<z64>(c, L.Gram, (size_t)nzmax * nzmax, rc); LG_TRY(rc);
@@ -1174,7 +1179,7 @@ int validate_options(const lobpcg_options &o) {
         return fail(LOBPCG_ERR_ARG, "gemm_split must be 0, 2 or 3");
     if (!(o.mixed_switch >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_switch must be >= 0");
     if (!(o.mixed_early >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_early must be >= 0");
-    if (o.fp64_gemm < 0 || o.fp64_gemm > 2) return fail(LOBPCG_ERR_ARG, "fp64_gemm must be 0, 1 or 2");
+    if (o.fp64_gemm < 0 || o.fp64_gemm > 3) return fail(LOBPCG_ERR_ARG, "fp64_gemm must be 0, 1, 2 or 3");
     return LOBPCG_OK;
 }
 
@@ -1361,7 +1366,8 @@ static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int 
     if (nb < 0) return fail(LOBPCG_ERR_ARG, "nb must be >= 0");
     if (nb == 0) return LOBPCG_OK;
     if (!X || !Y) return fail(LOBPCG_ERR_ARG, "X and Y must not be NULL");
-    if (precision != LOBPCG_C128 && precision != LOBPCG_C64 && precision != LOBPCG_C128_DF32)
+    if (precision != LOBPCG_C128 && precision != LOBPCG_C64 && precision != LOBPCG_C128_DF32 &&
+        precision != LOBPCG_C128_TC)
         return fail(LOBPCG_ERR_ARG, "unknown precision");
     const int npw = c->kp[k].npw;
     const size_t esz = precision == LOBPCG_C64 ? sizeof(c32) : sizeof(z64);
@@ -1381,9 +1387,13 @@ static int apply_impl(lobpcg_ctx *c, int k, const void *X, void *Y, int nb, int 
         LG_TRY(c->alloc.ensure(L.stageY, bytes));
         Yd = L.stageY.p;
     }
-    if (precision != LOBPCG_C64)
-        LG_TRY(apply_H_dev<double>(c, L, k, static_cast<const z64 *>(Xd), npw, static_cast<z64 *>(Yd), npw, nb,
-                                   nullptr, precision == LOBPCG_C128_DF32));
+    if (precision != LOBPCG_C64) {
+        L.gw.oz = precision == LOBPCG_C128_TC;
+        const int rc = apply_H_dev<double>(c, L, k, static_cast<const z64 *>(Xd), npw, static_cast<z64 *>(Yd), npw,
+                                           nb, nullptr, precision == LOBPCG_C128_DF32 || precision == LOBPCG_C128_TC);
+        L.gw.oz = false;
+        LG_TRY(rc);
+    }
     else
         LG_TRY(apply_H_dev<float>(c, L, k, static_cast<const c32 *>(Xd), npw, static_cast<c32 *>(Yd), npw, nb));
     if (!dy) {
@@ -1519,8 +1529,12 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         L0.bind(&c->alloc, nullptr, 1);
         L0.stream = c->stream;
         const bool mixed = c->opt.precision == LOBPCG_MIXED;
-        const bool df = c->opt.fp64_gemm == 2 || (c->opt.fp64_gemm == 0 && mixed);
-        for (int k = 0; k < c->nk; ++k) LG_TRY(autotune_k(c, L0, k, df, m));
+        const bool df = c->opt.fp64_gemm >= 2 || (c->opt.fp64_gemm == 0 && mixed);
+        L0.gw.oz = c->opt.fp64_gemm == 3 || (c->opt.fp64_gemm == 0 && mixed);
+        int rc_t = LOBPCG_OK;
+        for (int k = 0; k < c->nk && rc_t == LOBPCG_OK; ++k) rc_t = autotune_k(c, L0, k, df, m);
+        L0.gw.oz = false;
+        LG_TRY(rc_t);
         ms_tune = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
     }
     const auto t0 = std::chrono::steady_clock::now();

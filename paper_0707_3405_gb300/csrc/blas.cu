@@ -378,6 +378,7 @@ int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, 
 
 int zgemm_cn_lower(GemmWork &w, int n, int K, const z64 *A, int lda, const z64 *B, int ldb, z64 *C, int ldc,
                    cudaStream_t s, bool df) {
+    if (df && w.oz) return oz_gemm_cn(w, n, n, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, s, true);
     if (df)
         return launch_gemm_t<double, true, false, 4, true>(&w, n, n, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, C, ldc, s,
                                                           true, 4 * BK, true);
@@ -387,13 +388,15 @@ int zgemm_cn_lower(GemmWork &w, int n, int K, const z64 *A, int lda, const z64 *
 int zgemm_cn_df(GemmWork &w, int m, int n, int K, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
                 double beta, z64 *C, int ldc, cudaStream_t s) {
     if (m <= 0 || n <= 0) return LOBPCG_OK;
+    if (w.oz) return oz_gemm_cn(w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, s, false);
     return launch_gemm_t<double, true, false, 4, true>(&w, m, n, K, alpha, A, lda, B, ldb, beta, C, ldc, C, ldc, s,
                                                       true, 4 * BK, false);
 }
 
-int zgemm_nn_df(int M, int n, int k, double alpha, const z64 *A, int lda, const z64 *B, int ldb, double beta,
-                const z64 *C, int ldc, z64 *D, int ldd, cudaStream_t s) {
+int zgemm_nn_df(GemmWork *w, int M, int n, int k, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
+                double beta, const z64 *C, int ldc, z64 *D, int ldd, cudaStream_t s) {
     if (M <= 0 || n <= 0) return LOBPCG_OK;
+    if (w && w->oz && k > 0) return oz_gemm_nn(*w, M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D, ldd, s);
     return launch_gemm_t<double, false, false, 4, true>(nullptr, M, n, k, alpha, A, lda, B, ldb, beta, C, ldc, D,
                                                        ldd, s, false, 4 * BK, false);
 }

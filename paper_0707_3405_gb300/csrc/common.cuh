@@ -229,6 +229,10 @@ struct GemmWork {
     Allocator *alloc = nullptr;
     DevBuf part;
     bool df = false;  // complex128 gemm_small in double-FP32 arithmetic
+    // The FP64-class tall products (zgemm_cn_df, zgemm_nn_df, zgemm_cn_lower with df) run on the
+    // tensor cores with exact 8-bit BF16 slices (oz_gemm.cu) instead of double-FP32 CUDA cores.
+    bool oz = false;
+    DevBuf oz_a, oz_e, oz_p;  // digit tiles, chunk exponents, FP64 partial tiles
 };
 template <typename R>
 int gemm_cn(GemmWork &w, int m, int n, int K, R alpha, const cx<R> *A, int lda, const cx<R> *B, int ldb,
@@ -242,8 +246,18 @@ int zgemm_cn_lower(GemmWork &w, int n, int K, const z64 *A, int lda, const z64 *
 // arithmetic on the FP32 units (tall products; K split as for gemm_cn).
 int zgemm_cn_df(GemmWork &w, int m, int n, int K, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
                 double beta, z64 *C, int ldc, cudaStream_t s);
-int zgemm_nn_df(int M, int n, int k, double alpha, const z64 *A, int lda, const z64 *B, int ldb, double beta,
-                const z64 *C, int ldc, z64 *D, int ldd, cudaStream_t s);
+// w (nullable) carries the engine choice (w->oz) and its scratch.
+int zgemm_nn_df(GemmWork *w, int M, int n, int k, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
+                double beta, const z64 *C, int ldc, z64 *D, int ldd, cudaStream_t s);
+// FP64-class complex128 products on the tensor cores: digits of 8 bits (six BF16 slices per real
+// value, per-64-term chunk power-of-two scales), exact FP32 accumulation per chunk, double-FP32
+// sums across chunks (error about 2^-44 of sum |a||b|).  C = alpha A^H B + beta C (lower: only
+// i >= j written) and D = alpha A B + beta C.
+int oz_gemm_cn(GemmWork &w, int m, int n, int K, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
+               double beta, z64 *C, int ldc, cudaStream_t s, bool lower);
+int oz_gemm_nn(GemmWork &w, int M, int n, int k, double alpha, const z64 *A, int lda, const z64 *B, int ldb,
+               double beta, const z64 *C, int ldc, z64 *D, int ldd, cudaStream_t s);
+int oz_check_error();   // LOBPCG_ERR_TIMEOUT if a wait inside oz_gemm ran out (clears the flag)
 // Complex64 products on the tensor cores (3xTF32 split operands, FP32 accumulation):
 // C = alpha A^H B + beta C (K split over the GPU, FP64 partial sums) and
 // D = alpha A B + beta C.  gemm_cn<float> / gemm_nn<float> route here for long

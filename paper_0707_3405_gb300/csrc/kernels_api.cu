@@ -34,9 +34,18 @@ std::mutex &pool_mutex() {
 
 extern "C" {
 
+namespace {
+// Engine flag of the pool's GEMM scratch for one call (FP64-class on the tensor cores or not).
+struct OzScope {
+    GemmWork &w;
+    OzScope(GemmWork &w_, bool on) : w(w_) { w.oz = on; }
+    ~OzScope() { w.oz = false; }
+};
+}  // namespace
+
 int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A, int lda, const void *B, int ldb,
                      double beta, void *C, int ldc, void *stream) {
-    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C64)
+    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C128_TC && prec != LOBPCG_C64)
         return fail(LOBPCG_ERR_ARG, "unknown precision");
     if (m < 0 || n < 0 || K < 0) return fail(LOBPCG_ERR_ARG, "negative size");
     if (m == 0 || n == 0) return LOBPCG_OK;
@@ -46,9 +55,11 @@ int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A,
     if (prec == LOBPCG_C128)
         return gemm_cn<double>(pool().gw, m, n, K, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B),
                                ldb, beta, static_cast<z64 *>(C), ldc, s);
-    if (prec == LOBPCG_C128_DF32)
+    if (prec == LOBPCG_C128_DF32 || prec == LOBPCG_C128_TC) {
+        OzScope oz(pool().gw, prec == LOBPCG_C128_TC);
         return zgemm_cn_df(pool().gw, m, n, K, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B),
                            ldb, beta, static_cast<z64 *>(C), ldc, s);
+    }
     if (prec == LOBPCG_C64)
         return gemm_cn<float>(pool().gw, m, n, K, (float)alpha, static_cast<const c32 *>(A), lda,
                               static_cast<const c32 *>(B), ldb, (float)beta, static_cast<c32 *>(C), ldc, s);
@@ -57,19 +68,21 @@ int lobpcg_k_gemm_cn(int prec, int m, int n, int K, double alpha, const void *A,
 
 int lobpcg_k_gram_lower(int prec, int n, int K, const void *A, int lda, const void *B, int ldb, void *C,
                         int ldc, void *stream) {
-    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32) return fail(LOBPCG_ERR_ARG, "unknown precision");
+    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C128_TC)
+        return fail(LOBPCG_ERR_ARG, "unknown precision");
     if (n < 0 || K < 0) return fail(LOBPCG_ERR_ARG, "negative size");
     if (n == 0) return LOBPCG_OK;
     if (!A || !B || !C || lda < K || ldb < K || ldc < n) return fail(LOBPCG_ERR_ARG, "bad pointer or leading dimension");
     std::lock_guard<std::mutex> lk(pool_mutex());
+    OzScope oz(pool().gw, prec == LOBPCG_C128_TC);
     return zgemm_cn_lower(pool().gw, n, K, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb,
                           static_cast<z64 *>(C), ldc, reinterpret_cast<cudaStream_t>(stream),
-                          prec == LOBPCG_C128_DF32);
+                          prec != LOBPCG_C128);
 }
 
 int lobpcg_k_gemm_nn(int prec, int M, int n, int k, double alpha, const void *A, int lda, const void *B, int ldb,
                      double beta, const void *C, int ldc, void *D, int ldd, void *stream) {
-    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C64)
+    if (prec != LOBPCG_C128 && prec != LOBPCG_C128_DF32 && prec != LOBPCG_C128_TC && prec != LOBPCG_C64)
         return fail(LOBPCG_ERR_ARG, "unknown precision");
     if (M < 0 || n < 0 || k < 0) return fail(LOBPCG_ERR_ARG, "negative size");
     if (M == 0 || n == 0) return LOBPCG_OK;
@@ -80,8 +93,14 @@ int lobpcg_k_gemm_nn(int prec, int M, int n, int k, double alpha, const void *A,
         return gemm_nn<double>(M, n, k, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb, beta,
                                static_cast<const z64 *>(C), ldc, static_cast<z64 *>(D), ldd, s);
     if (prec == LOBPCG_C128_DF32)
-        return zgemm_nn_df(M, n, k, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb, beta,
-                           static_cast<const z64 *>(C), ldc, static_cast<z64 *>(D), ldd, s);
+        return zgemm_nn_df(nullptr, M, n, k, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B), ldb,
+                           beta, static_cast<const z64 *>(C), ldc, static_cast<z64 *>(D), ldd, s);
+    if (prec == LOBPCG_C128_TC) {
+        std::lock_guard<std::mutex> lk(pool_mutex());
+        OzScope oz(pool().gw, true);
+        return zgemm_nn_df(&pool().gw, M, n, k, alpha, static_cast<const z64 *>(A), lda, static_cast<const z64 *>(B),
+                           ldb, beta, static_cast<const z64 *>(C), ldc, static_cast<z64 *>(D), ldd, s);
+    }
     if (prec == LOBPCG_C64)
         return gemm_nn<float>(M, n, k, (float)alpha, static_cast<const c32 *>(A), lda, static_cast<const c32 *>(B), ldb,
                               (float)beta, static_cast<const c32 *>(C), ldc, static_cast<c32 *>(D), ldd, s);

@@ -438,7 +438,7 @@ int tc_check_error() {
         return fail(LOBPCG_ERR_TIMEOUT,
                     "a bounded device wait ran out (tensor-core GEMM mbarrier or tridiagonalisation grid barrier)");
     }
-    return LOBPCG_OK;
+    return oz_check_error();
 }
 
 }  // namespace lg

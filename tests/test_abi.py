@@ -84,7 +84,7 @@ def test_create_rejects_bad_arguments_before_any_device_call():
         (dict(opt=bad_opt(gemm_split=1)), ERR_UNSUPPORTED, "BF16x3"),
         (dict(opt=bad_opt(gemm_split=5)), ERR_ARG, "gemm_split"),
         (dict(opt=bad_opt(mixed_early=-1.0)), ERR_ARG, "mixed_early"),
-        (dict(opt=bad_opt(fp64_gemm=3)), ERR_ARG, "fp64_gemm"),
+        (dict(opt=bad_opt(fp64_gemm=4)), ERR_ARG, "fp64_gemm"),
     ]
     for kw, code, text in cases:
         rc, handle, msg = _raw_create(lib, lg, **kw)

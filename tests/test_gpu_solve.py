@@ -64,7 +64,7 @@ def test_solve_tiny_kb_kpoint(precision, M, m):
         _check_result(w, s, X, res, ref, orth=1e-12 if precision == "fp64" else 1e-10)
 
 
-@pytest.mark.parametrize("precision,fp64_gemm", [("fp64", 2), ("mixed", 1), ("mixed", 2)])
+@pytest.mark.parametrize("precision,fp64_gemm", [("fp64", 2), ("mixed", 1), ("mixed", 2), ("fp64", 3), ("mixed", 3)])
 def test_solve_fp64_gemm_engines(precision, fp64_gemm):
     """The FP64-class tall GEMMs in native FP64 (1) or double-FP32 (2) arithmetic on either
     schedule: the same eigenpairs to 1e-9 Ha (several blocks, constraint, KB projectors)."""

@@ -60,9 +60,9 @@ def test_gemm_wait_runs_out_and_returns(zero_spin):
 def test_solve_reports_timeout(zero_spin):
     import torch
     import paper_0707_3405_gb300 as lg
-    # 1563 plane waves: the mixed schedule's reductions run on the tensor cores
-    w = synth.tiny_workload(a=10.0, N=24, natoms=2, kb=True, nbands=8, block=4,
-                            ecut=0.5 * (2 * np.pi / 10.0 * 7.2) ** 2)
+    # about 17k plane waves: the mixed schedule's Grams run on the tensor cores with K splits of
+    # more stages than the ring holds, so their CTAs wait to refill it
+    w = synth.tiny_workload(a=16.0, N=64, natoms=2, kb=True, nbands=8, block=4)
     with make_solver(w, block_size=4, precision="mixed", max_sweeps=3) as s:
         X = torch.tensor(w.x0(s.npw(), 0, 8).T.copy(), device="cuda")
         with pytest.raises(lg.LobpcgError) as e:
