@@ -68,9 +68,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the warm-up and timed steps of --mode, no other legs")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply", "apply_df32"],
-                    help="with --ncu: LOBPCG sweeps, full solves to --tol, standalone apply_H, or the "
-                         "double-FP32 apply_H of the FP64-class H X")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply", "apply_df32", "fp64gemm"],
+                    help="with --ncu: LOBPCG sweeps, full solves to --tol, standalone apply_H, the "
+                         "double-FP32 apply_H of the FP64-class H X, or the FP64-class tensor-core A B "
+                         "(npw x nb x nb; nb = --nb, default the solve's band count)")
     ap.add_argument("--nb", type=int, default=0, help="with --ncu and an apply mode: bands (0 = all)")
     return ap.parse_args()
 
@@ -84,6 +85,27 @@ def ncu_run(args):
     __graft_entry__.build()
     w = make(args.workload)
     nbuf = nbuf_of(w, args.nbuf)
+    if args.mode == "fp64gemm":
+        lg.load()
+        import dataclasses
+        s0 = solver_for(dataclasses.replace(w, proj_E=np.zeros(0), kpts=w.kpts[:1]), "mixed")
+        M = s0.npw(0)
+        s0.close()
+        nb = args.nb if args.nb > 0 else w.nbands + nbuf
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3)
+        A = torch.randn((nb, M), dtype=torch.complex128, device="cuda", generator=g)
+        B = torch.randn((nb, nb), dtype=torch.complex128, device="cuda", generator=g)
+        D = torch.empty((nb, M), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.warmup + args.steps):
+            lg.gemm_nn(A, B, D=D, tc=True)
+        torch.cuda.synchronize()
+        lg.check_timeouts()
+        print(json.dumps({"ncu_run": True, "mode": args.mode, "shape": [M, nb, nb], "launches": lg.launch_count(),
+                          "s": time.perf_counter() - t0}))
+        return 0
     if args.mode == "solve":
         s = solver_for(w, args.precision, timing=False, max_sweeps=args.max_sweeps, tol=args.tol, nbuf=nbuf)
     else:
@@ -372,8 +394,9 @@ def phase_rates(ph_ms, ph_ms64, ph_fl, ph_fl64, ph_by, ph_by64, steps):
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 DF32_INSTR_PER_CMAC = 48.0
 TF32_PER_BF16 = 1.1 / 2.25        # nominal dense TF32 / BF16 tensor rates
-# Dominant kernel of the mixed solve on the benchmark cells (launch lists in profiles/): the
-# FP64-class GEMMs, timed here at the sweep-end rotation's shape.
+OZ_PAIRS = 21                     # digit-slice products per real product of the FP64-class tensor-core GEMM
+# Dominant kernel family of the mixed solve on the benchmark cells (launch lists in profiles/):
+# the FP64-class GEMMs, timed here at the sweep-end rotation's shape.
 DOMINANT = "fp64class_gemm"
 
 
@@ -397,7 +420,9 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
     on operands larger than L2, each against its own ceiling:
 
     * ``fp64class_gemm``: the FP64-class A B of the sweep-end rotation X C (npw x nbands x
-      nbands, complex128), the engine the mixed schedule uses;
+      nbands, complex128) on the tensor cores, the engine the mixed schedule uses: BF16 tensor
+      flops (21 digit-slice products per real product) against the measured BF16 rate; beside it
+      ``fp64class_gemm_df32``, the double-FP32 CUDA-core engine at the same shape;
     * ``gram_3xtf32``: the 3xTF32 tensor-core A^H B Gram of a block's [R W P] (3m x 3m x npw,
       complex64), tensor flops 3 x 8 m n K against the TF32 rate (measured BF16 x 1.1 / 2.25);
     * ``fft_c64``: the FP32 FFT passes A, B, C of H psi for one block (m bands) on a handle of the
@@ -411,7 +436,8 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
     try:
         stream = torch.cuda.current_stream()
     except Exception as e:  # no device: every entry records the error
-        return {k: {"error": f"{type(e).__name__}: {e}"} for k in ("fp64class_gemm", "gram_3xtf32", "fft_c64")}
+        return {k: {"error": f"{type(e).__name__}: {e}"}
+                for k in ("fp64class_gemm", "fp64class_gemm_df32", "gram_3xtf32", "fft_c64")}
     hbm = pk.get("hbm_gbs", FALLBACK["hbm_gbs"])
     tf32 = pk.get("bf16_tflops", FALLBACK["bf16_tflops"]) * TF32_PER_BF16
     m = w.block
@@ -422,12 +448,21 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
         A = torch.randn((k, M), dtype=torch.complex128, device="cuda", generator=g)
         B = torch.randn((n, k), dtype=torch.complex128, device="cuda", generator=g)
         D = torch.empty((n, M), dtype=torch.complex128, device="cuda")
-        t = _event_time(lambda: lg.gemm_nn(A, B, D=D, df32=True), reps, stream)
+        t = _event_time(lambda: lg.gemm_nn(A, B, D=D, tc=True), reps, stream)
         fl = 8.0 * M * n * k
-        peak = FP32_INSTR_PER_S / DF32_INSTR_PER_CMAC * 8.0 / 1e12
+        tfl = OZ_PAIRS * fl
+        bf16 = pk.get("bf16_tflops", FALLBACK["bf16_tflops"])
         out["fp64class_gemm"] = {
-            "kernel": "k_gemm_df<0,0,4>", "shape": [M, n, k], "bound": "alu", "unit": "TFLOP/s", "ms": t * 1e3,
-            "achieved": fl / t / 1e12, "peak": peak, "frac": fl / t / 1e12 / peak,
+            "kernel": "k_oz_split + k_oz_mma<1>", "shape": [M, n, k], "bound": "tensor", "unit": "TFLOP/s",
+            "ms": t * 1e3, "achieved": tfl / t / 1e12, "peak": bf16, "frac": tfl / t / 1e12 / bf16,
+            "fp64class_tflops": fl / t / 1e12,
+            "work_per_launch": f"{tfl:.4g} BF16 tensor flops ({OZ_PAIRS} digit-slice products x 8 M n k)",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops"}
+        t_df = _event_time(lambda: lg.gemm_nn(A, B, D=D, df32=True), 2, stream)
+        peak_df = FP32_INSTR_PER_S / DF32_INSTR_PER_CMAC * 8.0 / 1e12
+        out["fp64class_gemm_df32"] = {
+            "kernel": "k_gemm_df<0,0,4>", "shape": [M, n, k], "bound": "alu", "unit": "TFLOP/s", "ms": t_df * 1e3,
+            "achieved": fl / t_df / 1e12, "peak": peak_df, "frac": fl / t_df / 1e12 / peak_df,
             "work_per_launch": f"{fl:.4g} FP64-class flops (8 M n k)",
             "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz / 48 FP32 instructions per complex multiply-add"}
         del A, B, D

@@ -11,10 +11,11 @@
 //   * The reduction dimension is cut into chunks of 64 complex terms.  Within a
 //     chunk every operand vector (a row of the product's left or right factor)
 //     gets one power-of-two scale 2^e with max |x| < 2^e, and each real part is
-//     written exactly as x = 2^e sum_{p=1..6} d_p 2^{-8p} + (rest below
-//     2^{e-48}), with integer digits |d_1| <= 256, |d_p| <= 128 (round to
-//     nearest at each step; every step is exact in FP64).  Integers of that
-//     size are exact BF16 numbers.
+//     written as x = 2^e sum_{p=1..6} d_p 2^{-8p} + (rest at most 2^{e-49}),
+//     with integer digits |d_1| <= 256, |d_p| <= 128: x 2^{48-e} is rounded to
+//     an integer from its FP64 bit pattern and peeled into signed base-256
+//     digits with integer operations.  Integers of that size are exact BF16
+//     numbers.
 //   * x y = 2^{e_x + e_y} sum_{p,q} d_p d'_q 2^{-8(p+q)}: the digit products of
 //     one "level" l = p + q (l = 2..7; products with p + q > 7 are below 2^-48
 //     relative and dropped) are summed by the tensor core into one FP32
@@ -140,6 +141,29 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x, float y) {
     lo = e - (hi - s);
 }
 
+// The six base-256 digits of x relative to the chunk scale 2^e (|x| < 2^e), most significant
+// first: F = round(x 2^(48 - e)) is formed exactly from the mantissa with a rounding shift, then
+// peeled into signed digits d_6 .. d_2 in [-128, 127] from the low end; the rest, |d_1| <= 256,
+// is the top digit.  x = 2^e sum_p d_p 2^(-8p) up to 2^(e-49).  Integer operations only.
+__device__ __forceinline__ void digits(double x, int e, float (&d)[kSlices]) {
+    const long long bits = __double_as_longlong(x);
+    const int b = (int)((bits >> 52) & 0x7FF);
+    long long F = 0;
+    if (b > 0) {
+        const unsigned long long m = (unsigned long long)(bits & 0xFFFFFFFFFFFFFLL) | (1ULL << 52);
+        const int sh = 1027 + e - b;                       // >= 5 because |x| < 2^e
+        if (sh < 60) F = (long long)((m + (1ULL << (sh - 1))) >> sh);
+        if (bits < 0) F = -F;
+    }
+#pragma unroll
+    for (int p = kSlices - 1; p >= 1; --p) {
+        const long long dp = ((F + 128) & 0xFF) - 128;
+        d[p] = (float)dp;
+        F = (F - dp) >> 8;
+    }
+    d[0] = (float)F;
+}
+
 // ------------------------------------------------------------------ split
 // One CTA: 32 complex vectors x one chunk (64 complex terms) of the K range
 // [k0, k0 + nchunks * 64) of the operand X (element (v, k) at X[v * rs + k * ks]).
@@ -180,22 +204,27 @@ k_oz_split(const z64 *__restrict__ X, long long rs, long long ks, int nvec, int 
         }
     }
     __syncthreads();
-    // chunk exponent of each vector: 2^e > max |re|, |im| (e = 0 for an all-zero chunk)
+    // chunk exponent of each vector: 2^e > max |re|, |im| (e = 0 for an all-zero chunk).  Taken from
+    // the FP64 exponent fields with integer operations (this GPU's FP64 units are slow): a normal
+    // x with biased exponent b has |x| < 2^(b - 1022); subnormals count as zero.
     const int warp = tid >> 5, lane = tid & 31;
     for (int v = warp; v < 32; v += 8) {
-        double mx = 0.0;
-        for (int k = lane; k < kChunkC; k += 32) mx = fmax(mx, fmax(fabs(tile[v][k].x), fabs(tile[v][k].y)));
+        int bmax = 0;
+        for (int k = lane; k < kChunkC; k += 32) {
+            const int br = (int)((__double_as_longlong(tile[v][k].x) >> 52) & 0x7FF);
+            const int bi = (int)((__double_as_longlong(tile[v][k].y) >> 52) & 0x7FF);
+            bmax = max(bmax, max(br, bi));
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        for (int o = 16; o > 0; o >>= 1) bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
         if (lane == 0) {
-            int e = 0;
-            if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): mx < 2^e
+            const int e = bmax > 0 ? bmax - 1022 : 0;
             ex[v] = e;
             if (v0 + v < nvec_pad) E[(size_t)chunk * nvec_pad + v0 + v] = e;
         }
     }
     __syncthreads();
-    // digits: 8 elements per thread
+    // digits: 8 elements per thread, integer arithmetic on the FP64 bit patterns
 #pragma unroll 1
     for (int i = 0; i < 8; ++i) {
         const int idx = tid + 256 * i;
@@ -203,16 +232,9 @@ k_oz_split(const z64 *__restrict__ X, long long rs, long long ks, int nvec, int 
         if (v0 + v >= nvec_pad) continue;
         const double2 a = tile[v][k];
         const int e = ex[v];
-        double xr = ldexp(a.x, 8 - e), xi = ldexp(a.y, 8 - e);
         float dr[kSlices], di[kSlices];
-#pragma unroll
-        for (int p = 0; p < kSlices; ++p) {
-            const double r = rint(xr), s = rint(xi);
-            dr[p] = (float)r;
-            di[p] = (float)s;
-            xr = (xr - r) * 256.0;
-            xi = (xi - s) * 256.0;
-        }
+        digits(a.x, e, dr);
+        digits(a.y, e, di);
         const int kk = 2 * k;                       // real K of the re part within the chunk
         const int stage = chunk * kChunkStages + kk / kStageK, col = kk % kStageK;
 #pragma unroll
