@@ -241,6 +241,30 @@ int lobpcg_gvectors(const lobpcg_ctx *ctx, int k, int32_t *miller);
 int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int precision);
 
 /*
+ * Electron density of nb bands of k-point k on the real-space grid, the first
+ * step of the self-consistent loop (Sec. 2.1; computed by the same FFT as the
+ * local potential, Sec. 2.2 item iii, per-band contributions summed over
+ * bands as in Sec. 4.1):
+ *     rho(r_j) += sum_b f_b |psi_b(r_j)|^2,
+ *     psi_b(r) = Omega^-1/2 sum_G X[G, b] e^{i(k+G).r}   (Omega = a^3),
+ * so that (Omega / N^3) sum_j rho(r_j) = sum_b f_b for orthonormal bands.
+ *   X          device, npw_k x nb column-major, complex128 (precision =
+ *              LOBPCG_C128: FP64 transforms, or LOBPCG_C128_DF32:
+ *              double-FP32 transforms) or complex64 (LOBPCG_C64: FP32
+ *              transforms, FP32 sums over each band batch).
+ *   f          host, nb doubles: occupations (k-point weight included).
+ *   rho        device, N^3 doubles, C-order [x][y][z] (the layout of vloc_r),
+ *              accumulated into (zero it for a fresh density; call once per
+ *              k-point to sum over k).  The bands are summed in band order
+ *              within each grid point and nothing is summed atomically, so
+ *              the result is bitwise reproducible.
+ * Enqueued on the handle's stream; returns after the work is queued and the
+ * occupations are copied.  Errors: ERR_ARG (k, nb, NULL or host X / rho,
+ * non-finite f), ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED.
+ */
+int lobpcg_density(lobpcg_ctx *ctx, int k, const void *X, int nb, const double *f, double *rho, int precision);
+
+/*
  * Allocation-free Y = (T + V_loc) X for nb bands of k-point k.  The paper has
  * no counterpart: this entry point exists for callers that cannot allocate
  * device memory while they run (code inside another framework's memory pool

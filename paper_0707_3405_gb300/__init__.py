@@ -32,6 +32,7 @@ EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_struct_sizes", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
+    "lobpcg_density",
     "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz_df32", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
     "lobpcg_k_set_gemm_mode", "lobpcg_k_set_spin_limit", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
@@ -110,6 +111,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_struct_sizes": (i, [ctypes.POINTER(ctypes.c_int64)] * 3),
         "lobpcg_launch_count": (ctypes.c_longlong, []),
         "lobpcg_apply_local_noalloc": (i, [vp, i, vp, vp, i, i]),
+        "lobpcg_density": (i, [vp, i, vp, i, vp, vp, i]),
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
         "lobpcg_k_gram_lower": (i, [i, i, i, vp, i, vp, i, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
@@ -309,6 +311,27 @@ class Solver:
         if rc < 0:
             raise LobpcgError(rc, (self._lib.lobpcg_last_error(None) or b"").decode(errors="replace"))
         return Y
+
+    def density(self, k: int, X, f, rho=None, df32: bool = False):
+        """rho += sum_b f_b |psi_b(r)|^2 on the N^3 grid ([x][y][z], float64 CUDA tensor,
+        created zero when None) for the (nb, npw_k) CUDA block X; complex128 runs FP64
+        transforms (double-FP32 with df32=True), complex64 FP32 ones.  Returns rho."""
+        import torch
+        if X.dtype not in (torch.complex128, torch.complex64):
+            raise TypeError("X must be complex64 or complex128")
+        if X.dim() != 2 or not X.is_contiguous() or (X.shape[0] and X.shape[1] != self.npw(k)):
+            raise ValueError("X must be a contiguous (nb, npw_k) block")
+        fh = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1))
+        if fh.shape[0] != X.shape[0]:
+            raise ValueError("one occupation per band is needed")
+        if rho is None:
+            rho = torch.zeros((self.N, self.N, self.N), dtype=torch.float64, device=X.device)
+        if rho.dtype != torch.float64 or tuple(rho.shape) != (self.N,) * 3 or not rho.is_contiguous():
+            raise ValueError("rho must be a contiguous float64 (N, N, N) tensor")
+        prec = C64 if X.dtype == torch.complex64 else (C128_DF32 if df32 else C128)
+        _check(self._lib.lobpcg_density(self.handle, k, _ptr(X), int(X.shape[0]), fh.ctypes.data, _ptr(rho), prec),
+               self.handle)
+        return rho
 
     def solve(self, X, nbands: int | None = None) -> SolveResult:
         """Lowest eigenpairs; ``X`` is a list (one per k-point) of (M, npw_k)

@@ -175,6 +175,7 @@ struct Lane {
     GemmWork gw;
     EigWork ew;
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
+    DevBuf occ;  // occupations of a density call (FP64, then FP32)
     DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32, E32;
     // CUDA graphs of the FP32 H application on fixed buffers (options.use_graph), keyed by
     // (k, X, Y, nb); a graph is only replayed while the scratch it recorded is still in place
@@ -221,7 +222,7 @@ struct Lane {
         DevBuf *bufs[] = {&T2, &nlB, &stageX, &stageY, &Zb[0], &Zb[1], &HZb[0], &HZb[1], &Z32, &HZ32, &HXall,
                           &Tmp, &Gram, &Gram2, &Cbuf, &dtheta, &dres, &dwork, &Gc, &gw.part, &ew.buf, &ew.ibuf,
                           &ew.gw.part, &X32all, &HX32all, &Q32[0], &Q32[1], &HQ32[0], &HQ32[1], &D32, &Small32,
-                          &Xext, &T32, &E32};
+                          &Xext, &T32, &E32, &occ, &gw.oz_a, &gw.oz_e, &gw.oz_p};
         clear_graphs();
         for (DevBuf *b : bufs) a.release(*b);
         a.release(HXr);
@@ -1407,6 +1408,50 @@ int lobpcg_apply_H(lobpcg_ctx *ctx, int k, const void *X, void *Y, int nb, int p
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
     set_gemm_mode(ctx->opt.gemm_split);
     return ret(ctx, apply_impl(ctx, k, X, Y, nb, precision));
+}
+
+static int density_impl(lobpcg_ctx *c, int k, const void *X, int nb, const double *f, double *rho, int precision) {
+    if (k < 0 || k >= c->nk) return fail(LOBPCG_ERR_ARG, "k out of range");
+    if (nb < 0) return fail(LOBPCG_ERR_ARG, "nb must be >= 0");
+    if (nb == 0) return LOBPCG_OK;
+    if (!X || !f || !rho) return fail(LOBPCG_ERR_ARG, "X, f and rho must not be NULL");
+    if (precision != LOBPCG_C128 && precision != LOBPCG_C64 && precision != LOBPCG_C128_DF32)
+        return fail(LOBPCG_ERR_ARG, "unknown precision");
+    for (int b = 0; b < nb; ++b)
+        if (!std::isfinite(f[b])) return fail(LOBPCG_ERR_ARG, "f has non-finite values");
+    if (!is_device_ptr(X) || !is_device_ptr(rho)) return fail(LOBPCG_ERR_ARG, "X and rho must be device pointers");
+    KPoint &K = c->kp[k];
+    const FFTGeom &g = K.geom;
+    Lane &L = *c->lanes[0];
+    const bool f64 = precision != LOBPCG_C64;
+    const size_t cb = f64 ? sizeof(z64) : sizeof(c32);
+    const size_t per_band = cb * (size_t)g.Px * g.N * g.N;
+    int nbatch = (int)std::max<size_t>(1, c->fft_budget / per_band);
+    nbatch = std::min(std::min(nbatch, nb), 65535);
+    LG_TRY(c->alloc.ensure(L.T2, per_band * nbatch));
+    LG_TRY(c->alloc.ensure(L.occ, (sizeof(double) + sizeof(float)) * (size_t)nb));
+    std::vector<float> f32(f, f + nb);
+    double *fd = static_cast<double *>(L.occ.p);
+    float *ff = reinterpret_cast<float *>(fd + nb);
+    LG_CUDA_TRY(cudaMemcpyAsync(fd, f, sizeof(double) * nb, cudaMemcpyHostToDevice, c->stream));
+    LG_CUDA_TRY(cudaMemcpyAsync(ff, f32.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, c->stream));
+    const double scale = 1.0 / (c->cell.a * c->cell.a * c->cell.a);   // psi = Omega^-1/2 sum c(G) e^{i(k+G).r}
+    int rc;
+    if (f64)
+        rc = fft_density<double>(g, c->plan, static_cast<const z64 *>(X), K.npw, nb, c->tw64, fd, ff, scale, rho,
+                                 reinterpret_cast<z64 *>(L.T2.p), nbatch, c->stream, precision == LOBPCG_C128_DF32);
+    else
+        rc = fft_density<float>(g, c->plan, static_cast<const c32 *>(X), K.npw, nb, c->tw32, fd, ff, scale, rho,
+                                reinterpret_cast<c32 *>(L.T2.p), nbatch, c->stream, false);
+    LG_TRY(rc);
+    // the host copy of f32 must outlive its transfer
+    LG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return LOBPCG_OK;
+}
+
+int lobpcg_density(lobpcg_ctx *ctx, int k, const void *X, int nb, const double *f, double *rho, int precision) {
+    if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
+    return ret(ctx, density_impl(ctx, k, X, nb, f, rho, precision));
 }
 
 // Concurrent k-point lanes of one solve (k-points are independent, Sec. 5.2).

@@ -194,6 +194,16 @@ int fft_reg_prepare();                        // twiddle constants on the curren
 size_t fft_reg_smem_need(const FFTGeom &g);
 int fft_reg_apply(const FFTGeom &g, const c32 *X, int ldx, c32 *Y, int ldy, int nb, const float *kin,
                   const float *vt, c32 *T2, int nbatch, cudaStream_t s);
+// Density rho[x][y][z] += scale sum_b f_b |psi_b(r)|^2 of nb bands (Sec. 2.1, first step of the SC
+// loop) by pass A and an inverse x-transform: FP64 (df = false) or double-FP32 (df) passes for
+// complex128, the FP32 register passes (f32: the occupations in FP32) for complex64.  T2: scratch
+// as for fft_vloc_apply; rho (device, N^3 FP64) is accumulated into.
+template <typename R>
+int fft_density(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, int nb, const cx<R> *tw,
+                const double *f, const float *f32, double scale, double *rho, cx<R> *T2, int nbatch, cudaStream_t s,
+                bool df);
+int fft_reg_density(const FFTGeom &g, const c32 *X, int ldx, int nb, const float *f, double scale, double *rho,
+                    c32 *T2, int nbatch, cudaStream_t s);
 // Algorithmic floating-point operations of the three passes for one band
 // (5 n log2 n per length-n complex line FFT, plus the V and T multiplies).
 double fft_flops_per_band(const FFTGeom &g);

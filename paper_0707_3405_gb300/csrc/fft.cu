@@ -349,6 +349,53 @@ k_pass_c(const cx<CT> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx
     }
 }
 
+// Density pass (after pass A, Sec. 2.1 first step of the SC loop, by the same FFT as the local
+// potential, Sec. 2.2 item iii): per (y chunk, z) block, for the batch's bands in band order,
+// inverse x-FFT of the zero-padded lines and acc(x, y, z) += f_b |psi_b|^2 in shared memory; the
+// block then adds scale * acc to rho[x][y][z].  No atomics: every grid point belongs to one block.
+template <typename R, typename CT = R>
+__global__ void __launch_bounds__(kThreads)
+k_pass_d(const cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const cx<R> *__restrict__ twg, int yc,
+         int nbb, const double *__restrict__ f, double scale, double *__restrict__ rho) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = plan.N;
+    cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
+    cx<CT> *L = tw + N;
+    const int lsL = N + 1;
+    CT *acc = reinterpret_cast<CT *>(L + (size_t)yc * lsL);
+    const int y0 = blockIdx.x * yc, z = blockIdx.y;
+    const int ny = min(yc, N - y0);
+    const cx<CT> zero = mkc<CT>(0, 0);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = to_ct<CT>(twg[i]);
+    for (int i = threadIdx.x; i < ny * N; i += blockDim.x) acc[i] = CT(0);
+    const size_t NN = (size_t)N * N;
+    for (int b = 0; b < nbb; ++b) {
+        for (int i = threadIdx.x; i < ny * lsL; i += blockDim.x) L[i] = zero;
+        __syncthreads();
+        const cx<CT> *base = T2 + (size_t)b * Px * NN + (size_t)z * N + y0;
+        for (int i = threadIdx.x; i < Px * ny; i += blockDim.x) {
+            const int px = i / ny, yy = i - px * ny;
+            int ix = nx0m + px;
+            if (ix >= N) ix -= N;
+            L[yy * lsL + ix] = base[(size_t)px * NN + yy];
+        }
+        __syncthreads();
+        fft_lines<CT>(L, ny, lsL, 1, plan, tw, 1);
+        const CT fb = CT(f[b]);
+        for (int i = threadIdx.x; i < ny * N; i += blockDim.x) {
+            const int ix = i / ny, yy = i - ix * ny;
+            const cx<CT> v = L[yy * lsL + ix];
+            acc[yy * N + ix] += fb * (v.x * v.x + v.y * v.y);
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ny * N; i += blockDim.x) {
+        const int ix = i / ny, yy = i - ix * ny;
+        double *dst = rho + ((size_t)ix * N + y0 + yy) * N + z;
+        *dst += scale * (double)acc[yy * N + ix];
+    }
+}
+
 template <typename R>
 size_t smem_ac(const FFTGeom &g, int zc) {
     return sizeof(cx<R>) * ((size_t)g.N + (size_t)g.Py * g.N + (size_t)zc * (g.N + 1));
@@ -434,7 +481,63 @@ int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, c
     return LOBPCG_OK;
 }
 
+// rho += scale sum_b f_b |psi_b|^2 over batches of bands: pass A then the density pass.
+template <typename R, typename CT>
+int density_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, int nb, const cx<R> *tw,
+                   const double *f, double scale, double *rho, cx<CT> *T2, int nbatch, cudaStream_t s) {
+    const int N = g.N;
+    const int zc = pick_zc<R>(g);
+    if (zc == 0) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT grid too large for shared memory");
+    const size_t sm_ac = smem_ac<R>(g, zc);
+    const int yc = 16;
+    const size_t sm_d = sizeof(cx<CT>) * ((size_t)N + (size_t)yc * (N + 1)) + sizeof(CT) * (size_t)yc * N;
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load()) {
+        const int lim = max_dyn_smem();
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_a<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_d<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        attr_set.store(true);
+    }
+    if (sm_d > (size_t)max_dyn_smem()) return fail(LOBPCG_ERR_UNSUPPORTED, "density pass exceeds shared memory");
+    const int ny0m = ((g.ny0 % N) + N) % N;
+    const int nx0m = ((g.nx0 % N) + N) % N;
+    for (int b0 = 0; b0 < nb; b0 += nbatch) {
+        const int nbb = std::min(nbatch, nb - b0);
+        k_pass_a<R, CT><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(X + (size_t)b0 * ldx, ldx, T2, plan, g.Px, g.Py,
+                                                             ny0m, g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
+        LG_TRY(check_launch("density: fft pass A"));
+        k_pass_d<R, CT><<<dim3((N + yc - 1) / yc, N), kThreads, sm_d, s>>>(T2, plan, g.Px, nx0m, tw, yc, nbb,
+                                                                       f + b0, scale, rho);
+        LG_TRY(check_launch("density: x-lines and |psi|^2"));
+    }
+    return LOBPCG_OK;
+}
+
 }  // namespace
+
+template <typename R>
+int fft_density(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, int nb, const cx<R> *tw,
+                const double *f, const float *f32, double scale, double *rho, cx<R> *T2, int nbatch, cudaStream_t s,
+                bool df) {
+    if (nb <= 0) return LOBPCG_OK;
+    if constexpr (std::is_same<R, float>::value) {
+        if (fft_reg_supported(g.N)) return fft_reg_density(g, X, ldx, nb, f32, scale, rho, T2, nbatch, s);
+    } else {
+        if (df) {
+            FFTPlan p4;
+            if (!make_fft_plan(g.N, p4, false)) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plan");
+            return density_passes<R, df64>(g, p4, X, ldx, nb, tw, f, scale, rho, reinterpret_cast<cx<df64> *>(T2),
+                                           nbatch, s);
+        }
+    }
+    (void)f32;
+    return density_passes<R, R>(g, plan, X, ldx, nb, tw, f, scale, rho, T2, nbatch, s);
+}
+
+template int fft_density<float>(const FFTGeom &, const FFTPlan &, const c32 *, int, int, const c32 *, const double *,
+                                const float *, double, double *, c32 *, int, cudaStream_t, bool);
+template int fft_density<double>(const FFTGeom &, const FFTPlan &, const z64 *, int, int, const z64 *,
+                                 const double *, const float *, double, double *, z64 *, int, cudaStream_t, bool);
 
 template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,

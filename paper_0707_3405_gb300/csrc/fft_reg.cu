@@ -338,6 +338,53 @@ k_rb(C *__restrict__ T2, int Px, int nx0m, const float *__restrict__ vr) {
     }
 }
 
+// ------------------------------------------------------------- density pass
+// After pass A: one warp per (y, chunk of 32/T consecutive z), looping over the batch's bands in
+// band order: inverse x-FFT of the Px occupied planes (zero-padded to N), acc(x) += f_b |psi_b|^2
+// (FP32, in the warp's slice of shared memory), then rho[x][y][z] += scale acc (FP64).  Every
+// grid point belongs to one lane: no atomics, a fixed summation order.
+template <int N>
+__global__ void __launch_bounds__(32 * kWarps, RP<N>::MINB)
+k_rd(const C *__restrict__ T2, int Px, int nx0m, int nbb, const float *__restrict__ f, double scale,
+     double *__restrict__ rho) {
+    constexpr int T = RP<N>::T, E = N / T, BK = E / T, LPW = 32 / T;
+    constexpr int NZC = (N + LPW - 1) / LPW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float *acc = reinterpret_cast<float *>(smem_raw) + (size_t)wid * E * 32;   // [e][lane]
+    const int w = blockIdx.x * kWarps + wid;
+    const int y = w / NZC, zc = w - y * NZC;
+    if (y >= N) return;
+    const int l = lane / T, t = lane - l * T;
+    const int z = zc * LPW + l;
+    const bool ok = z < N;
+    const size_t NN = (size_t)N * N;
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e * 32 + lane] = 0.f;
+    for (int b = 0; b < nbb; ++b) {
+        const C *base = T2 + (size_t)b * Px * NN + (size_t)y * N + z;
+        C v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int px = t + T * e - nx0m;
+            px += (px < 0) ? N : 0;
+            v[e] = (ok && px < Px) ? base[(size_t)px * NN] : mkc<float>(0.f, 0.f);
+        }
+        s2b<N, true>(v, t);
+        const float fb = f[b];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e * 32 + lane] = fmaf(fb, v[e].x * v[e].x + v[e].y * v[e].y, acc[e * 32 + lane]);
+    }
+    if (!ok) return;
+#pragma unroll
+    for (int k2 = 0; k2 < T; ++k2)
+#pragma unroll
+        for (int i = 0; i < BK; ++i) {
+            const int x = t * BK + i + E * k2;
+            rho[((size_t)x * N + y) * N + z] += scale * (double)acc[(i + BK * k2) * 32 + lane];
+        }
+}
+
 // ------------------------------------------------------------- pass A
 // One CTA per (band, x-plane): scatter the plane's sphere coefficients into
 // the Py x N tile, inverse z-FFT of the occupied rows, inverse y-FFT of every
@@ -517,6 +564,43 @@ int run_reg(const FFTGeom &g, const C *X, int ldx, C *Y, int ldy, int nb, const 
     return LOBPCG_OK;
 }
 
+template <int N>
+int run_reg_density(const FFTGeom &g, const C *X, int ldx, int nb, const float *f, double scale, double *rho, C *T2,
+                    int nbatch, cudaStream_t s) {
+    constexpr int LPW = 32 / RP<N>::T, E = N / RP<N>::T;
+    constexpr int NZC = (N + LPW - 1) / LPW;
+    const size_t sm = tile_bytes(N, g.Py);
+    const size_t smd = sizeof(float) * (size_t)E * 32 * kWarps;
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        int dev = 0, smem_max = 0;
+        LG_CUDA_TRY(cudaGetDevice(&dev));
+        LG_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (sm > (size_t)smem_max || smd > (size_t)smem_max)
+            return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plane tile exceeds shared memory");
+        cudaFuncAttributes fa, fd;
+        LG_CUDA_TRY(cudaFuncGetAttributes(&fa, k_ra<N>));
+        LG_CUDA_TRY(cudaFuncGetAttributes(&fd, k_rd<N>));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_ra<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_max - (int)fa.sharedSizeBytes));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_rd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_max - (int)fd.sharedSizeBytes));
+        attr.store(true);
+    }
+    const int ny0m = ((g.ny0 % N) + N) % N;
+    const int nx0m = ((g.nx0 % N) + N) % N;
+    const int nwb = N * NZC;
+    for (int b0 = 0; b0 < nb; b0 += nbatch) {
+        const int nbb = std::min(nbatch, nb - b0);
+        k_ra<N><<<dim3(g.Px, nbb), 32 * kWarps, sm, s>>>(X + (size_t)b0 * ldx, ldx, T2, g.Px, g.Py, ny0m,
+                                                         g.plane_begin, g.plane_yrange, g.gmap);
+        LG_TRY(check_launch("density: fft pass A (registers)"));
+        k_rd<N><<<(nwb + kWarps - 1) / kWarps, 32 * kWarps, smd, s>>>(T2, g.Px, nx0m, nbb, f + b0, scale, rho);
+        LG_TRY(check_launch("density: x-lines and |psi|^2 (registers)"));
+    }
+    return LOBPCG_OK;
+}
+
 std::mutex g_tw_mu;
 bool g_tw_ready[kMaxDevices] = {false};
 
@@ -553,6 +637,20 @@ int fft_reg_apply(const FFTGeom &g, const C *X, int ldx, C *Y, int ldy, int nb, 
     switch (g.N) {
 #define LG_REG_CASE(n) \
     case n: return run_reg<n>(g, X, ldx, Y, ldy, nb, kin, vr, T2, nbatch, s);
+        LG_REG_CASE(8) LG_REG_CASE(12) LG_REG_CASE(16) LG_REG_CASE(20) LG_REG_CASE(24) LG_REG_CASE(36)
+        LG_REG_CASE(48) LG_REG_CASE(64) LG_REG_CASE(72) LG_REG_CASE(96) LG_REG_CASE(120) LG_REG_CASE(128)
+        LG_REG_CASE(160)
+#undef LG_REG_CASE
+        default: return fail(LOBPCG_ERR_UNSUPPORTED, "no register FFT for this grid");
+    }
+}
+
+int fft_reg_density(const FFTGeom &g, const C *X, int ldx, int nb, const float *f, double scale, double *rho, C *T2,
+                    int nbatch, cudaStream_t s) {
+    if (nb <= 0) return LOBPCG_OK;
+    switch (g.N) {
+#define LG_REG_CASE(n) \
+    case n: return run_reg_density<n>(g, X, ldx, nb, f, scale, rho, T2, nbatch, s);
         LG_REG_CASE(8) LG_REG_CASE(12) LG_REG_CASE(16) LG_REG_CASE(20) LG_REG_CASE(24) LG_REG_CASE(36)
         LG_REG_CASE(48) LG_REG_CASE(64) LG_REG_CASE(72) LG_REG_CASE(96) LG_REG_CASE(120) LG_REG_CASE(128)
         LG_REG_CASE(160)
