@@ -307,6 +307,23 @@ int lobpcg_apply_local_noalloc(lobpcg_ctx *ctx, int k, const void *X, void *Y, i
 int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid,
                  lobpcg_stats *stats);
 
+/*
+ * The same eigenpairs by band-by-band preconditioned conjugate gradient, the
+ * method Sec. 3.3 compares LOBPCG with (Teter, Payne and Allan 1989; the
+ * iterative-diagonalisation form of Bylander et al. 1990): every band in
+ * order, kept orthogonal to the bands before it, takes options.nline
+ * iterations of steepest descent preconditioned by the Teter ratio (the
+ * preconditioner of lobpcg_solve), Fletcher-Reeves conjugation and an exact
+ * line minimisation of the Rayleigh quotient on span[x, d]; each sweep is
+ * closed by the all-band Rayleigh-Ritz step and residual test of
+ * lobpcg_solve.  Same arguments, ownership, buffer bands and results as
+ * lobpcg_solve; options.precision = LOBPCG_FP64 runs FP64 throughout,
+ * LOBPCG_MIXED runs the H applications and GEMMs in the FP64-class engines
+ * (options.fp64_gemm).  block_size only sets the buffer-band rounding.
+ */
+int lobpcg_solve_pcg(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid,
+                     lobpcg_stats *stats);
+
 /* Sizes in bytes of lobpcg_cell, lobpcg_options and lobpcg_stats as this library
  * was compiled, so that a binding can check its own layouts against them (any
  * pointer may be NULL).  Always LOBPCG_OK; needs no device. */

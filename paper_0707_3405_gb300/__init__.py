@@ -32,7 +32,7 @@ EXPORTED = (
     "lobpcg_default_options", "lobpcg_create", "lobpcg_set_projectors", "lobpcg_set_stream",
     "lobpcg_set_options", "lobpcg_npw", "lobpcg_gvectors", "lobpcg_apply_H", "lobpcg_solve",
     "lobpcg_last_error", "lobpcg_destroy", "lobpcg_struct_sizes", "lobpcg_launch_count", "lobpcg_apply_local_noalloc",
-    "lobpcg_density",
+    "lobpcg_density", "lobpcg_solve_pcg",
     "lobpcg_k_gemm_cn", "lobpcg_k_gram_lower", "lobpcg_k_gemm_nn", "lobpcg_k_rayleigh_ritz", "lobpcg_k_rayleigh_ritz_df32", "lobpcg_k_rayleigh_ritz32", "lobpcg_k_heev",
     "lobpcg_k_set_gemm_mode", "lobpcg_k_set_spin_limit", "lobpcg_k_check_timeouts", "lobpcg_k_last_error",
 )
@@ -112,6 +112,7 @@ def load() -> ctypes.CDLL:
         "lobpcg_launch_count": (ctypes.c_longlong, []),
         "lobpcg_apply_local_noalloc": (i, [vp, i, vp, vp, i, i]),
         "lobpcg_density": (i, [vp, i, vp, i, vp, vp, i]),
+        "lobpcg_solve_pcg": (i, [vp, i, vp, vp, vp, ctypes.POINTER(Stats)]),
         "lobpcg_k_gemm_cn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]),
         "lobpcg_k_gram_lower": (i, [i, i, i, vp, i, vp, i, vp, i, vp]),
         "lobpcg_k_gemm_nn": (i, [i, i, i, i, d, vp, i, vp, i, d, vp, i, vp, i, vp]),
@@ -333,10 +334,11 @@ class Solver:
                self.handle)
         return rho
 
-    def solve(self, X, nbands: int | None = None) -> SolveResult:
+    def solve(self, X, nbands: int | None = None, method: str = "lobpcg") -> SolveResult:
         """Lowest eigenpairs; ``X`` is a list (one per k-point) of (M, npw_k)
         complex128 CUDA tensors holding start vectors, overwritten by the
-        eigenvectors."""
+        eigenvectors.  method = "lobpcg" (block LOBPCG, Algorithm 1) or "pcg"
+        (band-by-band PCG, the comparison method of Sec. 3.3)."""
         if not isinstance(X, (list, tuple)):
             X = [X]
         if len(X) != self.nk:
@@ -346,8 +348,8 @@ class Solver:
         eig = np.zeros((self.nk, M))
         res = np.zeros((self.nk, M))
         st = Stats()
-        rc = _check(self._lib.lobpcg_solve(self.handle, M, ptrs, eig.ctypes.data, res.ctypes.data,
-                                           ctypes.byref(st)), self.handle)
+        fn = {"lobpcg": self._lib.lobpcg_solve, "pcg": self._lib.lobpcg_solve_pcg}[method]
+        rc = _check(fn(self.handle, M, ptrs, eig.ctypes.data, res.ctypes.data, ctypes.byref(st)), self.handle)
         return SolveResult(eig, res, rc, st.as_dict())
 
     def close(self):

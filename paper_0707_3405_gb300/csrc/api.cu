@@ -176,6 +176,7 @@ struct Lane {
     EigWork ew;
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
     DevBuf occ;  // occupations of a density call (FP64, then FP32)
+    DevBuf pcgv, pcgs;  // PCG: seven band vectors, reduction and scalar scratch
     DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32, E32;
     // CUDA graphs of the FP32 H application on fixed buffers (options.use_graph), keyed by
     // (k, X, Y, nb); a graph is only replayed while the scratch it recorded is still in place
@@ -222,7 +223,7 @@ struct Lane {
         DevBuf *bufs[] = {&T2, &nlB, &stageX, &stageY, &Zb[0], &Zb[1], &HZb[0], &HZb[1], &Z32, &HZ32, &HXall,
                           &Tmp, &Gram, &Gram2, &Cbuf, &dtheta, &dres, &dwork, &Gc, &gw.part, &ew.buf, &ew.ibuf,
                           &ew.gw.part, &X32all, &HX32all, &Q32[0], &Q32[1], &HQ32[0], &HQ32[1], &D32, &Small32,
-                          &Xext, &T32, &E32, &occ, &gw.oz_a, &gw.oz_e, &gw.oz_p};
+                          &Xext, &T32, &E32, &occ, &gw.oz_a, &gw.oz_e, &gw.oz_p, &pcgv, &pcgs};
         clear_graphs();
         for (DevBuf *b : bufs) a.release(*b);
         a.release(HXr);
@@ -1167,6 +1168,94 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     return maxr <= c->opt.tol ? LOBPCG_OK : LOBPCG_NOT_CONVERGED;
 }
 
+// Band-by-band PCG (the method Sec. 3.3 compares LOBPCG with) on one k-point for M bands of
+// which the first Mreq must converge: every band in order, kept orthogonal to the bands before
+// it, takes nline PCG iterations (pcg.cu); each sweep is closed by the same all-band
+// Rayleigh-Ritz step and FP64 residual test as the LOBPCG sweeps.  FP64 schedule: FP64
+// everywhere; MIXED: the H applications and GEMMs in the FP64-class engines (double-FP32 FFT
+// passes, tensor-core digit-slice GEMMs); the band steps themselves are FP64.
+int solve_pcg_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h,
+                int &sweeps_done, Prof *prof, SolveCounters &cnt) {
+    Solver sv;
+    sv.c = c;
+    sv.L = &L;
+    sv.prof = prof;
+    sv.k = k;
+    sv.npw = c->kp[k].npw;
+    sv.M = M;
+    sv.m = c->opt.block_size;
+    sv.nblk = M / sv.m;
+    sv.mixed = false;
+    sv.df = c->opt.fp64_gemm >= 2 || (c->opt.fp64_gemm == 0 && c->opt.precision == LOBPCG_MIXED);
+    L.ew.df = sv.df;
+    L.gw.oz = c->opt.fp64_gemm == 3 || (c->opt.fp64_gemm == 0 && c->opt.precision == LOBPCG_MIXED);
+    sv.X = X;
+    sv.s = L.stream;
+    sv.drop_tol = 1e-12;
+    sv.drop_tol32 = 1e-3;
+    const int npw = sv.npw;
+    int rc = 0;
+    sv.HX = carve<z64>(c, L.HXall, (size_t)npw * M, rc); LG_TRY(rc);
+    sv.Tmp = carve<z64>(c, L.Tmp, (size_t)npw * M, rc); LG_TRY(rc);
+    sv.S = carve<z64>(c, L.Gram, (size_t)M * M, rc); LG_TRY(rc);
+    sv.A = carve<z64>(c, L.Gram2, (size_t)M * M, rc); LG_TRY(rc);
+    sv.C = carve<z64>(c, L.Cbuf, (size_t)M * M, rc); LG_TRY(rc);
+    sv.G = carve<z64>(c, L.Gc, (size_t)M, rc); LG_TRY(rc);
+    sv.theta = carve<double>(c, L.dtheta, M, rc); LG_TRY(rc);
+    sv.res = carve<double>(c, L.dres, M, rc); LG_TRY(rc);
+    double *w = carve<double>(c, L.dwork, 4 * (size_t)M + 64 + colsum_part_elems(M), rc); LG_TRY(rc);
+    sv.work = w;
+    sv.ndrop = reinterpret_cast<int *>(w + 4 * (size_t)M);
+    sv.part = w + 4 * (size_t)M + 64;
+    z64 *vv = carve<z64>(c, L.pcgv, 6 * (size_t)npw, rc); LG_TRY(rc);
+    double *ps = carve<double>(c, L.pcgs, pcg_scratch_doubles(npw, M), rc); LG_TRY(rc);
+    PcgBand pb;
+    pb.npw = npw;
+    pb.s = sv.s;
+    pb.kin = c->kp[k].kin64;
+    pb.Y = X;
+    pb.ldy = npw;
+    pb.xi = vv;
+    pb.eta = vv + npw;
+    pb.d = vv + 2 * (size_t)npw;
+    pb.dh = vv + 3 * (size_t)npw;
+    pb.hd = vv + 4 * (size_t)npw;
+    pcg_carve(pb, ps, npw, M);
+    sweeps_done = 0;
+    double maxr = 0.0;
+    for (int sw = 0; sw < c->opt.max_sweeps; ++sw) {
+        for (int n = 0; n < M; ++n) {
+            pb.j = n;
+            pb.x = sv.col(X, n);
+            pb.hx = sv.col(sv.HX, n);
+            LG_TRY(pb.prepare_start());
+            LG_TRY(sv.applyH64(pb.x, pb.hx, 1));
+            LG_TRY(pb.after_hx());
+            for (int it = 0; it < c->opt.nline; ++it) {
+                LG_TRY(pb.direction(it == 0));
+                LG_TRY(sv.applyH64(pb.dh, pb.hd, 1));
+                LG_TRY(pb.step());
+                ++sv.iterations;
+            }
+        }
+        sv.early = false;
+        LG_TRY(sv.final_rr(eig_h, res_h));
+        if (prof) prof->collect();
+        ++sweeps_done;
+        maxr = 0.0;
+        bool finite = true;
+        for (int i = 0; i < Mreq; ++i) {
+            finite = finite && std::isfinite(res_h[i]) && std::isfinite(eig_h[i]);
+            maxr = std::max(maxr, res_h[i]);
+        }
+        if (!finite) return fail(LOBPCG_ERR_BREAKDOWN, "non-finite Ritz value or residual");
+        if (maxr <= c->opt.tol) break;
+    }
+    cnt.a64 += sv.applies64;
+    cnt.iters += sv.iterations;
+    return maxr <= c->opt.tol ? LOBPCG_OK : LOBPCG_NOT_CONVERGED;
+}
+
 int validate_options(const lobpcg_options &o) {
     if (o.block_size < 1) return fail(LOBPCG_ERR_ARG, "block_size must be >= 1");
     if (o.nline < 1) return fail(LOBPCG_ERR_ARG, "nline must be >= 1");
@@ -1515,7 +1604,11 @@ static int autotune_k(lobpcg_ctx *c, Lane &L, int k, bool df, int nb) {
 
 // One k-point on one lane: stage host vectors, add buffer bands, solve, copy back.
 static int solve_one(lobpcg_ctx *c, Lane &L, int k, int M, int nbuf, void *Xk, double *eig_k, double *res_k,
-                     int &sw, Prof *prof, SolveCounters &cnt) {
+                     int &sw, Prof *prof, SolveCounters &cnt, bool pcg) {
+    auto run = [&](int MM, z64 *XX, double *ee, double *rr) {
+        return pcg ? solve_pcg_k(c, L, k, MM, M, XX, ee, rr, sw, prof, cnt)
+                   : solve_k(c, L, k, MM, M, XX, ee, rr, sw, prof, cnt);
+    };
     const bool host = !is_device_ptr(Xk);
     const int npw = c->kp[k].npw;
     const size_t bytes = sizeof(z64) * (size_t)npw * M;
@@ -1533,14 +1626,14 @@ static int solve_one(lobpcg_ctx *c, Lane &L, int k, int M, int nbuf, void *Xk, d
         LG_CUDA_TRY(cudaMemcpyAsync(Xe, Xd, bytes, cudaMemcpyDeviceToDevice, L.stream));
         LG_TRY(fill_random(npw, nbuf, Xe + (size_t)npw * M, npw, 0x51ED270Bu + 977u * (unsigned)k, L.stream));
         std::vector<double> ebuf(2 * (size_t)(M + nbuf));
-        rc = solve_k(c, L, k, M + nbuf, M, Xe, ebuf.data(), ebuf.data() + (M + nbuf), sw, prof, cnt);
+        rc = run(M + nbuf, Xe, ebuf.data(), ebuf.data() + (M + nbuf));
         if (rc < 0) return rc;
         LG_CUDA_TRY(cudaMemcpyAsync(Xd, Xe, bytes, cudaMemcpyDeviceToDevice, L.stream));
         LG_CUDA_TRY(cudaStreamSynchronize(L.stream));
         std::memcpy(eig_k, ebuf.data(), sizeof(double) * M);
         std::memcpy(res_k, ebuf.data() + (M + nbuf), sizeof(double) * M);
     } else {
-        rc = solve_k(c, L, k, M, M, Xd, eig_k, res_k, sw, prof, cnt);
+        rc = run(M, Xd, eig_k, res_k);
         if (rc < 0) return rc;
     }
     if (host) {
@@ -1550,7 +1643,8 @@ static int solve_one(lobpcg_ctx *c, Lane &L, int k, int M, int nbuf, void *Xk, d
     return rc;
 }
 
-static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double *resid, lobpcg_stats *st) {
+static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double *resid, lobpcg_stats *st,
+                      bool pcg = false) {
     if (!X || !eig || !resid) return fail(LOBPCG_ERR_ARG, "X, eig and resid must not be NULL");
     const int m = c->opt.block_size;
     if (M < 1 || M % m) return fail(LOBPCG_ERR_ARG, "nbands must be a positive multiple of block_size");
@@ -1638,7 +1732,7 @@ static int solve_impl(lobpcg_ctx *c, int M, void *const *X, double *eig, double 
         pr.s = c->lanes[l]->stream;
         for (int k = l; k < c->nk; k += nl) {
             const int rc = solve_one(c, *c->lanes[l], k, M, nbuf, X[k], eig + (size_t)k * M, resid + (size_t)k * M,
-                                     sweeps_k[k], pr.on ? &pr : nullptr, cnts[l]);
+                                     sweeps_k[k], pr.on ? &pr : nullptr, cnts[l], pcg);
             if (rc < 0) {
                 lane_rc[l] = rc;
                 lane_err[l] = last_fail();
@@ -1708,6 +1802,12 @@ int lobpcg_solve(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, doubl
     if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
     set_gemm_mode(ctx->opt.gemm_split);
     return ret(ctx, solve_impl(ctx, nbands, X, eig, resid, stats));
+}
+
+int lobpcg_solve_pcg(lobpcg_ctx *ctx, int nbands, void *const *X, double *eig, double *resid, lobpcg_stats *stats) {
+    if (!ctx) return fail(LOBPCG_ERR_ARG, "ctx is NULL");
+    set_gemm_mode(ctx->opt.gemm_split);
+    return ret(ctx, solve_impl(ctx, nbands, X, eig, resid, stats, true));
 }
 
 int lobpcg_struct_sizes(int64_t *cell, int64_t *options, int64_t *stats) {

@@ -296,6 +296,32 @@ int gemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alph
 int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
                 const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s);
 
+// ------------------------------------------------------------------ band-by-band PCG (pcg.cu)
+// Device-side steps of one band of the PCG comparison method: every scalar lives in sc (device),
+// so a band iteration never waits for the host.  Vectors are npw long, FP64; Y (npw x j, ld ldy)
+// holds the orthonormal bands before this one.
+struct PcgBand {
+    int npw = 0, j = 0, ldy = 0;
+    cudaStream_t s = nullptr;
+    const double *kin = nullptr;
+    const z64 *Y = nullptr;
+    z64 *x = nullptr, *hx = nullptr, *xi = nullptr, *eta = nullptr, *d = nullptr, *dh = nullptr, *hd = nullptr;
+    double *part = nullptr, *sc = nullptr;   // reduction partials, scalar block (16 doubles)
+    z64 *gpart = nullptr, *G = nullptr;      // projection partials and coefficients
+    int prepare_start();                     // x off span(Y), normalised
+    int after_hx();                          // eps = <x|Hx>, Ekin(x)
+    int direction(bool first);               // steps 1-5: dh (normalised search direction)
+    int step();                              // step 6 with hd = H dh: line minimum, x and Hx updated
+    int project(z64 *v, const z64 *x);       // v off span(Y) twice, then off x (x may be NULL)
+    int sums(int nq, const z64 *a0, const z64 *b0, const z64 *a1, const z64 *b1, const z64 *a2, const z64 *b2,
+             int mode, int act);
+    int vec(int op, z64 *v, const z64 *a, const z64 *b, z64 *w);
+};
+// Doubles of scratch a PcgBand needs for npw plane waves and up to M earlier bands (part, sc,
+// gpart, G carved from one buffer).
+size_t pcg_scratch_doubles(int npw, int M);
+void pcg_carve(PcgBand &pb, double *base, int npw, int M);   // sets sc, part, gpart, G
+
 // ------------------------------------------------------------------ dense FP64 eigen-solvers
 // Orders the cooperative launches (grid-barrier kernels) of concurrent streams one after
 // another, so that two such grids never compete for residency.
