@@ -845,6 +845,103 @@ k_multisect(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, RT
     if (sub == 0) theta[k] = 0.5 * (lo + hi);
 }
 
+// Double-FP32 Sturm count on pair copies of d and e^2 (shared memory): the same recurrence,
+// its divisions on the FP32 units (one SM sub-partition issues an FP64 instruction for a whole
+// warp in 64 cycles on this GPU, an FP32 one in 1).  About 2^-47 relative per operation: the
+// count is exact for a matrix within a few such roundings of T.
+__device__ __forceinline__ int sturm_count_df(const df64 *__restrict__ d, const df64 *__restrict__ e2, int n, df64 x,
+                                              float pivmin) {
+    int c = 0;
+    df64 q = d[0] - x;
+    if (fabsf(q.hi) < pivmin) q = df64(-pivmin);
+    c += (q.hi < 0.f);
+    for (int i = 1; i < n; ++i) {
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (fabsf(q.hi) < pivmin) q = df64(-pivmin);
+        c += (q.hi < 0.f);
+    }
+    return c;
+}
+
+// Multisection of the FP64-class Rayleigh-Ritz step (same rounds as k_multisect): FP32 rounds
+// narrow the bracket, double-FP32 rounds finish it; the bracket bounds come from FP32 copies of
+// T with a generous pad.  Dynamic shared memory: d, e^2 as pairs, then as floats (24 n bytes).
+__global__ void __launch_bounds__(32)
+k_multisect_df(int n, int m, const double *__restrict__ d, const double *__restrict__ e, double *__restrict__ theta) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    df64 *dd = reinterpret_cast<df64 *>(smraw);
+    df64 *de2 = dd + n;
+    float *ds = reinterpret_cast<float *>(de2 + n);
+    float *e2s = ds + n;
+    const int k = blockIdx.x, sub = threadIdx.x;
+    if (k >= m) return;
+    for (int i = sub; i < n; i += kMsLanes) {
+        dd[i] = df64(d[i]);
+        const df64 ei = (i + 1 < n) ? df64(e[i]) : df64(0.f);
+        de2[i] = ei * ei;
+        ds[i] = dd[i].hi;
+        e2s[i] = de2[i].hi;
+    }
+    __syncwarp();
+    // Gershgorin bracket in FP32, padded well above its rounding
+    float lo_f = FLT_MAX, hi_f = -FLT_MAX, emax2 = 0.f;
+    for (int i = 0; i < n; ++i) {
+        float r = 0.f;
+        if (i > 0) r += sqrtf(e2s[i - 1]);
+        if (i < n - 1) { r += sqrtf(e2s[i]); emax2 = fmaxf(emax2, e2s[i]); }
+        lo_f = fminf(lo_f, ds[i] - r);
+        hi_f = fmaxf(hi_f, ds[i] + r);
+    }
+    const float tn = fmaxf(fabsf(lo_f), fabsf(hi_f));
+    const float piv = FLT_MIN * fmaxf(1.f, fmaxf(emax2, tn * tn));
+    const float gpad = 64.f * FLT_EPSILON * tn * (float)n + 4.f * piv;
+    lo_f -= gpad;
+    hi_f += gpad;
+    const float margin = 32.f * FLT_EPSILON * tn + 4.f * piv;
+    float l32 = lo_f, h32 = hi_f;
+    for (int it = 0; it < 8 && h32 - l32 > 4.f * margin; ++it) {  // warp-uniform
+        const float w = h32 - l32;
+        const float x = l32 + w * (float)(sub + 1) / (float)(kMsLanes + 1);
+        const int c = sturm_count32(ds, e2s, n, x, piv);
+        const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
+        const int T = __popc(mask) - 1;
+        const float xlo = __shfl_sync(0xffffffffu, x, T < 0 ? 0 : T);
+        const float xhi = __shfl_sync(0xffffffffu, x, T < kMsLanes - 1 ? T + 1 : kMsLanes - 1);
+        if (T >= 0) l32 = xlo;
+        if (T < kMsLanes - 1) h32 = xhi;
+    }
+    const df64 lo_g(lo_f), hi_g(hi_f);
+    df64 lo = fmax(lo_g, df64(l32) - df64(margin)), hi = fmin(hi_g, df64(h32) + df64(margin));
+    bool check = true;
+    const float eps_df = 0x1p-45f;
+    for (int it = 0; it < 40; ++it) {
+        const df64 w = hi - lo;
+        if (w.hi <= 2.f * eps_df * fmaxf(fabsf(lo.hi), fabsf(hi.hi)) + 4.f * piv) break;  // warp-uniform
+        df64 x;
+        if (check)  // bracket ends on the end lanes, 30 points between
+            x = (sub == 0) ? lo : (sub == kMsLanes - 1) ? hi : lo + w * df64((float)sub / (float)(kMsLanes - 1));
+        else
+            x = lo + w * df64((float)(sub + 1) / (float)(kMsLanes + 1));
+        const int c = sturm_count_df(dd, de2, n, x, piv);
+        if (check) {
+            check = false;
+            const bool ok = __shfl_sync(0xffffffffu, c, 0) <= k && __shfl_sync(0xffffffffu, c, kMsLanes - 1) > k;
+            if (!ok) {  // the FP32 bracket missed (not expected): restart from Gershgorin
+                lo = lo_g;
+                hi = hi_g;
+                continue;
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, c <= k);
+        const int T = __popc(mask) - 1;
+        const df64 xlo = __shfl_sync(0xffffffffu, x, T < 0 ? 0 : T);
+        const df64 xhi = __shfl_sync(0xffffffffu, x, T < kMsLanes - 1 ? T + 1 : kMsLanes - 1);
+        if (T >= 0) lo = xlo;
+        if (T < kMsLanes - 1) hi = xhi;
+    }
+    if (sub == 0) theta[k] = (double)((lo + hi) * df64(0.5f));
+}
+
 // ------------------------------------------------------------------ eigenvectors (inverse iteration)
 template <typename RT>
 __device__ __forceinline__ RT hash_uniform(unsigned int a, unsigned int b) {
@@ -1171,8 +1268,20 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
         k_tri_last<RT><<<1, 32, 0, s>>>(n, A, lda, dg);
         LG_TRY(check_launch("tridiag last"));
     }
-    k_multisect<RT><<<m, kMsLanes, 0, s>>>(n, m, dg, eg, theta);
-    LG_TRY(check_launch("multisection"));
+    bool ms_done = false;
+    if constexpr (std::is_same<RT, double>::value) {
+        if (w.df) {  // FP64-class path: the fine rounds in double-FP32
+            const size_t smem_ms = 24 * (size_t)n;
+            if (smem_ms > 48 * 1024) LG_TRY(allow_max_dyn_smem((const void *)k_multisect_df));
+            k_multisect_df<<<m, kMsLanes, smem_ms, s>>>(n, m, dg, eg, theta);
+            LG_TRY(check_launch("multisection (double-FP32)"));
+            ms_done = true;
+        }
+    }
+    if (!ms_done) {
+        k_multisect<RT><<<m, kMsLanes, 0, s>>>(n, m, dg, eg, theta);
+        LG_TRY(check_launch("multisection"));
+    }
     const size_t smem_ii = 6 * sizeof(RT) * (size_t)n + (size_t)n;
     if (smem_ii > 48 * 1024)
         LG_TRY(allow_max_dyn_smem((const void *)k_inviter<RT>));
