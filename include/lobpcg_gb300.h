@@ -138,6 +138,16 @@ typedef struct {
                             exact BF16 digit slices (the LOBPCG_C128_TC arithmetic).  The serial
                             recurrences (multisection, inverse iteration, back-transformation) stay
                             FP64. */
+    int    gamma_real;   /* 1: k-points at Gamma (k = 0) are solved in the real-orbital form (the
+                            Gamma-point trick of plane-wave codes; the paper expands complex orbitals,
+                            Sec. 2.1): eigenvectors with c(-G) = conj(c(G)), stored packed on the half
+                            sphere (G = 0 and one of each +-G pair), coefficient matrices real, and H
+                            applied to two real bands at once as one complex band.  Valid when H
+                            commutes with c(G) -> conj(c(-G)): a real local potential and projectors
+                            real in r space up to one phase each (true of the synthetic cells).  The
+                            start vectors are projected onto the real form; the returned vectors are
+                            full-sphere complex128 with the symmetry.  Ignored by lobpcg_solve_pcg and
+                            at other k-points.  0 (default): complex orbitals everywhere. */
 } lobpcg_options;
 
 /* Phases of a solve, for the per-phase timers of lobpcg_stats. */

@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("gemm_split", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tol", ctypes.c_double), ("mem_cap", ctypes.c_longlong),
                 ("timing", ctypes.c_int), ("nbuf", ctypes.c_int), ("mixed_switch", ctypes.c_double),
-                ("mixed_early", ctypes.c_double), ("fp64_gemm", ctypes.c_int)]
+                ("mixed_early", ctypes.c_double), ("fp64_gemm", ctypes.c_int), ("gamma_real", ctypes.c_int)]
 
 
 PHASES = ("fft", "nonlocal", "gram", "constraint", "rr", "update")
@@ -192,7 +192,7 @@ class Solver:
                  block_size: int = 64, nline: int = 4, max_sweeps: int = 100, precision: str = "fp64",
                  tol: float = 1e-8, mem_cap: int = 0, timing: bool = False, nbuf: int = 0,
                  mixed_switch: float | None = None, mixed_early: float | None = None, stream=None,
-                 fp64_gemm: int = 0, use_graph: bool = False, autotune: bool = False):
+                 fp64_gemm: int = 0, use_graph: bool = False, autotune: bool = False, gamma_real: bool = False):
         lib = load()
         self._lib = lib
         self.handle = ctypes.c_void_p()
@@ -204,7 +204,7 @@ class Solver:
         self.nproj = int(E.shape[0])
         self.nk = int(kp.shape[0])
         opt = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
-                            mixed_early, fp64_gemm, use_graph, autotune)
+                            mixed_early, fp64_gemm, use_graph, autotune, gamma_real)
         cell = Cell(a, N, ecut)
         self._stream = stream
         rc = lib.lobpcg_create(ctypes.byref(self.handle), ctypes.byref(cell), self.nk, kp.ctypes.data,
@@ -220,7 +220,8 @@ class Solver:
 
     @staticmethod
     def _options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing=False, nbuf=0,
-                 mixed_switch=None, mixed_early=None, fp64_gemm=0, use_graph=False, autotune=False) -> Options:
+                 mixed_switch=None, mixed_early=None, fp64_gemm=0, use_graph=False, autotune=False,
+                 gamma_real=False) -> Options:
         o = default_options()
         o.block_size, o.nline, o.max_sweeps = block_size, nline, max_sweeps
         o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
@@ -235,13 +236,14 @@ class Solver:
         o.fp64_gemm = fp64_gemm
         o.use_graph = 1 if use_graph else 0
         o.autotune = 1 if autotune else 0
+        o.gamma_real = 1 if gamma_real else 0
         return o
 
     def set_options(self, block_size=64, nline=4, max_sweeps=100, precision="fp64", tol=1e-8, mem_cap=0,
                     timing=False, nbuf=0, mixed_switch=None, mixed_early=None, fp64_gemm=0, use_graph=False,
-                    autotune=False):
+                    autotune=False, gamma_real=False):
         o = self._options(block_size, nline, max_sweeps, precision, tol, mem_cap, timing, nbuf, mixed_switch,
-                          mixed_early, fp64_gemm, use_graph, autotune)
+                          mixed_early, fp64_gemm, use_graph, autotune, gamma_real)
         _check(self._lib.lobpcg_set_options(self.handle, ctypes.byref(o)), self.handle)
 
     def set_stream(self, stream):

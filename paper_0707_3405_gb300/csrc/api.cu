@@ -162,6 +162,11 @@ struct KPoint {
     // FFT scratch budget per band batch (bytes; 0 = the handle default), chosen by the autotuner
     size_t fft_budget32 = 0, fft_budget64 = 0;
     bool tuned = false;
+    // Gamma point: packed half-sphere tables of the real form (see gamma_pack_full)
+    bool gamma = false;
+    int n_half = 0;
+    int *half = nullptr, *mirror = nullptr;
+    double *kin_half64 = nullptr;
 };
 
 // Everything one k-point solve (or one apply_H call) writes: scratch, solver buffers and the
@@ -177,6 +182,7 @@ struct Lane {
     DevBuf Zb[2], HZb[2], Z32, HZ32, HXall, Tmp, Gram, Gram2, Cbuf, dtheta, dres, dwork, Gc;
     DevBuf occ;  // occupations of a density call (FP64, then FP32)
     DevBuf pcgv, pcgs;  // PCG: seven band vectors, reduction and scalar scratch
+    DevBuf rfi, rfo, Xpk;  // Gamma real form: sphere pairs in / out of an H application, packed X
     DevBuf X32all, HX32all, Q32[2], HQ32[2], D32, Small32, Xext, T32, E32;
     // CUDA graphs of the FP32 H application on fixed buffers (options.use_graph), keyed by
     // (k, X, Y, nb); a graph is only replayed while the scratch it recorded is still in place
@@ -223,7 +229,8 @@ struct Lane {
         DevBuf *bufs[] = {&T2, &nlB, &stageX, &stageY, &Zb[0], &Zb[1], &HZb[0], &HZb[1], &Z32, &HZ32, &HXall,
                           &Tmp, &Gram, &Gram2, &Cbuf, &dtheta, &dres, &dwork, &Gc, &gw.part, &ew.buf, &ew.ibuf,
                           &ew.gw.part, &X32all, &HX32all, &Q32[0], &Q32[1], &HQ32[0], &HQ32[1], &D32, &Small32,
-                          &Xext, &T32, &E32, &occ, &gw.oz_a, &gw.oz_e, &gw.oz_p, &pcgv, &pcgs};
+                          &Xext, &T32, &E32, &occ, &gw.oz_a, &gw.oz_e, &gw.oz_p, &pcgv, &pcgs, &rfi, &rfo,
+                          &Xpk};
         clear_graphs();
         for (DevBuf *b : bufs) a.release(*b);
         a.release(HXr);
@@ -349,6 +356,33 @@ int build_basis(lobpcg_ctx *c, KPoint &K) {
     LG_TRY(upload(c, &K.kin32, k32.data(), k32.size()));
     if (fft_smem_need<double>(g) == 0 || fft_smem_need<float>(g) == 0)
         return fail(LOBPCG_ERR_UNSUPPORTED, "FFT grid too large for one SM's shared memory");
+    K.gamma = K.k[0] == 0.0 && K.k[1] == 0.0 && K.k[2] == 0.0;
+    if (K.gamma) {
+        // half set {0} u S+ (S+: n_x > 0, or n_x = 0 and n_y > 0, or n_x = n_y = 0 and n_z > 0),
+        // G = 0 first, then S+ in sphere order; the sphere holds -G with every G
+        std::map<std::tuple<int, int, int>, int> pos;
+        for (int p = 0; p < K.npw; ++p) pos[std::make_tuple(K.miller[3 * p], K.miller[3 * p + 1], K.miller[3 * p + 2])] = p;
+        std::vector<int> hv, mv;
+        std::vector<double> kh;
+        const auto z = pos.find(std::make_tuple(0, 0, 0));
+        if (z == pos.end()) return fail(LOBPCG_ERR_ARG, "Gamma sphere without G = 0");
+        hv.push_back(z->second);
+        mv.push_back(z->second);
+        kh.push_back(kin[z->second]);
+        for (int p = 0; p < K.npw; ++p) {
+            const int a = K.miller[3 * p], b = K.miller[3 * p + 1], d = K.miller[3 * p + 2];
+            if (!(a > 0 || (a == 0 && b > 0) || (a == 0 && b == 0 && d > 0))) continue;
+            const auto q = pos.find(std::make_tuple(-a, -b, -d));
+            if (q == pos.end()) return fail(LOBPCG_ERR_ARG, "Gamma sphere not symmetric under G -> -G");
+            hv.push_back(p);
+            mv.push_back(q->second);
+            kh.push_back(kin[p]);
+        }
+        K.n_half = (int)hv.size();
+        LG_TRY(upload(c, &K.half, hv.data(), hv.size()));
+        LG_TRY(upload(c, &K.mirror, mv.data(), mv.size()));
+        LG_TRY(upload(c, &K.kin_half64, kh.data(), kh.size()));
+    }
     return LOBPCG_OK;
 }
 
@@ -435,6 +469,27 @@ int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y
     return LOBPCG_OK;
 }
 
+// H on packed real-form bands (Gamma point): bands 2i and 2i+1 go through one complex H
+// application as c_a + i c_b and are separated afterwards (see gamma_pack_pairs), so the FFT and
+// KB work is halved.  Zin, Zout: n_half x nb, ld n_half.
+template <typename R>
+int apply_real(lobpcg_ctx *c, Lane &L, int k, const cx<R> *Zin, cx<R> *Zout, int nb, Prof *prof, bool df) {
+    if (nb <= 0) return LOBPCG_OK;
+    KPoint &K = c->kp[k];
+    const int np = (nb + 1) / 2;
+    const size_t bytes = sizeof(cx<R>) * (size_t)K.npw * np;
+    LG_TRY(c->alloc.ensure(L.rfi, bytes));
+    LG_TRY(c->alloc.ensure(L.rfo, bytes));
+    cx<R> *Ci = reinterpret_cast<cx<R> *>(L.rfi.p), *Co = reinterpret_cast<cx<R> *>(L.rfo.p);
+    {
+        PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 2.0 * (double)bytes, false);
+        LG_TRY(gamma_unpack_pairs<R>(K.n_half, nb, Zin, K.n_half, K.half, K.mirror, Ci, K.npw, L.stream));
+    }
+    LG_TRY(apply_H_dev<R>(c, L, k, Ci, K.npw, Co, K.npw, np, prof, df));
+    PhaseScope ps(prof, LOBPCG_PH_UPDATE, 0.0, 2.0 * (double)bytes, false);
+    return gamma_pack_pairs<R>(K.n_half, nb, Co, K.npw, K.half, K.mirror, Zout, K.n_half, L.stream);
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -484,6 +539,8 @@ struct Solver {
     int k, npw, M, m, nblk;
     bool mixed;
     bool df = false;  // FP64-class tall GEMMs in double-FP32 arithmetic
+    bool real = false;  // Gamma real form: packed half-sphere bands, real coefficient matrices
+    const double *kin = nullptr;  // kinetic table of the stored rows (packed in the real form)
     double *part = nullptr;  // scratch of the per-column reductions (colsum_part_elems(nzmax))
     cudaStream_t s;
     z64 *X, *HX;             // all bands, FP64 (X is the caller's buffer)
@@ -534,10 +591,18 @@ struct Solver {
     double cbytes32(double cols) const { return 8.0 * npw * cols; }
 
     int applyH64(const z64 *Xin, z64 *Yout, int nb) {
+        if (real) {
+            applies64 += (nb + 1) / 2;
+            return apply_real<double>(c, *L, k, Xin, Yout, nb, prof, df);
+        }
         applies64 += nb;
         return apply_H_dev<double>(c, *L, k, Xin, npw, Yout, npw, nb, prof, df);
     }
     int applyH32(const c32 *Xin, c32 *Yout, int nb) {
+        if (real) {
+            applies32 += (nb + 1) / 2;
+            return apply_real<float>(c, *L, k, Xin, Yout, nb, prof, false);
+        }
         applies32 += nb;
         // (the legacy default stream cannot be captured)
         if (c->opt.use_graph && !prof && s != nullptr && s != cudaStreamLegacy) return graph_apply32(Xin, Yout, nb);
@@ -591,15 +656,27 @@ struct Solver {
     }
 
     // ---------------------------------------------------------- FP64 helpers
+    // In the real form every coefficient matrix is the real part of the packed product
+    // (Re(z_a^H z_b) is the real inner product of the real-form vectors).
+    template <typename R>
+    int realpart(int rows, int cols, cx<R> *Cc, int ldc) {
+        return real ? zero_imag<R>(rows, cols, Cc, ldc, s) : LOBPCG_OK;
+    }
     int gemm_cn64(int ph, int mm, int nn, const z64 *Aa, const z64 *Bb, z64 *Cc, int ldc) {
-        PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes64(mm + nn), !df);
-        if (df) return zgemm_cn_df(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
-        return gemm_cn<double>(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s);
+        {
+            PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes64(mm + nn), !df);
+            if (df) LG_TRY(zgemm_cn_df(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s));
+            else LG_TRY(gemm_cn<double>(L->gw, mm, nn, npw, 1.0, Aa, npw, Bb, npw, 0.0, Cc, ldc, s));
+        }
+        return realpart<double>(mm, nn, Cc, ldc);
     }
     // Hermitian Gram (lower triangle only; the Rayleigh-Ritz reads no more)
     int gram64(int nn, const z64 *Aa, const z64 *Bb, z64 *Cc) {
-        PhaseScope ps(prof, LOBPCG_PH_GRAM, 4.0 * nn * (nn + 1) * (double)npw, cbytes64(2 * nn), !df);
-        return zgemm_cn_lower(L->gw, nn, npw, Aa, npw, Bb, npw, Cc, nn, s, df);
+        {
+            PhaseScope ps(prof, LOBPCG_PH_GRAM, 4.0 * nn * (nn + 1) * (double)npw, cbytes64(2 * nn), !df);
+            LG_TRY(zgemm_cn_lower(L->gw, nn, npw, Aa, npw, Bb, npw, Cc, nn, s, df));
+        }
+        return realpart<double>(nn, nn, Cc, nn);
     }
     int gemm_nn64(int ph, int nn, int kk, double alpha, const z64 *Aa, const z64 *Bb, int ldb, double beta,
                   const z64 *Cc, z64 *Dd) {
@@ -608,8 +685,11 @@ struct Solver {
         return gemm_nn<double>(npw, nn, kk, alpha, Aa, npw, Bb, ldb, beta, Cc, npw, Dd, npw, s);
     }
     int gemm_cn32(int ph, int mm, int nn, const c32 *Aa, const c32 *Bb, c32 *Cc, int ldc) {
-        PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes32(mm + nn), false);
-        return gemm_cn<float>(L->gw, mm, nn, npw, 1.0f, Aa, npw, Bb, npw, 0.0f, Cc, ldc, s);
+        {
+            PhaseScope ps(prof, ph, 8.0 * mm * nn * (double)npw, cbytes32(mm + nn), false);
+            LG_TRY(gemm_cn<float>(L->gw, mm, nn, npw, 1.0f, Aa, npw, Bb, npw, 0.0f, Cc, ldc, s));
+        }
+        return realpart<float>(mm, nn, Cc, ldc);
     }
     int gemm_nn32(int ph, int nn, int kk, float alpha, const c32 *Aa, const c32 *Bb, int ldb, float beta,
                   const c32 *Cc, c32 *Dd) {
@@ -620,9 +700,12 @@ struct Solver {
     // Cholesky pivot of the unit-diagonal Gram: a kept direction amplifies the Gram's rounding
     // by 1/pivot^2, so tol is ~1e3 x the Gram's unit roundoff (FP64 Grams 1e-12, FP32 Grams 1e-3).
     int rr(int nz, int mm, double tol, int lead = 0) {
-        const double n3 = (double)nz * nz * nz;
-        PhaseScope ps(prof, LOBPCG_PH_RR, 8.0 * (3.0 * n3 + 2.0 * nz * (double)nz * mm), 0.0, true);
-        return rayleigh_ritz(L->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s, lead);
+        {
+            const double n3 = (double)nz * nz * nz;
+            PhaseScope ps(prof, LOBPCG_PH_RR, 8.0 * (3.0 * n3 + 2.0 * nz * (double)nz * mm), 0.0, true);
+            LG_TRY(rayleigh_ritz(L->ew, nz, mm, S, nz, A, nz, tol, theta, C, nz, ndrop, s, lead));
+        }
+        return realpart<double>(nz, mm, C, nz);   // a real symmetric pencil has real Ritz vectors
     }
     template <typename Ro, typename Ri>
     int cast(int cols, const cx<Ri> *a, cx<Ro> *b) {
@@ -678,7 +761,7 @@ struct Solver {
             z64 *W = col(Zc, m), *HW = col(HZc, m);
             {   // steps 2-3: R = HX - X Upsilon, W = K(R)
                 PhaseScope ps(prof, LOBPCG_PH_UPDATE, 20.0 * npw * m, cbytes64(3.0 * m), true);
-                LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, c->kp[k].kin64, W, npw, work, part, s));
+                LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, kin, W, npw, work, part, s));
             }
             LG_TRY(constrain64(W, m, b * m));
             LG_TRY(applyH64(W, HW, m));
@@ -773,7 +856,7 @@ struct Solver {
             LG_TRY(constrain32(R32, m, X32, m, LOBPCG_PH_UPDATE));
             {   // step 3: W = K(R)
                 PhaseScope ps(prof, LOBPCG_PH_UPDATE, 10.0 * npw * m, cbytes64(m) + 2.0 * cbytes32(m), false);
-                LG_TRY(precond32(npw, m, Xb, npw, c->kp[k].kin64, R32, npw, W32, npw, work, part, s));
+                LG_TRY(precond32(npw, m, Xb, npw, kin, R32, npw, W32, npw, work, part, s));
             }
             LG_TRY(constrain32(W32, m, X32all, j0, LOBPCG_PH_CONSTRAINT));
             LG_TRY(constrain32(W32, m, X32, m, LOBPCG_PH_UPDATE));
@@ -917,6 +1000,10 @@ struct Solver {
         Lane &R = *L->side;
         LG_CUDA_TRY(cudaEventRecord(L->ev_main, s));
         LG_CUDA_TRY(cudaStreamWaitEvent(R.stream, L->ev_main, 0));
+        if (real) {
+            applies64 += (m + 1) / 2;
+            return apply_real<double>(c, R, k, col(X, b * m), col(HXr, b * m), m, nullptr, df);
+        }
         applies64 += m;
         return apply_H_dev<double>(c, R, k, col(X, b * m), npw, col(HXr, b * m), npw, m, nullptr, df);
     }
@@ -1014,7 +1101,7 @@ struct SolveCounters {
 
 // Solve one k-point for M bands of which the first Mreq must converge (the rest are buffer bands).
 int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_h, double *res_h, int &sweeps_done,
-            Prof *prof, SolveCounters &cnt) {
+            Prof *prof, SolveCounters &cnt, bool real = false) {
     L.clear_graphs();  // buffers may have moved since an earlier solve
     // whatever way this returns, no side-stream work (reading X) outlives it
     struct SideSync {
@@ -1028,7 +1115,9 @@ int solve_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *eig_
     sv.L = &L;
     sv.prof = prof;
     sv.k = k;
-    sv.npw = c->kp[k].npw;
+    sv.real = real;
+    sv.npw = real ? c->kp[k].n_half : c->kp[k].npw;
+    sv.kin = real ? c->kp[k].kin_half64 : c->kp[k].kin64;
     sv.M = M;
     sv.m = c->opt.block_size;
     sv.nblk = M / sv.m;
@@ -1182,6 +1271,7 @@ int solve_pcg_k(lobpcg_ctx *c, Lane &L, int k, int M, int Mreq, z64 *X, double *
     sv.prof = prof;
     sv.k = k;
     sv.npw = c->kp[k].npw;
+    sv.kin = c->kp[k].kin64;
     sv.M = M;
     sv.m = c->opt.block_size;
     sv.nblk = M / sv.m;
@@ -1270,6 +1360,7 @@ int validate_options(const lobpcg_options &o) {
     if (!(o.mixed_switch >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_switch must be >= 0");
     if (!(o.mixed_early >= 0.0)) return fail(LOBPCG_ERR_ARG, "mixed_early must be >= 0");
     if (o.fp64_gemm < 0 || o.fp64_gemm > 3) return fail(LOBPCG_ERR_ARG, "fp64_gemm must be 0, 1, 2 or 3");
+    if (o.gamma_real != 0 && o.gamma_real != 1) return fail(LOBPCG_ERR_ARG, "gamma_real must be 0 or 1");
     return LOBPCG_OK;
 }
 
@@ -1295,6 +1386,7 @@ int lobpcg_default_options(lobpcg_options *opt) {
     opt->mixed_switch = 0.0;
     opt->mixed_early = 1e-3;
     opt->fp64_gemm = 0;
+    opt->gamma_real = 0;
     return LOBPCG_OK;
 }
 
@@ -1619,7 +1711,27 @@ static int solve_one(lobpcg_ctx *c, Lane &L, int k, int M, int nbuf, void *Xk, d
         LG_CUDA_TRY(cudaMemcpyAsync(Xd, Xk, bytes, cudaMemcpyHostToDevice, L.stream));
     }
     int rc;
-    if (nbuf > 0) {
+    const KPoint &K = c->kp[k];
+    if (!pcg && c->opt.gamma_real && K.gamma) {
+        // Gamma real form: the start vectors projected onto it and packed on the half sphere
+        // (n_half rows), buffer bands pseudo-random there (G = 0 component real), solved packed,
+        // unpacked into the caller's sphere vectors (c(-G) = conj(c(G)))
+        const int nz = K.n_half;
+        LG_TRY(c->alloc.ensure(L.Xpk, sizeof(z64) * (size_t)nz * (M + nbuf)));
+        z64 *Xp = static_cast<z64 *>(L.Xpk.p);
+        LG_TRY(gamma_pack_full<double>(nz, M, Xd, npw, K.half, K.mirror, Xp, nz, L.stream));
+        if (nbuf > 0) {
+            LG_TRY(fill_random(nz, nbuf, Xp + (size_t)nz * M, nz, 0x51ED270Bu + 977u * (unsigned)k, L.stream));
+            LG_TRY(zero_imag<double>(1, nbuf, Xp + (size_t)nz * M, nz, L.stream));
+        }
+        std::vector<double> ebuf(2 * (size_t)(M + nbuf));
+        rc = solve_k(c, L, k, M + nbuf, M, Xp, ebuf.data(), ebuf.data() + (M + nbuf), sw, prof, cnt, true);
+        if (rc < 0) return rc;
+        LG_TRY(gamma_unpack_full<double>(nz, M, Xp, nz, K.half, K.mirror, Xd, npw, L.stream));
+        LG_CUDA_TRY(cudaStreamSynchronize(L.stream));
+        std::memcpy(eig_k, ebuf.data(), sizeof(double) * M);
+        std::memcpy(res_k, ebuf.data() + (M + nbuf), sizeof(double) * M);
+    } else if (nbuf > 0) {
         // buffer bands: an internal block of M + nbuf columns, the extra ones pseudo-random
         LG_TRY(c->alloc.ensure(L.Xext, sizeof(z64) * (size_t)npw * (M + nbuf)));
         z64 *Xe = static_cast<z64 *>(L.Xext.p);

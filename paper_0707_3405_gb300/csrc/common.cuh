@@ -296,6 +296,25 @@ int gemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alph
 int zgemm_small(GemmWork *w, char opA, char opB, int m, int n, int k, double alpha, const z64 *A, int lda,
                 const z64 *B, int ldb, double beta, z64 *C, int ldc, cudaStream_t s);
 
+// ------------------------------------------------------------------ Gamma-point real form (vec.cu)
+// Packed half-sphere storage of real-form vectors (c(-G) = conj(c(G))): z[0] = c(0), z[g] =
+// sqrt(2) c(G_g) for G_g in the half set; half[g] / mirror[g]: sphere positions of G_g / -G_g.
+template <typename R>
+int gamma_pack_full(int nz, int nb, const cx<R> *C, int ldc, const int *half, const int *mirror, cx<R> *Z, int ldz,
+                    cudaStream_t s);
+template <typename R>
+int gamma_unpack_full(int nz, int nb, const cx<R> *Z, int ldz, const int *half, const int *mirror, cx<R> *C, int ldc,
+                      cudaStream_t s);
+// bands 2i, 2i+1 of Z -> sphere column i of C as c_a + i c_b, and back from Y = H C
+template <typename R>
+int gamma_unpack_pairs(int nz, int nb, const cx<R> *Z, int ldz, const int *half, const int *mirror, cx<R> *C, int ldc,
+                       cudaStream_t s);
+template <typename R>
+int gamma_pack_pairs(int nz, int nb, const cx<R> *Y, int ldy, const int *half, const int *mirror, cx<R> *Z, int ldz,
+                     cudaStream_t s);
+template <typename R>
+int zero_imag(int rows, int cols, cx<R> *A, int lda, cudaStream_t s);
+
 // ------------------------------------------------------------------ band-by-band PCG (pcg.cu)
 // Device-side steps of one band of the PCG comparison method: every scalar lives in sc (device),
 // so a band iteration never waits for the host.  Vectors are npw long, FP64; Y (npw x j, ld ldy)

@@ -526,4 +526,163 @@ template int copy_cast<float, float>(int, int, const c32 *, int, c32 *, int, cud
 template int scale_rows<double>(int, int, const double *, z64 *, int, cudaStream_t);
 template int scale_rows<float>(int, int, const float *, c32 *, int, cudaStream_t);
 
+
+// ------------------------------------------------------------------ Gamma-point real form
+// At k = 0, with H commuting with c(G) -> conj(c(-G)), the eigenvectors can be taken real in
+// r space: c(-G) = conj(c(G)).  Such a vector is stored packed on the half sphere
+// {G = 0} u S+ (S+: n_x > 0, or n_x = 0 and n_y > 0, or n_x = n_y = 0 and n_z > 0), G = 0 first:
+//     z[0] = c(0) (real),  z[g] = sqrt(2) c(G_g)  (G_g in S+),
+// so that Re(z_a^H z_b) = c_a^H c_b (the real inner product of the real form).  half[g] is the
+// position of G_g in the sphere's order and mirror[g] the position of -G_g (mirror[0] = half[0]).
+namespace {
+
+constexpr double kRsqrt2 = 0.70710678118654752440;
+
+// Sphere vectors (npw x nb) -> packed (nz x nb): z[g] = (c(G) + conj(c(-G))) / sqrt(2), z[0] = Re c(0)
+// (the projection of an arbitrary vector onto the real form).
+template <typename R>
+__global__ void k_gamma_pack_full(int nz, int nb, const cx<R> *__restrict__ C, int ldc, const int *__restrict__ half,
+                                  const int *__restrict__ mirror, cx<R> *__restrict__ Z, int ldz) {
+    const size_t tot = (size_t)nz * nb;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e % nz), b = (int)(e / nz);
+        const cx<R> cp = C[(size_t)b * ldc + half[g]];
+        if (g == 0) {
+            Z[(size_t)b * ldz] = mkc<R>(cp.x, (R)0);
+        } else {
+            const cx<R> cq = C[(size_t)b * ldc + mirror[g]];
+            Z[(size_t)b * ldz + g] = mkc<R>((R)kRsqrt2 * (cp.x + cq.x), (R)kRsqrt2 * (cp.y - cq.y));
+        }
+    }
+}
+
+// Packed (nz x nb) -> sphere vectors (npw x nb): c(G) = z / sqrt(2), c(-G) = conj(z) / sqrt(2).
+template <typename R>
+__global__ void k_gamma_unpack_full(int nz, int nb, const cx<R> *__restrict__ Z, int ldz, const int *__restrict__ half,
+                                    const int *__restrict__ mirror, cx<R> *__restrict__ C, int ldc) {
+    const size_t tot = (size_t)nz * nb;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e % nz), b = (int)(e / nz);
+        const cx<R> z = Z[(size_t)b * ldz + g];
+        if (g == 0) {
+            C[(size_t)b * ldc + half[0]] = mkc<R>(z.x, (R)0);
+        } else {
+            C[(size_t)b * ldc + half[g]] = mkc<R>((R)kRsqrt2 * z.x, (R)kRsqrt2 * z.y);
+            C[(size_t)b * ldc + mirror[g]] = mkc<R>((R)kRsqrt2 * z.x, -(R)kRsqrt2 * z.y);
+        }
+    }
+}
+
+// Two packed real-form bands a = band 2i, b = band 2i+1 -> one sphere vector c_a + i c_b
+// (column i of C; b = 0 past the last band).  H is complex-linear, so one application gives
+// H c_a + i H c_b.
+template <typename R>
+__global__ void k_gamma_unpack_pairs(int nz, int nb, const cx<R> *__restrict__ Z, int ldz, const int *__restrict__ half,
+                                     const int *__restrict__ mirror, cx<R> *__restrict__ C, int ldc) {
+    const int np = (nb + 1) / 2;
+    const size_t tot = (size_t)nz * np;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e % nz), i = (int)(e / nz);
+        const cx<R> a = Z[(size_t)(2 * i) * ldz + g];
+        const cx<R> b = (2 * i + 1 < nb) ? Z[(size_t)(2 * i + 1) * ldz + g] : mkc<R>((R)0, (R)0);
+        cx<R> *Ci = C + (size_t)i * ldc;
+        if (g == 0) {
+            Ci[half[0]] = mkc<R>(a.x, b.x);
+        } else {
+            const R s = (R)kRsqrt2;
+            Ci[half[g]] = mkc<R>(s * (a.x - b.y), s * (a.y + b.x));     // (a + i b) / sqrt(2)
+            Ci[mirror[g]] = mkc<R>(s * (a.x + b.y), s * (b.x - a.y));   // (conj a + i conj b) / sqrt(2)
+        }
+    }
+}
+
+// Y = H c_a + i H c_b (sphere) -> packed H a, H b: with both images real-form,
+// (H c_a)(G) = (Y(G) + conj(Y(-G))) / 2 and (H c_b)(G) = (Y(G) - conj(Y(-G))) / (2 i).
+template <typename R>
+__global__ void k_gamma_pack_pairs(int nz, int nb, const cx<R> *__restrict__ Y, int ldy, const int *__restrict__ half,
+                                   const int *__restrict__ mirror, cx<R> *__restrict__ Z, int ldz) {
+    const int np = (nb + 1) / 2;
+    const size_t tot = (size_t)nz * np;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(e % nz), i = (int)(e / nz);
+        const cx<R> *Yi = Y + (size_t)i * ldy;
+        cx<R> a, b;
+        if (g == 0) {
+            const cx<R> y0 = Yi[half[0]];
+            a = mkc<R>(y0.x, (R)0);
+            b = mkc<R>(y0.y, (R)0);
+        } else {
+            const cx<R> yp = Yi[half[g]], yq = Yi[mirror[g]];
+            const R s = (R)kRsqrt2;
+            a = mkc<R>(s * (yp.x + yq.x), s * (yp.y - yq.y));   // (Y(G) + conj Y(-G)) / sqrt(2)
+            const R u = yp.x - yq.x, v = yp.y + yq.y;          // Y(G) - conj Y(-G)
+            b = mkc<R>(s * v, -s * u);                          // that / (i sqrt(2))
+        }
+        Z[(size_t)(2 * i) * ldz + g] = a;
+        if (2 * i + 1 < nb) Z[(size_t)(2 * i + 1) * ldz + g] = b;
+    }
+}
+
+template <typename R>
+__global__ void k_zero_imag(int rows, int cols, cx<R> *__restrict__ A, int lda) {
+    const size_t tot = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        A[(size_t)j * lda + i].y = (R)0;
+    }
+}
+
+int gamma_grid(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
+
+}  // namespace
+
+template <typename R>
+int gamma_pack_full(int nz, int nb, const cx<R> *C, int ldc, const int *half, const int *mirror, cx<R> *Z, int ldz,
+                    cudaStream_t s) {
+    if (nz <= 0 || nb <= 0) return LOBPCG_OK;
+    k_gamma_pack_full<R><<<gamma_grid((size_t)nz * nb), 256, 0, s>>>(nz, nb, C, ldc, half, mirror, Z, ldz);
+    return check_launch("gamma pack");
+}
+template <typename R>
+int gamma_unpack_full(int nz, int nb, const cx<R> *Z, int ldz, const int *half, const int *mirror, cx<R> *C, int ldc,
+                      cudaStream_t s) {
+    if (nz <= 0 || nb <= 0) return LOBPCG_OK;
+    k_gamma_unpack_full<R><<<gamma_grid((size_t)nz * nb), 256, 0, s>>>(nz, nb, Z, ldz, half, mirror, C, ldc);
+    return check_launch("gamma unpack");
+}
+template <typename R>
+int gamma_unpack_pairs(int nz, int nb, const cx<R> *Z, int ldz, const int *half, const int *mirror, cx<R> *C, int ldc,
+                       cudaStream_t s) {
+    if (nz <= 0 || nb <= 0) return LOBPCG_OK;
+    k_gamma_unpack_pairs<R><<<gamma_grid((size_t)nz * ((nb + 1) / 2)), 256, 0, s>>>(nz, nb, Z, ldz, half, mirror, C,
+                                                                                   ldc);
+    return check_launch("gamma unpack pairs");
+}
+template <typename R>
+int gamma_pack_pairs(int nz, int nb, const cx<R> *Y, int ldy, const int *half, const int *mirror, cx<R> *Z, int ldz,
+                     cudaStream_t s) {
+    if (nz <= 0 || nb <= 0) return LOBPCG_OK;
+    k_gamma_pack_pairs<R><<<gamma_grid((size_t)nz * ((nb + 1) / 2)), 256, 0, s>>>(nz, nb, Y, ldy, half, mirror, Z,
+                                                                                 ldz);
+    return check_launch("gamma pack pairs");
+}
+template <typename R>
+int zero_imag(int rows, int cols, cx<R> *A, int lda, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return LOBPCG_OK;
+    k_zero_imag<R><<<gamma_grid((size_t)rows * cols), 256, 0, s>>>(rows, cols, A, lda);
+    return check_launch("real part");
+}
+#define LG_GAMMA_INST(R)                                                                                             \
+    template int gamma_pack_full<R>(int, int, const cx<R> *, int, const int *, const int *, cx<R> *, int, cudaStream_t); \
+    template int gamma_unpack_full<R>(int, int, const cx<R> *, int, const int *, const int *, cx<R> *, int,          \
+                                      cudaStream_t);                                                               \
+    template int gamma_unpack_pairs<R>(int, int, const cx<R> *, int, const int *, const int *, cx<R> *, int,         \
+                                       cudaStream_t);                                                              \
+    template int gamma_pack_pairs<R>(int, int, const cx<R> *, int, const int *, const int *, cx<R> *, int,           \
+                                     cudaStream_t);                                                                \
+    template int zero_imag<R>(int, int, cx<R> *, int, cudaStream_t);
+LG_GAMMA_INST(double)
+LG_GAMMA_INST(float)
+#undef LG_GAMMA_INST
+
 }  // namespace lg
