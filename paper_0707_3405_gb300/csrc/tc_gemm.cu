@@ -363,10 +363,26 @@ int launch_cn(GemmWork &w, int m, int n, int K, float alpha, const c32 *A, int l
     LG_TRY(ensure_smem(k_tc_cn<NT>, SMEM, attr));
     const int tm = (m + 127) / 128, tn = (n + NT - 1) / NT;
     const int tiles = tm * tn;
-    // one CTA per SM (shared memory); split K so the grid covers the GPU, chunks of at most 2048
-    const int want = std::max(1, (num_sms_tc() + tiles - 1) / tiles);
-    int kchunk = (K + want - 1) / want;
-    kchunk = std::min(2048, ((kchunk + KBC - 1) / KBC) * KBC);
+    // one CTA per SM (shared memory): split K over the GPU.  Cost model in units of one 16-term
+    // stage of a CTA (about a microsecond): whole waves x stages per CTA, plus the FP64 partial
+    // tiles written and summed (about 7 MB per stage-time of HBM traffic); the cheapest split
+    // with chunks of 256 to 8192 terms wins.
+    const int sms = num_sms_tc();
+    int kchunk = std::max(KBC, ((K + KBC - 1) / KBC) * KBC);
+    double best = 1e300;
+    for (int ns = 1; ns <= 4 * sms; ++ns) {
+        const int kc = ((K + ns - 1) / ns + KBC - 1) / KBC * KBC;
+        if (kc > 8192) continue;
+        if (kc < 256 && ns > 1) break;
+        const int nsp = (K + kc - 1) / kc;
+        const long long ctas = (long long)tiles * nsp;
+        const long long waves = (ctas + sms - 1) / sms;
+        const double cost = (double)waves * (kc / KBC) + (double)nsp * 32.0 * m * (double)n / 7.2e6;
+        if (cost < best) {
+            best = cost;
+            kchunk = kc;
+        }
+    }
     kchunk = std::max(kchunk, KBC);
     const int nsplit = (K + kchunk - 1) / kchunk;
     LG_TRY(w.alloc->ensure(w.part, sizeof(z64) * (size_t)nsplit * m * n));
