@@ -201,12 +201,28 @@ __device__ __forceinline__ C shfl_xor_c(C a, int m) {
     return mkc<float>(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
 }
 
-__device__ __forceinline__ C sel4(int s, C a0, C a1, C a2, C a3) {
-    C r = a0;
-    r = (s == 1) ? a1 : r;
-    r = (s == 2) ? a2 : r;
-    r = (s == 3) ? a3 : r;
-    return r;
+// 4 x 4 transpose across the four lanes t = 0..3 of a line: on return lane t holds, in a[s], the
+// value lane s held in a[t].  Two butterfly stages: lanes t and t^1 swap the two elements whose
+// index bit 0 differs from bit 0 of t, then lanes t and t^2 swap the two whose bit 1 differs from
+// bit 1 of t (12 selects and 4 shuffles per stage).  Pure data movement: the values are those of
+// any other exchange, bit for bit.
+__device__ __forceinline__ void xpose4(C (&a)[4], int t) {
+    const bool b0 = (t & 1) != 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const C send = b0 ? a[2 * k] : a[2 * k + 1];
+        const C recv = shfl_xor_c(send, 1);
+        a[2 * k] = b0 ? recv : a[2 * k];
+        a[2 * k + 1] = b0 ? a[2 * k + 1] : recv;
+    }
+    const bool b1 = (t & 2) != 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const C send = b1 ? a[k] : a[k + 2];
+        const C recv = shfl_xor_c(send, 2);
+        a[k] = b1 ? recv : a[k];
+        a[k + 2] = b1 ? a[k + 2] : recv;
+    }
 }
 
 // Strided -> block: in v[e] = x[t + T e]; out v[i + (E/T) k2] = X[(t E/T + i) + E k2].
@@ -235,14 +251,8 @@ __device__ __forceinline__ void s2b(C *v, int t) {
         C out[E];
 #pragma unroll
         for (int i = 0; i < BK; ++i) {
-            const C own = sel4(t, v[i], v[BK + i], v[2 * BK + i], v[3 * BK + i]);
-            C r[4];
-#pragma unroll
-            for (int m = 1; m < 4; ++m)
-                r[m] = shfl_xor_c(sel4(t ^ m, v[i], v[BK + i], v[2 * BK + i], v[3 * BK + i]), m);
-            C w[4];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) w[s] = sel4(s ^ t, own, r[1], r[2], r[3]);
+            C w[4] = {v[i], v[BK + i], v[2 * BK + i], v[3 * BK + i]};
+            xpose4(w, t);   // w[s] = lane s's v[t BK + i]
             Base<4, INV>::run(w);
 #pragma unroll
             for (int k2 = 0; k2 < 4; ++k2) out[i + BK * k2] = w[k2];
@@ -279,12 +289,9 @@ __device__ __forceinline__ void b2s(C *v, int t) {
             const int x1 = t * BK + i;
 #pragma unroll
             for (int s = 1; s < 4; ++s) w[s] = w[s] * twc<N, INV>((x1 * s) % N);
-            const C own = sel4(t, w[0], w[1], w[2], w[3]);
-            C r[4];
+            xpose4(w, t);   // w[s] = lane s's w[t]
 #pragma unroll
-            for (int m = 1; m < 4; ++m) r[m] = shfl_xor_c(sel4(t ^ m, w[0], w[1], w[2], w[3]), m);
-#pragma unroll
-            for (int s = 0; s < 4; ++s) out[s * BK + i] = sel4(s ^ t, own, r[1], r[2], r[3]);
+            for (int s = 0; s < 4; ++s) out[s * BK + i] = w[s];
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = out[e];
