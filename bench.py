@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--fp64", action="store_true",
                     help="run the FP64-only comparison solve also on cells where it takes minutes")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-gamma-real", action="store_true",
+                    help="skip the Gamma-point real-orbital solve of a Gamma cell (reported beside the headline)")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the warm-up and timed steps of --mode, no other legs")
     ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply", "apply_df32", "fp64gemm"],
@@ -210,7 +212,7 @@ def nbuf_of(w, nbuf_arg):
 
 
 def solver_for(w, precision, timing=False, max_sweeps=1, tol=1e-8, nbuf=0, autotune=False, use_graph=False,
-               kidx=None):
+               kidx=None, gamma_real=False):
     """A library handle for the k-points ``kidx`` of workload ``w`` (all when None)."""
     import dataclasses
     import paper_0707_3405_gb300 as lg
@@ -219,7 +221,7 @@ def solver_for(w, precision, timing=False, max_sweeps=1, tol=1e-8, nbuf=0, autot
     return lg.Solver(wl.a, wl.N, wl.ecut, wl.kpts, wl.vloc(), wl.proj_E if wl.nproj else None,
                      beta=(lambda mil, k: wl.beta(mil, k)) if wl.nproj else None, block_size=w.block,
                      nline=w.nline, max_sweeps=max_sweeps, precision=precision, tol=tol, timing=timing,
-                     nbuf=nbuf, autotune=autotune, use_graph=use_graph)
+                     nbuf=nbuf, autotune=autotune, use_graph=use_graph, gamma_real=gamma_real)
 
 
 def start_block(w, s, k=0, device=True, pinned=False, kglobal=None):
@@ -636,6 +638,30 @@ def main():
     kroof = kernel_rooflines(w, npw, w.nbands + nbuf, pk)
     roof = roofline_of(kroof)
 
+    # Gamma-point real-orbital form (options.gamma_real) of the same solve, on Gamma cells
+    gamma_real = None
+    if not sharded and w.nk == 1 and not np.any(w.kpts[0]) and not args.no_gamma_real:
+        s3 = solver_for(w, args.precision, timing=False, max_sweeps=args.max_sweeps, tol=args.tol, nbuf=nbuf,
+                        use_graph=True, gamma_real=True)
+        X3 = X0[0].clone()
+        for rep in range(2):   # the first solve is a warm-up
+            X3.copy_(X0[0])
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            r3 = s3.solve([X3])
+            g1.record(stream)
+            torch.cuda.synchronize()
+        el = g0.elapsed_time(g1) / 1e3
+        gamma_real = {"s_to_tol": el, "sweeps": r3.stats["sweeps"], "converged": bool(r3.status == 0),
+                      "max_resid": float(r3.resid.max()),
+                      "max_eig_diff_vs_complex_Ha": float(np.abs(r3.eig[0] - eig_main[0]).max()),
+                      "speedup_vs_complex": s_to_tol / el}
+        if gold and 0 in gold:
+            gamma_real["eig_err_vs_oracle_golden_Ha"] = float(np.abs(r3.eig[0][:len(gold[0])] -
+                                                                   gold[0][:w.nbands]).max())
+        s3.close()
+
     # the FP64-only path on the same problem from the same start
     fp64 = None
     if not args.no_fp64 and args.precision != "fp64" and (args.fp64 or run_fp64_default(w)):
@@ -686,6 +712,7 @@ def main():
             "apply_H": applyh,
             "autotune_ms_first_solve": ms_autotune,
             "fp64_path": fp64,
+            "gamma_real_form": gamma_real,
             "phases_ms_per_solve": phases,
             "phase_rates": prl,
         }
