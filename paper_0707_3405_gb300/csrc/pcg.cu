@@ -154,7 +154,7 @@ __global__ void k_pcg_vec(int npw, int op, z64 *__restrict__ v, const z64 *__res
                 v[g] = (p / (p + 16.0 * x * x * x * x)) * a[g];
                 break;
             }
-            case 4: v[g] = a[g] + gam * v[g]; break;
+            case 4: v[g] = gam != 0.0 ? a[g] + gam * v[g] : a[g]; break;   // no previous d on the first
             case 5: v[g] = a[g] - co * b[g]; break;
             case 6: {
                 v[g] = c * v[g] + s * a[g];
