@@ -732,6 +732,13 @@ struct Solver {
         }
         return LOBPCG_OK;
     }
+    // V <- V - Xb (Xb^H V) for the m columns of V, and HV <- HV - HXb (Xb^H V) when given
+    int project_block64(const z64 *Xb, const z64 *HXb, z64 *V, z64 *HV) {
+        LG_TRY(gemm_cn64(LOBPCG_PH_UPDATE, m, m, Xb, V, G, m));
+        LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, -1.0, Xb, G, m, 1.0, V, V));
+        if (HV) LG_TRY(gemm_nn64(LOBPCG_PH_UPDATE, m, m, -1.0, HXb, G, m, 1.0, HV, HV));
+        return LOBPCG_OK;
+    }
     int constrain32(c32 *V, int nv, const c32 *Y, int j, int ph) {
         if (j <= 0) return LOBPCG_OK;
         for (int rep = 0; rep < 2; ++rep) {
@@ -764,7 +771,12 @@ struct Solver {
                 LG_TRY(residual_precond<double>(npw, m, Zc, npw, HZc, npw, theta, kin, W, npw, work, part, s));
             }
             LG_TRY(constrain64(W, m, b * m));
+            // W and P off span(X_b) (P's H image likewise): span[X, W, P], hence the step in exact
+            // arithmetic, is unchanged, but the Gram matrix stays away from singular when bands of
+            // a degenerate shell converge and leave W and P as rounding noise close to span(X_b)
+            LG_TRY(project_block64(Zc, nullptr, W, nullptr));
             LG_TRY(applyH64(W, HW, m));
+            if (nP) LG_TRY(project_block64(Zc, HZc, col(Zc, 2 * m), col(HZc, 2 * m)));
             // step 4: Rayleigh-Ritz on span[X, W, P]
             const int nz = (2 + nP) * m;
             LG_TRY(gram64(nz, Zc, Zc, S));
