@@ -15,11 +15,13 @@
 //      eigenvalues by multisection on Sturm counts (a warp per eigenvalue),
 //      eigenvectors by inverse iteration with partial-pivoting tridiagonal
 //      LU and modified Gram-Schmidt inside clusters of close eigenvalues,
-//      back-transformation by the reflectors;
+//      back-transformation by the reflectors in blocks of 32 (compact WY form);
 //   5. C = D L^-H Q.
 // Every step runs on the GPU in FP64; no host synchronisation.
 #include "common.cuh"
 #include "df64.cuh"
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cfloat>
@@ -298,12 +300,9 @@ struct Refl {
     cx<RT> scal;  // v[r] = x[r] * scal for r >= 1
 };
 
-template <typename RT, bool CG = false, typename PT = RT>
-__device__ Refl<RT> make_reflector(const cx<PT> *__restrict__ col, int L, RT *sh) {
-    RT s = 0.0;
-    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(CG ? ldcg_as<RT>(col + r) : ld_as<RT>(col + r));
-    s = block_sum(s, sh);
-    const cx<RT> alpha = CG ? ldcg_as<RT>(col) : ld_as<RT>(col);
+// Reflector from alpha = x[0] and s = sum_{r>=1} |x[r]|^2 (LAPACK larfg convention).
+template <typename RT>
+__device__ __forceinline__ Refl<RT> reflector_from(cx<RT> alpha, RT s) {
     Refl<RT> R;
     if (s == 0.0 && alpha.y == 0.0) {
         R.tau = mkc<RT>(0.0, 0.0);
@@ -318,6 +317,45 @@ __device__ Refl<RT> make_reflector(const cx<PT> *__restrict__ col, int L, RT *sh
     const RT dd = abs2(den);
     R.scal = mkc<RT>(den.x / dd, -den.y / dd);
     return R;
+}
+
+template <typename RT, bool CG = false, typename PT = RT>
+__device__ Refl<RT> make_reflector(const cx<PT> *__restrict__ col, int L, RT *sh) {
+    RT s = 0.0;
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(CG ? ldcg_as<RT>(col + r) : ld_as<RT>(col + r));
+    s = block_sum(s, sh);
+    return reflector_from<RT>(CG ? ldcg_as<RT>(col) : ld_as<RT>(col), s);
+}
+
+// Block sum whose cross-warp step is one warp's shuffle tree (a fixed order): for large
+// blocks, where every thread summing all warp partials would cost more issue slots than
+// the rest of the step.  sh holds 33 entries; every thread gets the result.
+template <typename RT>
+__device__ RT block_sum_tree(RT v, RT *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        RT t = lane < nw ? sh[lane] : RT(0.0);
+        t = warp_sum(t);
+        if (lane == 0) sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// make_reflector with the tree sum and the scalar arithmetic in one thread, broadcast
+// through shared memory (*rb).
+template <typename RT, typename PT = RT>
+__device__ Refl<RT> make_reflector_bc(const cx<PT> *__restrict__ col, int L, RT *sh, Refl<RT> *rb) {
+    RT s = 0.0;
+    for (int r = 1 + threadIdx.x; r < L; r += blockDim.x) s += abs2(ld_as<RT>(col + r));
+    s = block_sum_tree(s, sh);
+    if (threadIdx.x == 0) *rb = reflector_from<RT>(ld_as<RT>(col), s);
+    __syncthreads();
+    return *rb;
 }
 
 // Step i, part 1: reflector (every block, redundantly) and y = A22 v by 32x32 tiles;
@@ -710,6 +748,144 @@ k_tri_fused(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ H
     }
 }
 
+// a - w_r conj(v_c) - v_r conj(w_c), each real part through fused multiply-adds
+template <typename CT>
+__device__ __forceinline__ cx<CT> rank2_entry(cx<CT> a, cx<CT> wr, cx<CT> vr, cx<CT> vc, cx<CT> wc) {
+    CT re = fma(-wr.x, vc.x, a.x);
+    re = fma(-wr.y, vc.y, re);
+    re = fma(-vr.x, wc.x, re);
+    re = fma(-vr.y, wc.y, re);
+    CT im = fma(-wr.y, vc.x, a.y);
+    im = fma(wr.x, vc.y, im);
+    im = fma(-vr.y, wc.x, im);
+    im = fma(vr.x, wc.y, im);
+    return mkc<CT>(re, im);
+}
+// acc + a b
+template <typename CT>
+__device__ __forceinline__ cx<CT> cmac(cx<CT> acc, cx<CT> a, cx<CT> b) {
+    CT re = fma(a.x, b.x, acc.x);
+    re = fma(-a.y, b.y, re);
+    CT im = fma(a.x, b.y, acc.y);
+    im = fma(a.y, b.x, im);
+    return mkc<CT>(re, im);
+}
+
+// The same reduction held in the shared memory of one thread-block cluster of CS CTAs, for
+// matrices small enough to fit there (n up to about 416 with 16 CTAs).  CTA q keeps the rows
+// r = q + CS j of the full Hermitian matrix, row-major, so that y = A v needs no reduction
+// across CTAs.  Per column i, after one cluster barrier every CTA holds y_i = A^(i) v_i and
+// column i+1 of A^(i), both gathered through distributed shared memory, and forms w_i, the
+// next column, d, e and reflector i+1 on its own: the same operations on the same values in
+// the same order, so the same bits in every CTA.  Then each CTA applies the rank-2 update to
+// its rows of the trailing block and, in the same pass, multiplies them by v_{i+1} (one warp
+// per row), and sends its entries of y_{i+1} and of column i+2 to every CTA.  The gathered
+// vectors alternate between two buffers, so that one barrier per column orders every write
+// after the reads of the buffer it overwrites.  Outputs as k_tri_fused (Hv, taus in the
+// compute type; d, e).  Dynamic shared memory: nr x n matrix entries (nr = ceil(n / CS)) and
+// 7 n vector entries.
+template <typename RT, typename CT>
+__global__ void __launch_bounds__(1024, 1)
+k_tri_cluster(int n, const cx<RT> *__restrict__ A, int lda, cx<RT> *__restrict__ Hv, cx<RT> *__restrict__ taus,
+              RT *__restrict__ dg, RT *__restrict__ eg) {
+    static_assert(sizeof(cx<CT>) == sizeof(cx<RT>), "the compute type keeps the storage size");
+    namespace cgn = cooperative_groups;
+    cgn::cluster_group cl = cgn::this_cluster();
+    const int CS = (int)cl.num_blocks(), q = (int)cl.block_rank();
+    const int nr = (n + CS - 1) / CS;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    cx<CT> *M = reinterpret_cast<cx<CT> *>(dsm);       // local row j = global row q + CS j
+    cx<CT> *vb = M + (size_t)nr * n;                    // v_i and v_{i+1}, by parity of i
+    cx<CT> *w = vb + 2 * n;                             // w_i
+    cx<CT> *yg = w + n;                                 // gathered y, two parities
+    cx<CT> *cg = yg + 2 * n;                            // gathered next column, two parities
+    __shared__ CT sh[33];
+    __shared__ Refl<CT> rb;
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, nw = blockDim.x >> 5;
+    const cx<CT> zero = mkc<CT>(0.0, 0.0);
+    // every CTA of the cluster running before any of them writes another's shared memory
+    cl.sync();
+    for (size_t e = tid; e < (size_t)nr * n; e += blockDim.x) {
+        const int j = (int)(e / n), c = (int)(e % n), r = q + CS * j;
+        M[e] = r < n ? ld_as<CT>(A + (size_t)c * lda + r) : zero;
+    }
+    // reflector 0 from column 0 of A, d[0]
+    Refl<CT> R = make_reflector_bc<CT, RT>(A + 1, n - 1, sh, &rb);
+    for (int r = tid; r < n; r += blockDim.x)
+        vb[r] = (r < 1) ? zero : (r == 1 ? mkc<CT>(1.0, 0.0) : ld_as<CT>(A + r) * R.scal);
+    if (q == 0 && tid == 0) dg[0] = A[0].x;
+    __syncthreads();
+    // y_0 = A[J,J] v_0 and column 1 on the owned rows of J = [1, n), sent to every CTA
+    for (int j = wp; j < nr; j += nw) {
+        const int r = q + CS * j;
+        if (r < 1 || r >= n) continue;
+        const cx<CT> *Mr = M + (size_t)j * n;
+        cx<CT> acc = zero;
+        for (int c = 1 + lane; c < n; c += 32) acc = cmac(acc, Mr[c], vb[c]);
+        acc.x = warp_sum(acc.x);
+        acc.y = warp_sum(acc.y);
+        if (lane < CS) {
+            cl.map_shared_rank(yg, lane)[r] = acc;
+            cl.map_shared_rank(cg, lane)[r] = Mr[1];
+        }
+    }
+    cl.sync();
+    for (int i = 0; i + 1 < n; ++i) {
+        const int par = i & 1;
+        cx<CT> *v = vb + (size_t)par * n, *vn = vb + (size_t)(1 - par) * n;
+        const cx<CT> *yv = yg + (size_t)par * n;
+        cx<CT> *x = cg + (size_t)par * n;
+        // w_i = tau y - |tau|^2 / 2 (v^H y) v on J = [i+1, n)
+        CT dre = 0.0;
+        for (int r = i + 1 + tid; r < n; r += blockDim.x) dre += v[r].x * yv[r].x + v[r].y * yv[r].y;
+        dre = block_sum_tree(dre, sh);
+        const CT t2 = (CT)0.5 * abs2(R.tau) * dre;
+        for (int r = i + 1 + tid; r < n; r += blockDim.x) w[r] = R.tau * yv[r] - t2 * v[r];
+        __syncthreads();
+        // column i+1 of A^(i+1) (in place of the gathered column of A^(i)), d[i+1]
+        const cx<CT> vi1 = v[i + 1], wi1 = w[i + 1];
+        for (int r = i + 1 + tid; r < n; r += blockDim.x) x[r] = x[r] - mul_conj(w[r], vi1) - mul_conj(v[r], wi1);
+        __syncthreads();
+        if (q == 0) {
+            cx<CT> *HvC = reinterpret_cast<cx<CT> *>(Hv);
+            for (int r = i + 1 + tid; r < n; r += blockDim.x) HvC[(size_t)i * n + r] = v[r];
+            if (tid == 0) {
+                reinterpret_cast<cx<CT> *>(taus)[i] = R.tau;
+                eg[i] = (RT)R.beta;
+                dg[i + 1] = (RT)x[i + 1].x;
+            }
+        }
+        if (i + 2 >= n) break;  // last column: nothing left to transform
+        const Refl<CT> Rn = make_reflector_bc<CT>(x + i + 2, n - i - 2, sh, &rb);
+        for (int r = tid; r < n; r += blockDim.x)
+            vn[r] = (r < i + 2) ? zero : (r == i + 2 ? mkc<CT>(1.0, 0.0) : x[r] * Rn.scal);
+        __syncthreads();
+        // rank-2 update of the owned rows of the trailing block [i+2, n)^2, times v_{i+1}
+        const int c2 = i + 2, nxt = 1 - par;
+        for (int j = wp; j < nr; j += nw) {
+            const int r = q + CS * j;
+            if (r < c2 || r >= n) continue;
+            cx<CT> *Mr = M + (size_t)j * n;
+            const cx<CT> wr = w[r], vr = v[r];
+            cx<CT> acc = zero;
+            for (int c = c2 + lane; c < n; c += 32) {
+                const cx<CT> a = rank2_entry(Mr[c], wr, vr, v[c], w[c]);
+                Mr[c] = a;
+                acc = cmac(acc, a, vn[c]);
+            }
+            acc.x = warp_sum(acc.x);
+            acc.y = warp_sum(acc.y);
+            __syncwarp();
+            if (lane < CS) {
+                cl.map_shared_rank(yg, lane)[(size_t)nxt * n + r] = acc;
+                cl.map_shared_rank(cg, lane)[(size_t)nxt * n + r] = Mr[c2];
+            }
+        }
+        R = Rn;
+        cl.sync();
+    }
+}
+
 template <typename RT>
 __global__ void k_tri_last(int n, const cx<RT> *__restrict__ A, int lda, RT *__restrict__ dg) {
     if (threadIdx.x == 0) dg[n - 1] = A[(size_t)(n - 1) * lda + n - 1].x;
@@ -1045,78 +1221,193 @@ k_inviter(int n, int m, const RT *__restrict__ d, const RT *__restrict__ e, cons
 }
 
 // ------------------------------------------------------------------ back-transformation
-// V[:, j] = H_0 H_1 ... H_{n-2} z_j (complex), one warp per eigenvector (z in shared
-// memory, warp-shuffle dot products: no block-wide barrier per reflector).
-template <typename RT>
-__global__ void __launch_bounds__(32)
-k_backtransform(int n, int m, const cx<RT> *__restrict__ Hv, const cx<RT> *__restrict__ taus, const RT *__restrict__ Z,
-                cx<RT> *__restrict__ V, int ldv) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx<RT> *z = reinterpret_cast<cx<RT> *>(smraw);
-    const int j = blockIdx.x, lane = threadIdx.x;
-    if (j >= m) return;
-    for (int r = lane; r < n; r += 32) z[r] = mkc<RT>(Z[(size_t)j * n + r], 0.0);
-    __syncwarp();
-    for (int i = n - 2; i >= 0; --i) {
-        const cx<RT> tau = taus[i];
-        if (tau.x == 0.0 && tau.y == 0.0) continue;
-        const int L = n - i - 1;
-        const cx<RT> *v = Hv + (size_t)i * n + i + 1;
-        RT sre = 0.0, sim = 0.0;
-        for (int r = lane; r < L; r += 32) {
-            const cx<RT> a = v[r], b = z[i + 1 + r];
-            sre += a.x * b.x + a.y * b.y;
-            sim += a.x * b.y - a.y * b.x;
+// V = H_0 H_1 ... H_{n-2} Z with H_i = I - tau_i v_i v_i^H, applied kWy reflectors at a time in
+// the compact WY form (Schreiber and Van Loan, 1989): H_{i0} ... H_{i0+k-1} = I - Y T Y^H with
+// Y = [v_{i0} ... v_{i0+k-1}] and T upper triangular, T_jj = tau_j and
+// T[0:j, j] = -tau_j T[0:j, 0:j] (Y[:, 0:j]^H v_j).  Each block then costs one reduction
+// (t = Y^H z) instead of one per reflector.  v_i is read only on its support r >= i + 1.
+constexpr int kWy = 32;
+
+// Partial Gram matrices G = Y^H Y of each block of kWy reflectors (block b: reflectors
+// 32 b ...), over row chunk ch of the block's rows [32 b + 1, n): grid (blocks, chunks).  The
+// chunk of Y is staged in shared memory (zero where v_k has no support, r <= 32 b + k); thread
+// (k, g) accumulates G[k][g + 8 u], u = 0..3.  Gp[b][ch] is a full kWy x kWy row-major matrix.
+constexpr int kWyRows = 64;   // rows of a chunk
+template <typename CT>
+__global__ void __launch_bounds__(256)
+k_wy_gram(int n, int nch, const cx<CT> *__restrict__ Hv, cx<CT> *__restrict__ Gp) {
+    __shared__ cx<CT> Ys[kWyRows][kWy + 1];
+    const int b = blockIdx.x, ch = blockIdx.y, i0 = b * kWy, kb = min(kWy, n - 1 - i0);
+    const int rows = n - (i0 + 1), per = (rows + nch - 1) / nch;
+    const int r0 = i0 + 1 + ch * per, r1 = min(n, r0 + per);
+    const int tid = threadIdx.x, k = tid >> 3, g = tid & 7;
+    const cx<CT> zero = mkc<CT>(0.0, 0.0);
+    cx<CT> acc[4] = {zero, zero, zero, zero};
+    for (int c0 = r0; c0 < r1; c0 += kWyRows) {
+        __syncthreads();
+        for (int e = tid; e < kWyRows * kWy; e += blockDim.x) {
+            const int kk = e / kWyRows, rr = e % kWyRows, r = c0 + rr;
+            Ys[rr][kk] = (kk < kb && r < r1 && r > i0 + kk) ? Hv[(size_t)(i0 + kk) * n + r] : zero;
         }
-        sre = warp_sum(sre);
-        sim = warp_sum(sim);
-        const cx<RT> ts = tau * mkc<RT>(sre, sim);
-        for (int r = lane; r < L; r += 32) z[i + 1 + r] = z[i + 1 + r] - ts * v[r];
-        __syncwarp();
+        __syncthreads();
+        const int nr = min(kWyRows, r1 - c0);
+        for (int rr = 0; rr < nr; ++rr) {
+            const cx<CT> a = conjc(Ys[rr][k]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = cmac(acc[u], a, Ys[rr][g + 8 * u]);
+        }
     }
-    for (int r = lane; r < n; r += 32) V[(size_t)j * ldv + r] = z[r];
+    cx<CT> *out = Gp + ((size_t)b * nch + ch) * kWy * kWy;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[k * kWy + g + 8 * u] = acc[u];
 }
 
-// The same in double-FP32 for reflectors stored as pairs (the double-FP32 tridiagonalisation),
-// four warps per vector: one SM's FP64 units bound the one-warp FP64 version, while the pair
-// arithmetic spreads over the four FP32 sub-partitions.  Dot products: warp shuffles, then the
-// four warp sums in a fixed order (reproducible).
-template <typename RT>
-__global__ void __launch_bounds__(128)
-k_backtransform_df(int n, int m, const cx<df64> *__restrict__ Hv, const cx<df64> *__restrict__ taus,
-                   const RT *__restrict__ Z, cx<RT> *__restrict__ V, int ldv) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx<df64> *z = reinterpret_cast<cx<df64> *>(smraw);
-    __shared__ df64 red[2][4];
-    const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    if (j >= m) return;
-    for (int r = tid; r < n; r += 128) z[r] = mkc<df64>((df64)Z[(size_t)j * n + r], df64(0.f));
+// T of each block from its Gram (chunk partials summed in chunk order): T_jj = tau_j, then
+// pairs of adjacent diagonal blocks of width h = 1, 2, 4, 8, 16 merged by
+// T12 = -T11 G12 T22 (the product of the two blocks' WY forms), each merge level in two
+// parallel matrix products.  kWy x kWy row-major into Tf[b], zero outside the reflectors.
+template <typename CT>
+__global__ void __launch_bounds__(256)
+k_wy_t(int n, int nch, const cx<CT> *__restrict__ Gp, const cx<CT> *__restrict__ taus, cx<CT> *__restrict__ Tf) {
+    __shared__ cx<CT> G[kWy][kWy + 1];
+    __shared__ cx<CT> T[kWy][kWy + 1];
+    __shared__ cx<CT> X[kWy][kWy + 1];
+    const int b = blockIdx.x, i0 = b * kWy, kb = min(kWy, n - 1 - i0), tid = threadIdx.x;
+    const cx<CT> zero = mkc<CT>(0.0, 0.0);
+    for (int e = tid; e < kWy * kWy; e += blockDim.x) {
+        const int k = e / kWy, j = e % kWy;
+        cx<CT> sum = zero;
+        for (int ch = 0; ch < nch; ++ch) sum = sum + Gp[((size_t)b * nch + ch) * kWy * kWy + e];
+        G[k][j] = sum;
+        T[k][j] = (k == j && k < kb) ? taus[i0 + k] : zero;
+    }
     __syncthreads();
-    for (int i = n - 2; i >= 0; --i) {
-        const cx<df64> tau = taus[i];
-        if (tau.x == df64(0.f) && tau.y == df64(0.f)) continue;  // uniform
-        const int L = n - i - 1;
-        const cx<df64> *v = Hv + (size_t)i * n + i + 1;
-        df64 sre(0.f), sim(0.f);
-        for (int r = tid; r < L; r += 128) {
-            const cx<df64> a = v[r], b = z[i + 1 + r];
-            sre += a.x * b.x + a.y * b.y;
-            sim += a.x * b.y - a.y * b.x;
-        }
-        sre = warp_sum(sre);
-        sim = warp_sum(sim);
-        if (lane == 0) {
-            red[0][wp] = sre;
-            red[1][wp] = sim;
+    for (int h = 1; h < kWy; h *= 2) {
+        // entries of the merges at this level: (kWy / 2h) merges x h x h
+        const int nent = (kWy / (2 * h)) * h * h;
+        // X = T11 G12
+        for (int e = tid; e < nent; e += blockDim.x) {
+            const int mg = e / (h * h), k = (e % (h * h)) / h, l = e % h;
+            const int a = mg * 2 * h;
+            cx<CT> u = zero;
+            for (int p = k; p < h; ++p) u = cmac(u, T[a + k][a + p], G[a + p][a + h + l]);
+            X[a + k][a + h + l] = u;
         }
         __syncthreads();
-        sre = ((red[0][0] + red[0][1]) + red[0][2]) + red[0][3];
-        sim = ((red[1][0] + red[1][1]) + red[1][2]) + red[1][3];
-        const cx<df64> ts = tau * mkc<df64>(sre, sim);
-        for (int r = tid; r < L; r += 128) z[i + 1 + r] = z[i + 1 + r] - ts * v[r];
+        // T12 = -X T22
+        for (int e = tid; e < nent; e += blockDim.x) {
+            const int mg = e / (h * h), k = (e % (h * h)) / h, l = e % h;
+            const int a = mg * 2 * h;
+            cx<CT> u = zero;
+            for (int p = 0; p <= l; ++p) u = cmac(u, X[a + k][a + h + p], T[a + h + p][a + h + l]);
+            T[a + k][a + h + l] = zero - u;
+        }
         __syncthreads();
     }
-    for (int r = tid; r < n; r += 128) V[(size_t)j * ldv + r] = mkc<RT>((RT)z[r].x, (RT)z[r].y);
+    for (int e = tid; e < kWy * kWy; e += blockDim.x) Tf[(size_t)b * kWy * kWy + e] = T[e / kWy][e % kWy];
+}
+
+// NV eigenvectors per CTA (z in shared memory in the compute type CT), blocks from the last
+// to the first: t = Y^H z (a warp per reflector, KU reflectors at once for independent
+// accumulation chains, fixed-order warp sums), s = T t (eight lanes per entry, combined by a
+// shuffle tree), z -= Y s (a thread per row, KU partial sums).  Dynamic shared memory:
+// NV n entries.
+template <typename RT, typename CT, int NV>
+__global__ void __launch_bounds__(256)
+k_backtransform_wy(int n, int m, const cx<CT> *__restrict__ Hv, const cx<CT> *__restrict__ Tf,
+                   const RT *__restrict__ Z, cx<RT> *__restrict__ V, int ldv) {
+    constexpr int KU = NV >= 4 ? 1 : 4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<CT> *z = reinterpret_cast<cx<CT> *>(smraw);   // [NV][n]
+    __shared__ cx<CT> t[NV][kWy], sv[NV][kWy];
+    const int j0 = blockIdx.x * NV, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, nw = blockDim.x >> 5;
+    const cx<CT> zero = mkc<CT>(0.0, 0.0);
+    for (int e = tid; e < NV * n; e += blockDim.x) {
+        const int vv = e / n, r = e % n;
+        z[e] = (j0 + vv < m) ? mkc<CT>((CT)Z[(size_t)(j0 + vv) * n + r], CT(0.0)) : zero;
+    }
+    __syncthreads();
+    const int nblk = (n - 1 + kWy - 1) / kWy;
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int i0 = b * kWy, kb = min(kWy, n - 1 - i0);
+        // t_k = v_{i0+k}^H z, reflectors k = k0 + nw u (u < KU) together
+        for (int k0 = wp; k0 < kWy; k0 += nw * KU) {
+            cx<CT> acc[KU][NV];
+#pragma unroll
+            for (int u = 0; u < KU; ++u)
+#pragma unroll
+                for (int vv = 0; vv < NV; ++vv) acc[u][vv] = zero;
+            for (int r = i0 + 1 + lane; r < n; r += 32) {
+                cx<CT> zr[NV];
+#pragma unroll
+                for (int vv = 0; vv < NV; ++vv) zr[vv] = z[vv * n + r];
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+                    const int k = k0 + nw * u;
+                    if (k < kb && r > i0 + k) {   // v_{i0+k} lives on r >= i0 + k + 1
+                        const cx<CT> a = conjc(Hv[(size_t)(i0 + k) * n + r]);
+#pragma unroll
+                        for (int vv = 0; vv < NV; ++vv) acc[u][vv] = cmac(acc[u][vv], a, zr[vv]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int k = k0 + nw * u;
+#pragma unroll
+                for (int vv = 0; vv < NV; ++vv) {
+                    const CT re = warp_sum(acc[u][vv].x), im = warp_sum(acc[u][vv].y);
+                    if (lane == 0 && k < kWy) t[vv][k] = mkc<CT>(re, im);
+                }
+            }
+        }
+        __syncthreads();
+        // s = T t: entry (vv, k) from eight lanes, lane part p taking l = k + p, k + p + 8, ...
+        const cx<CT> *Tb = Tf + (size_t)b * kWy * kWy;
+        for (int e = tid; e < NV * kWy * 8; e += blockDim.x) {
+            const int p = e & 7, k = (e >> 3) % kWy, vv = (e >> 3) / kWy;
+            cx<CT> u = zero;
+            for (int l = k + p; l < kb; l += 8) u = cmac(u, Tb[k * kWy + l], t[vv][l]);
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                u.x += __shfl_xor_sync(0xffffffffu, u.x, o);
+                u.y += __shfl_xor_sync(0xffffffffu, u.y, o);
+            }
+            if (p == 0) sv[vv][k] = u;
+        }
+        __syncthreads();
+        // z -= Y s on the rows the block touches
+        for (int r = i0 + 1 + tid; r < n; r += blockDim.x) {
+            const int kmax = min(kb, r - i0);   // v_{i0+k}[r] is zero for r <= i0 + k
+            cx<CT> d[NV][KU];                   // KU partial sums per vector
+#pragma unroll
+            for (int vv = 0; vv < NV; ++vv)
+#pragma unroll
+                for (int q = 0; q < KU; ++q) d[vv][q] = zero;
+            for (int k = 0; k < kmax; k += KU) {
+#pragma unroll
+                for (int q = 0; q < KU; ++q) {
+                    if (k + q < kmax) {
+                        const cx<CT> a = Hv[(size_t)(i0 + k + q) * n + r];
+#pragma unroll
+                        for (int vv = 0; vv < NV; ++vv) d[vv][q] = cmac(d[vv][q], a, sv[vv][k + q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int vv = 0; vv < NV; ++vv) {
+                cx<CT> tot = d[vv][0];
+#pragma unroll
+                for (int q = 1; q < KU; ++q) tot = tot + d[vv][q];
+                z[vv * n + r] = z[vv * n + r] - tot;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < NV * n; e += blockDim.x) {
+        const int vv = e / n, r = e % n;
+        if (j0 + vv < m) V[(size_t)(j0 + vv) * ldv + r] = mkc<RT>((RT)z[e].x, (RT)z[e].y);
+    }
 }
 
 template <typename RT>
@@ -1146,6 +1437,78 @@ int allow_max_dyn_smem(const void *fn) {
     return LOBPCG_OK;
 }
 
+// The cluster-resident tridiagonalisation when the matrix fits one cluster's shared memory
+// (16 CTAs above n = 192, else 8) and the device can place such a cluster; done = false
+// leaves the reduction to the grid-wide kernels.
+template <typename RT, typename CT>
+int launch_tri_cluster(int n, const cx<RT> *A, int lda, cx<RT> *Hv, cx<RT> *taus, RT *dg, RT *eg, cudaStream_t s,
+                       bool &done) {
+    done = false;
+    const int CS = n > 192 ? 16 : 8;
+    const int nr = (n + CS - 1) / CS;
+    const size_t dsm = sizeof(cx<CT>) * ((size_t)nr * n + 7 * (size_t)n);
+    int dev = 0, smem_max = 0, cl_ok = 0;
+    LG_CUDA_TRY(cudaGetDevice(&dev));
+    LG_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    LG_CUDA_TRY(cudaDeviceGetAttribute(&cl_ok, cudaDevAttrClusterLaunch, dev));
+    const void *fn = (const void *)k_tri_cluster<RT, CT>;
+    cudaFuncAttributes fa;
+    LG_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    if (!cl_ok || dsm + fa.sharedSizeBytes > (size_t)smem_max) return LOBPCG_OK;
+    // the same (largest) limit from every caller: concurrent lanes launch this kernel with
+    // different sizes, and a per-call limit set by one would invalidate another's launch
+    LG_TRY(allow_max_dyn_smem(fn));
+    if (CS > 8) LG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(std::min(1024, 32 * nr));  // one warp per owned row
+    cfg.dynamicSmemBytes = dsm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess || ncl < 1) {
+        (void)cudaGetLastError();  // this cluster shape cannot be placed: not an error
+        return LOBPCG_OK;
+    }
+    LG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tri_cluster<RT, CT>, n, A, lda, Hv, taus, dg, eg));
+    LG_TRY(check_launch("tridiagonalisation (cluster)"));
+    done = true;
+    return LOBPCG_OK;
+}
+constexpr int kTriClusterMaxN = 416;
+constexpr int kWyChunks = 8;   // row chunks of the back-transformation's Gram partials
+
+// T factors, then the blocked application; NV eigenvectors per CTA, as many as keep about
+// 128 CTAs or more (each CTA reads every reflector once).
+template <typename RT, typename CT>
+int backtransform_wy(int n, int m, const cx<CT> *Hv, const cx<CT> *taus, cx<CT> *Tf, cx<CT> *Gp, const RT *Z,
+                     cx<RT> *V, int ldv, cudaStream_t s) {
+    const int nblk = (n - 1 + kWy - 1) / kWy;
+    const int nch = kWyChunks;
+    k_wy_gram<CT><<<dim3(nblk, nch), 256, 0, s>>>(n, nch, Hv, Gp);
+    LG_TRY(check_launch("back-transform Gram partials"));
+    k_wy_t<CT><<<nblk, 256, 0, s>>>(n, nch, Gp, taus, Tf);
+    LG_TRY(check_launch("back-transform T factors"));
+    const int NV = m >= 8 * 128 ? 8 : m >= 4 * 128 ? 4 : m >= 2 * 128 ? 2 : 1;
+    const size_t smem = sizeof(cx<CT>) * (size_t)NV * n;
+    const int grid = (m + NV - 1) / NV;
+    auto run = [&](auto kern) -> int {
+        if (smem > 48 * 1024) LG_TRY(allow_max_dyn_smem((const void *)kern));
+        kern<<<grid, 256, smem, s>>>(n, m, Hv, Tf, Z, V, ldv);
+        return check_launch("back-transform (compact WY)");
+    };
+    if (NV == 8) return run(k_backtransform_wy<RT, CT, 8>);
+    if (NV == 4) return run(k_backtransform_wy<RT, CT, 4>);
+    if (NV == 2) return run(k_backtransform_wy<RT, CT, 2>);
+    return run(k_backtransform_wy<RT, CT, 1>);
+}
+
 template <typename RT>
 int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT> *V, int ldv, cudaStream_t s) {
     if (n <= 0 || m <= 0) return LOBPCG_OK;
@@ -1161,6 +1524,8 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     const size_t o_wv = take(sizeof(cx<RT>) * 2 * (size_t)n);
     const size_t o_z = take(sizeof(RT) * (size_t)n * m);
     const size_t o_cnt = take(sizeof(unsigned int) * n);
+    const size_t o_tf = take(sizeof(cx<RT>) * (size_t)kWy * kWy * ((n + kWy - 1) / kWy));
+    const size_t o_gp = take(sizeof(cx<RT>) * (size_t)kWy * kWy * kWyChunks * ((n + kWy - 1) / kWy));
     LG_TRY(w.alloc->ensure(w.buf, off));
     char *base = reinterpret_cast<char *>(w.buf.p);
     cx<RT> *Hv = reinterpret_cast<cx<RT> *>(base + o_hv);
@@ -1171,10 +1536,22 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
     cx<RT> *wv = reinterpret_cast<cx<RT> *>(base + o_wv);
     RT *Z = reinterpret_cast<RT *>(base + o_z);
     unsigned int *cnt = reinterpret_cast<unsigned int *>(base + o_cnt);
+    cx<RT> *Tf = reinterpret_cast<cx<RT> *>(base + o_tf);
+    cx<RT> *Gp = reinterpret_cast<cx<RT> *>(base + o_gp);
     LG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * n, s));
     LG_CUDA_TRY(cudaMemsetAsync(taus, 0, sizeof(cx<RT>) * n, s));
     bool coop_done = false, hv_df = false;
-    if (n >= 2) {
+    if (n >= 2 && n <= kTriClusterMaxN) {
+        bool done = false, df = false;
+        if constexpr (std::is_same<RT, double>::value) {
+            df = w.df;  // the double-FP32 compute type, as in the grid-wide kernel below
+            if (df) LG_TRY((launch_tri_cluster<RT, df64>(n, A, lda, Hv, taus, dg, eg, s, done)));
+        }
+        if (!df) LG_TRY((launch_tri_cluster<RT, RT>(n, A, lda, Hv, taus, dg, eg, s, done)));
+        coop_done = done;
+        hv_df = done && df;
+    }
+    if (!coop_done && n >= 2) {
         // fused version: tiles resident in shared memory, one grid barrier per column; 16 x 16
         // tiles for small matrices (more SMs share a column's FP64 work), else 32 x 32
         int dev = 0, sms = 0, coop = 0, smem_max = 0;
@@ -1287,20 +1664,19 @@ int heev_lowest_t(EigWork &w, int n, int m, cx<RT> *A, int lda, RT *theta, cx<RT
         LG_TRY(allow_max_dyn_smem((const void *)k_inviter<RT>));
     k_inviter<RT><<<m, 32, smem_ii, s>>>(n, m, dg, eg, theta, Z);
     LG_TRY(check_launch("inverse iteration"));
-    const size_t smem = sizeof(cx<RT>) * (size_t)n;
-    if (smem > 48 * 1024) {
-        LG_TRY(allow_max_dyn_smem((const void *)k_backtransform<RT>));
+    if (n == 1) {
+        LG_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(cx<RT>) * ldv, Z, sizeof(RT), sizeof(RT), m, cudaMemcpyDeviceToDevice, s));
+        LG_CUDA_TRY(cudaMemset2DAsync(reinterpret_cast<char *>(V) + sizeof(RT), sizeof(cx<RT>) * ldv, 0, sizeof(RT), m, s));
+        return check_launch("back-transform (n = 1)");
     }
     if constexpr (sizeof(cx<RT>) == sizeof(cx<df64>)) {
-        if (hv_df) {
-            if (smem > 48 * 1024) LG_TRY(allow_max_dyn_smem((const void *)k_backtransform_df<RT>));
-            k_backtransform_df<RT><<<m, 128, smem, s>>>(n, m, reinterpret_cast<const cx<df64> *>(Hv),
-                                                        reinterpret_cast<const cx<df64> *>(taus), Z, V, ldv);
-            return check_launch("back-transform (double-FP32)");
-        }
+        if (hv_df)
+            return backtransform_wy<RT, df64>(n, m, reinterpret_cast<const cx<df64> *>(Hv),
+                                              reinterpret_cast<const cx<df64> *>(taus),
+                                              reinterpret_cast<cx<df64> *>(Tf), reinterpret_cast<cx<df64> *>(Gp), Z,
+                                              V, ldv, s);
     }
-    k_backtransform<RT><<<m, 32, smem, s>>>(n, m, Hv, taus, Z, V, ldv);
-    return check_launch("back-transform");
+    return backtransform_wy<RT, RT>(n, m, Hv, taus, Tf, Gp, Z, V, ldv, s);
 }
 
 template <typename RT>

@@ -203,7 +203,7 @@ def _herm(rng, n):
     return A + A.conj().T
 
 
-@pytest.mark.parametrize("n", [1, 2, 5, 33, 48, 192, 257])
+@pytest.mark.parametrize("n", [1, 2, 5, 33, 48, 192, 193, 257, 384, 416, 417])
 def test_heev(n):
     import torch
     import paper_0707_3405_gb300 as lg
@@ -234,7 +234,7 @@ def test_heev_degenerate_clusters():
     assert np.abs(V.conj().T @ V - np.eye(n)).max() < 1e-12
 
 
-@pytest.mark.parametrize("n,m", [(3, 1), (48, 16), (192, 64), (384, 128)])
+@pytest.mark.parametrize("n,m", [(3, 1), (48, 16), (192, 64), (384, 128), (416, 100), (640, 200)])
 @pytest.mark.parametrize("df32", [False, True])
 def test_rayleigh_ritz_generalized(n, m, df32):
     """FP64 Rayleigh-Ritz against scipy's generalized eigh; df32 = the double-FP32 variant
