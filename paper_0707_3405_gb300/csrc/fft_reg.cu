@@ -3,13 +3,15 @@
 //
 // Same three passes as the shared-memory engine, with these differences:
 //   * A length-N line is held in the registers of T adjacent lanes of one warp
-//     (T = 1, 2 or 4; E = N / T points per lane).  With the line split as
+//     (T = 2 or 4; E = N / T points per lane).  With the line split as
 //     x[t + T e], each lane first runs an E-point DFT over e entirely in
 //     registers (compile-time mixed radix 4/8/3/5/2), multiplies by the
 //     W_N^{t k} twiddles, then the T lanes of the line swap values with warp
 //     shuffles and finish with T-point DFTs.  The result sits in "block
-//     layout": lane t holds outputs (t E/T + i) + E k2.  The reverse path
-//     (block layout in, strided layout out) runs the same steps backwards.
+//     layout": lane t holds outputs (t BK + i) + E k2, BK = ceil(E / T); where
+//     T does not divide E (N = 72, 120 on four lanes) the last lane's trailing
+//     slots are padding.  The reverse path (block layout in, strided layout
+//     out) runs the same steps backwards.
 //     No shared memory and no barrier inside a line FFT.
 //   * The half-box scratch is laid out T2[b][px][y][z] (z fastest) and the
 //     potential V(r) / N^3 as [y][x][z], so that the 32 / T lines of a warp
@@ -46,11 +48,18 @@ constexpr int kMaxDevices = 64;
 
 template <int N>
 struct RP {
-    static constexpr int T = (N % 16 == 0) ? 4 : 2;
+    // four lanes per line from N = 64 up (N a multiple of 4), else two
+    static constexpr int T = (N % 16 == 0 || (N % 4 == 0 && N >= 64)) ? 4 : 2;
+    static constexpr int E = N / T;                 // points per lane (strided layout)
+    static constexpr int BK = (E + T - 1) / T;      // block-layout slots per output group
+    static constexpr int VS = T * BK;               // register slots per lane (>= E)
     static constexpr int OFF = tw_off(N);
     // resident CTAs per SM the register budget is sized for (fewer for long per-lane lines)
-    static constexpr int MINB = (N / T <= 24) ? 4 : (N / T <= 40) ? 3 : 2;
-    static_assert(N % (T * T) == 0, "a line must split into T blocks of E / T points");
+    static constexpr int MINB = (E <= 24) ? 4 : (E <= 40) ? 3 : 2;
+    static_assert(N % T == 0, "a line must split over its T lanes");
+    static_assert(T == 4 || E % T == 0, "two-lane lines split into two blocks of E / 2 points");
+    // block-layout slot i of lane t holds output group t BK + i, which exists for t BK + i < E
+    static __device__ __forceinline__ bool slot_ok(int t, int i) { return t * BK + i < E; }
 };
 
 __constant__ float2 c_tw[kTwTotal];
@@ -225,10 +234,12 @@ __device__ __forceinline__ void xpose4(C (&a)[4], int t) {
     }
 }
 
-// Strided -> block: in v[e] = x[t + T e]; out v[i + (E/T) k2] = X[(t E/T + i) + E k2].
+// Strided -> block: in v[e] = x[t + T e] (e < E); out v[i + BK k2] = X[(t BK + i) + E k2] for the
+// slots with t BK + i < E (BK = ceil(E / T); with four lanes and E not a multiple of 4 the last
+// lane's trailing slots are padding, exchanged as zeros and never stored).
 template <int N, bool INV>
 __device__ __forceinline__ void s2b(C *v, int t) {
-    constexpr int T = RP<N>::T, E = N / T, BK = E / T;
+    constexpr int T = RP<N>::T, E = RP<N>::E, BK = RP<N>::BK, VS = RP<N>::VS;
     RDFT<E, N, INV>::run(v);
     if constexpr (T == 2) {
 #pragma unroll
@@ -248,24 +259,27 @@ __device__ __forceinline__ void s2b(C *v, int t) {
     } else if constexpr (T == 4) {
 #pragma unroll
         for (int k = 1; k < E; ++k) v[k] = v[k] * twc<N, INV>((t * k) % N);
-        C out[E];
+        const C zero = mkc<float>(0.f, 0.f);
+        C out[VS];
 #pragma unroll
         for (int i = 0; i < BK; ++i) {
-            C w[4] = {v[i], v[BK + i], v[2 * BK + i], v[3 * BK + i]};
+            C w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = (q * BK + i < E) ? v[q * BK + i] : zero;
             xpose4(w, t);   // w[s] = lane s's v[t BK + i]
             Base<4, INV>::run(w);
 #pragma unroll
             for (int k2 = 0; k2 < 4; ++k2) out[i + BK * k2] = w[k2];
         }
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = out[e];
+        for (int e = 0; e < VS; ++e) v[e] = out[e];
     }
 }
 
-// Block -> strided: in v[i + (E/T) x2] = x[(t E/T + i) + E x2]; out v[e] = X[t + T e].
+// Block -> strided: in v[i + BK x2] = x[(t BK + i) + E x2] (valid slots); out v[e] = X[t + T e].
 template <int N, bool INV>
 __device__ __forceinline__ void b2s(C *v, int t) {
-    constexpr int T = RP<N>::T, E = N / T, BK = E / T;
+    constexpr int T = RP<N>::T, E = RP<N>::E, BK = RP<N>::BK;
     if constexpr (T == 2) {
         C out[E];
 #pragma unroll
@@ -286,12 +300,13 @@ __device__ __forceinline__ void b2s(C *v, int t) {
         for (int i = 0; i < BK; ++i) {
             C w[4] = {v[i], v[i + BK], v[i + 2 * BK], v[i + 3 * BK]};
             Base<4, INV>::run(w);
-            const int x1 = t * BK + i;
+            const int x1 = t * BK + i;   // a padding slot's twiddle index stays inside [0, N)
 #pragma unroll
             for (int s = 1; s < 4; ++s) w[s] = w[s] * twc<N, INV>((x1 * s) % N);
             xpose4(w, t);   // w[s] = lane s's w[t]
 #pragma unroll
-            for (int s = 0; s < 4; ++s) out[s * BK + i] = w[s];
+            for (int s = 0; s < 4; ++s)
+                if (s * BK + i < E) out[s * BK + i] = w[s];
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = out[e];
@@ -308,7 +323,7 @@ constexpr int kWarps = 4;  // warps per CTA
 template <int N>
 __global__ void __launch_bounds__(32 * kWarps, RP<N>::MINB)
 k_rb(C *__restrict__ T2, int Px, int nx0m, const float *__restrict__ vr) {
-    constexpr int T = RP<N>::T, E = N / T, BK = E / T, LPW = 32 / T;
+    constexpr int T = RP<N>::T, E = RP<N>::E, BK = RP<N>::BK, VS = RP<N>::VS, LPW = 32 / T;
     constexpr int NZC = (N + LPW - 1) / LPW;
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -319,7 +334,7 @@ k_rb(C *__restrict__ T2, int Px, int nx0m, const float *__restrict__ vr) {
     const bool ok = z < N;
     const size_t NN = (size_t)N * N;
     C *base = T2 + (size_t)blockIdx.y * Px * NN + (size_t)y * N + z;
-    C v[E];
+    C v[VS];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         int px = t + T * e - nx0m;
@@ -333,7 +348,7 @@ k_rb(C *__restrict__ T2, int Px, int nx0m, const float *__restrict__ vr) {
 #pragma unroll
         for (int i = 0; i < BK; ++i) {
             const int x = t * BK + i + E * k2;
-            v[i + BK * k2] = (ok ? vy[(size_t)x * N] : 0.f) * v[i + BK * k2];
+            v[i + BK * k2] = (ok && RP<N>::slot_ok(t, i) ? vy[(size_t)x * N] : 0.f) * v[i + BK * k2];
         }
     b2s<N, false>(v, t);
     if (!ok) return;
@@ -354,11 +369,11 @@ template <int N>
 __global__ void __launch_bounds__(32 * kWarps, RP<N>::MINB)
 k_rd(const C *__restrict__ T2, int Px, int nx0m, int nbb, const float *__restrict__ f, double scale,
      double *__restrict__ rho) {
-    constexpr int T = RP<N>::T, E = N / T, BK = E / T, LPW = 32 / T;
+    constexpr int T = RP<N>::T, E = RP<N>::E, BK = RP<N>::BK, VS = RP<N>::VS, LPW = 32 / T;
     constexpr int NZC = (N + LPW - 1) / LPW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float *acc = reinterpret_cast<float *>(smem_raw) + (size_t)wid * E * 32;   // [e][lane]
+    float *acc = reinterpret_cast<float *>(smem_raw) + (size_t)wid * VS * 32;  // [slot][lane]
     const int w = blockIdx.x * kWarps + wid;
     const int y = w / NZC, zc = w - y * NZC;
     if (y >= N) return;
@@ -367,10 +382,10 @@ k_rd(const C *__restrict__ T2, int Px, int nx0m, int nbb, const float *__restric
     const bool ok = z < N;
     const size_t NN = (size_t)N * N;
 #pragma unroll
-    for (int e = 0; e < E; ++e) acc[e * 32 + lane] = 0.f;
+    for (int e = 0; e < VS; ++e) acc[e * 32 + lane] = 0.f;
     for (int b = 0; b < nbb; ++b) {
         const C *base = T2 + (size_t)b * Px * NN + (size_t)y * N + z;
-        C v[E];
+        C v[VS];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             int px = t + T * e - nx0m;
@@ -380,13 +395,14 @@ k_rd(const C *__restrict__ T2, int Px, int nx0m, int nbb, const float *__restric
         s2b<N, true>(v, t);
         const float fb = f[b];
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc[e * 32 + lane] = fmaf(fb, v[e].x * v[e].x + v[e].y * v[e].y, acc[e * 32 + lane]);
+        for (int e = 0; e < VS; ++e) acc[e * 32 + lane] = fmaf(fb, v[e].x * v[e].x + v[e].y * v[e].y, acc[e * 32 + lane]);
     }
     if (!ok) return;
 #pragma unroll
     for (int k2 = 0; k2 < T; ++k2)
 #pragma unroll
         for (int i = 0; i < BK; ++i) {
+            if (!RP<N>::slot_ok(t, i)) continue;
             const int x = t * BK + i + E * k2;
             rho[((size_t)x * N + y) * N + z] += scale * (double)acc[(i + BK * k2) * 32 + lane];
         }
@@ -400,7 +416,7 @@ template <int N>
 __global__ void __launch_bounds__(32 * kWarps, RP<N>::MINB)
 k_ra(const C *__restrict__ X, int ldx, C *__restrict__ T2, int Px, int Py, int ny0m,
      const int *__restrict__ plane_begin, const int2 *__restrict__ yrange, const int *__restrict__ gmap) {
-    constexpr int T = RP<N>::T, E = N / T, BK = E / T, LPW = 32 / T, P = N + 2;
+    constexpr int T = RP<N>::T, E = RP<N>::E, BK = RP<N>::BK, VS = RP<N>::VS, LPW = 32 / T, P = N + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);
     const int px = blockIdx.x, b = blockIdx.y;
@@ -424,7 +440,7 @@ k_ra(const C *__restrict__ X, int ldx, C *__restrict__ T2, int Px, int Py, int n
         const int r = yr.x + r0 + l;
         const bool ok = r0 + l < nrows;
         C *row = S + (ok ? r : yr.x) * P;
-        C v[E];
+        C v[VS];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = ok ? row[t + T * e] : zero;
         s2b<N, true>(v, t);
@@ -433,7 +449,8 @@ k_ra(const C *__restrict__ X, int ldx, C *__restrict__ T2, int Px, int Py, int n
 #pragma unroll
             for (int k2 = 0; k2 < T; ++k2)
 #pragma unroll
-                for (int i = 0; i < BK; ++i) row[t * BK + i + E * k2] = v[i + BK * k2];
+                for (int i = 0; i < BK; ++i)
+                    if (RP<N>::slot_ok(t, i)) row[t * BK + i + E * k2] = v[i + BK * k2];
         }
     }
     __syncthreads();
@@ -443,7 +460,7 @@ k_ra(const C *__restrict__ X, int ldx, C *__restrict__ T2, int Px, int Py, int n
     for (int zc = wid; zc < NZC; zc += kWarps) {
         const int z = zc * LPW + l;
         const bool ok = z < N;
-        C v[E];
+        C v[VS];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             int py = t + T * e - ny0m;
@@ -455,7 +472,8 @@ k_ra(const C *__restrict__ X, int ldx, C *__restrict__ T2, int Px, int Py, int n
 #pragma unroll
             for (int k2 = 0; k2 < T; ++k2)
 #pragma unroll
-                for (int i = 0; i < BK; ++i) out[(size_t)(t * BK + i + E * k2) * N + z] = v[i + BK * k2];
+                for (int i = 0; i < BK; ++i)
+                    if (RP<N>::slot_ok(t, i)) out[(size_t)(t * BK + i + E * k2) * N + z] = v[i + BK * k2];
         }
     }
 }
@@ -469,7 +487,7 @@ __global__ void __launch_bounds__(32 * kWarps, RP<N>::MINB)
 k_rc(const C *__restrict__ T2, C *__restrict__ Y, int ldy, const C *__restrict__ X, int ldx,
      const float *__restrict__ kin, int Px, int Py, int ny0m, const int *__restrict__ plane_begin,
      const int2 *__restrict__ yrange, const int *__restrict__ gmap) {
-    constexpr int T = RP<N>::T, E = N / T, BK = E / T, LPW = 32 / T, P = N + 2;
+    constexpr int T = RP<N>::T, E = RP<N>::E, BK = RP<N>::BK, VS = RP<N>::VS, LPW = 32 / T, P = N + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);
     const int px = blockIdx.x, b = blockIdx.y;
@@ -481,7 +499,7 @@ k_rc(const C *__restrict__ T2, C *__restrict__ Y, int ldy, const C *__restrict__
     for (int zc = wid; zc < NZC; zc += kWarps) {
         const int z = zc * LPW + l;
         const bool ok = z < N;
-        C v[E];
+        C v[VS];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = ok ? in[(size_t)(t + T * e) * N + z] : zero;
         s2b<N, false>(v, t);
@@ -490,6 +508,7 @@ k_rc(const C *__restrict__ T2, C *__restrict__ Y, int ldy, const C *__restrict__
             for (int k2 = 0; k2 < T; ++k2)
 #pragma unroll
                 for (int i = 0; i < BK; ++i) {
+                    if (!RP<N>::slot_ok(t, i)) continue;
                     int py = t * BK + i + E * k2 - ny0m;
                     py += (py < 0) ? N : 0;
                     if (py < Py) S[py * P + z] = v[i + BK * k2];
@@ -503,7 +522,7 @@ k_rc(const C *__restrict__ T2, C *__restrict__ Y, int ldy, const C *__restrict__
         const int r = yr.x + r0 + l;
         const bool ok = r0 + l < nrows;
         C *row = S + (ok ? r : yr.x) * P;
-        C v[E];
+        C v[VS];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = ok ? row[t + T * e] : zero;
         s2b<N, false>(v, t);
@@ -512,7 +531,8 @@ k_rc(const C *__restrict__ T2, C *__restrict__ Y, int ldy, const C *__restrict__
 #pragma unroll
             for (int k2 = 0; k2 < T; ++k2)
 #pragma unroll
-                for (int i = 0; i < BK; ++i) row[t * BK + i + E * k2] = v[i + BK * k2];
+                for (int i = 0; i < BK; ++i)
+                    if (RP<N>::slot_ok(t, i)) row[t * BK + i + E * k2] = v[i + BK * k2];
         }
     }
     __syncthreads();
@@ -574,10 +594,10 @@ int run_reg(const FFTGeom &g, const C *X, int ldx, C *Y, int ldy, int nb, const 
 template <int N>
 int run_reg_density(const FFTGeom &g, const C *X, int ldx, int nb, const float *f, double scale, double *rho, C *T2,
                     int nbatch, cudaStream_t s) {
-    constexpr int LPW = 32 / RP<N>::T, E = N / RP<N>::T;
+    constexpr int LPW = 32 / RP<N>::T, VS = RP<N>::VS;
     constexpr int NZC = (N + LPW - 1) / LPW;
     const size_t sm = tile_bytes(N, g.Py);
-    const size_t smd = sizeof(float) * (size_t)E * 32 * kWarps;
+    const size_t smd = sizeof(float) * (size_t)VS * 32 * kWarps;
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         int dev = 0, smem_max = 0;
