@@ -427,10 +427,23 @@ k_ra(const C *__restrict__ X, int ldx, C *__restrict__ T2, int Px, int Py, int n
     __syncthreads();
     const C *Xb = X + (size_t)b * ldx;
     const int g0 = plane_begin[px], g1 = plane_begin[px + 1];
-    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-        const int gm = gmap[g];
-        const int py = gm / N;
-        S[py * P + (gm - py * N)] = Xb[g];
+    // eight coefficients per thread in flight (the loads are independent)
+    constexpr int U = 8;
+    for (int gb = g0 + threadIdx.x; gb < g1; gb += U * blockDim.x) {
+        int gm[U];
+        C xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = gb + u * blockDim.x;
+            gm[u] = g < g1 ? gmap[g] : -1;
+            xv[u] = g < g1 ? Xb[g] : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (gm[u] >= 0) {
+                const int py = gm[u] / N;
+                S[py * P + (gm[u] - py * N)] = xv[u];
+            }
     }
     __syncthreads();
     // inverse z-FFT of the occupied rows, in place in the tile
@@ -539,12 +552,28 @@ k_rc(const C *__restrict__ T2, C *__restrict__ Y, int ldy, const C *__restrict__
     const int g0 = plane_begin[px], g1 = plane_begin[px + 1];
     C *Yb = Y + (size_t)b * ldy;
     const C *Xb = X + (size_t)b * ldx;
-    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-        const int gm = gmap[g];
-        const int py = gm / N;
-        C v = S[py * P + (gm - py * N)];
-        if (kin) v = v + kin[g] * Xb[g];
-        Yb[g] = v;
+    // eight coefficients per thread in flight (the loads are independent)
+    constexpr int U = 8;
+    for (int gb = g0 + threadIdx.x; gb < g1; gb += U * blockDim.x) {
+        int gm[U];
+        C xv[U];
+        float kv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = gb + u * blockDim.x;
+            const bool in = g < g1;
+            gm[u] = in ? gmap[g] : 0;
+            xv[u] = (in && kin) ? Xb[g] : zero;
+            kv[u] = (in && kin) ? kin[g] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = gb + u * blockDim.x;
+            if (g < g1) {
+                const int py = gm[u] / N;
+                Yb[g] = S[py * P + (gm[u] - py * N)] + kv[u] * xv[u];
+            }
+        }
     }
 }
 
