@@ -72,3 +72,17 @@ def test_solve_mp72x10_all_kpoints_vs_oracle():
             assert checks.orthonormality_error(Xn) < 1e-10
             if k in refs:
                 assert np.abs(res.eig[k] - refs[k]).max() < 1e-9, (k, np.abs(res.eig[k] - refs[k]).max())
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_solve_gamma120_all_bands_vs_oracle(real):
+    """The 120^3 Gamma cell the mixed-vs-FP64 comparison is made on: 1024 bands in blocks of
+    128 plus 128 buffer bands, mixed schedule, complex orbitals and the real-orbital form."""
+    w = synth.make_workload("gamma120")
+    ref = np.loadtxt(os.path.join(GOLDEN, "gamma120_eig.txt"))
+    with make_solver(w, block_size=128, nline=4, max_sweeps=30, precision="mixed", tol=1e-8, nbuf=128,
+                     gamma_real=real) as s:
+        X = _start(w, s)
+        res = s.solve([X])
+        assert res.status == 0, res.stats
+        _check_all(w, s, 0, X, res.eig[0], res.resid[0], ref, 1e-10)
