@@ -509,14 +509,20 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
     return out
 
 
+# DRAM bytes per launch (read + write) from one ncu capture, by kernel entry and shape; valid only
+# while the kernel is unchanged since the capture (the summary names the command).
+TRAFFIC = {("fp64class_gemm", (113081, 1152, 1152)): (1.905e10, "profiles/fp64class_tensor_gemm_traffic_gamma120.md")}
+
+
 def roofline_of(kr, dominant=DOMINANT):
     """The contract's roofline object: the dominant kernel's CUDA-event rate against its peak."""
     d = kr.get(dominant, {})
     if "achieved" not in d:
         return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "kernel": dominant, "error": d.get("error", "not measured")}
+    traffic, tsrc = TRAFFIC.get((dominant, tuple(d["shape"])), (None, None))
     return {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-            "frac": d["frac"], "traffic": None, "kernel": d["kernel"], "shape": d["shape"],
+            "frac": d["frac"], "traffic": traffic, "traffic_source": tsrc, "kernel": d["kernel"], "shape": d["shape"],
             "work_per_launch": d["work_per_launch"], "peak_source": d["peak_source"] + " (of measured)"
             if "MEASURED" in d["peak_source"] else d["peak_source"]}
 
