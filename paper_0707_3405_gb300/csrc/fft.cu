@@ -186,6 +186,10 @@ template <typename CT>
 constexpr int vpt() { return sizeof(CT) == 8 && !std::is_same<CT, double>::value ? 4 : 8; }
 template <typename CT>
 constexpr bool radix8() { return vpt<CT>() == 8; }
+// Threads of the plane passes (A, C): their shared plane tile allows one block per SM, so the
+// double-FP32 passes, which fit 128 registers a thread, run 512 threads to keep 16 warps there.
+template <typename CT>
+constexpr int plane_threads() { return vpt<CT>() == 4 ? 512 : kThreads; }
 
 // In-place FFT of `nlines` lines (line stride ls, element stride es) by the whole block.
 // sg = -1: forward (e^{-i...}); sg = +1: inverse without 1/N.
@@ -224,7 +228,7 @@ __device__ __forceinline__ cx<CT> to_ct(cx<R> v) {
 }
 
 template <typename R, typename CT = R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int Py, int ny0m,
          const int *__restrict__ plane_begin, const int2 *__restrict__ yrange, const int *__restrict__ gmap,
          const cx<R> *__restrict__ twg, int zc_max) {
@@ -305,7 +309,7 @@ k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__res
 }
 
 template <typename R, typename CT = R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_c(const cx<CT> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx<R> *__restrict__ X, int ldx,
          const R *__restrict__ kin, FFTPlan plan, int Px, int Py, int ny0m, const int *__restrict__ plane_begin,
          const int2 *__restrict__ yrange, const int *__restrict__ gmap, const cx<R> *__restrict__ twg,
@@ -469,12 +473,12 @@ int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, c
         const int nbb = std::min(nbatch, nb - b0);
         const cx<R> *Xb = X + (size_t)b0 * ldx;
         cx<R> *Yb = Y + (size_t)b0 * ldy;
-        k_pass_a<R, CT><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
+        k_pass_a<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
                                                              g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass A"));
         k_pass_b<R, CT><<<dim3((N + yc - 1) / yc, N, nbb), kThreads, sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
         LG_TRY(check_launch("fft pass B"));
-        k_pass_c<R, CT><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
+        k_pass_c<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
                                                              g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass C"));
     }
@@ -503,7 +507,7 @@ int density_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
     const int nx0m = ((g.nx0 % N) + N) % N;
     for (int b0 = 0; b0 < nb; b0 += nbatch) {
         const int nbb = std::min(nbatch, nb - b0);
-        k_pass_a<R, CT><<<dim3(g.Px, nbb), kThreads, sm_ac, s>>>(X + (size_t)b0 * ldx, ldx, T2, plan, g.Px, g.Py,
+        k_pass_a<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(X + (size_t)b0 * ldx, ldx, T2, plan, g.Px, g.Py,
                                                              ny0m, g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("density: fft pass A"));
         k_pass_d<R, CT><<<dim3((N + yc - 1) / yc, N), kThreads, sm_d, s>>>(T2, plan, g.Px, nx0m, tw, yc, nbb,
