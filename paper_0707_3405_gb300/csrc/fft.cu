@@ -188,6 +188,7 @@ template <typename CT>
 constexpr bool radix8() { return vpt<CT>() == 8; }
 // Threads of the plane passes (A, C): their shared plane tile allows one block per SM, so the
 // double-FP32 passes, which fit 128 registers a thread, run 512 threads to keep 16 warps there.
+// Pass B likewise: 512 threads take its 16 lines in one group (half the stage barriers).
 template <typename CT>
 constexpr int plane_threads() { return vpt<CT>() == 4 ? 512 : kThreads; }
 
@@ -269,7 +270,7 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan 
 }
 
 template <typename R, typename CT = R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__restrict__ vt,
          const cx<R> *__restrict__ twg, int yc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -476,7 +477,7 @@ int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, c
         k_pass_a<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
                                                              g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass A"));
-        k_pass_b<R, CT><<<dim3((N + yc - 1) / yc, N, nbb), kThreads, sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
+        k_pass_b<R, CT><<<dim3((N + yc - 1) / yc, N, nbb), plane_threads<CT>(), sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
         LG_TRY(check_launch("fft pass B"));
         k_pass_c<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
                                                              g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
