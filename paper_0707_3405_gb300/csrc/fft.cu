@@ -133,10 +133,14 @@ struct DFT<R, 8> {
 
 // One Stockham stage over `nlines` lines (all butterflies held in registers
 // between the two barriers, so the stage can run in place).
-template <typename R, int RDX, int VPT>
-__device__ __forceinline__ void fft_stage(cx<R> *buf, int nlines, int ls, int es, int N, int Ns,
+// NC > 0: the line length and the stage's Ns are the compile-time NC and NSC (constant index
+// arithmetic); NC = 0: the runtime N and Ns.
+template <typename R, int RDX, int VPT, int NC = 0, int NSC = 1>
+__device__ __forceinline__ void fft_stage(cx<R> *buf, int nlines, int ls, int es, int N_, int Ns_,
                                           const cx<R> *tw, int sg) {
     constexpr int NB = (VPT + RDX - 1) / RDX;
+    const int N = NC ? NC : N_;
+    const int Ns = NC ? NSC : Ns_;
     const int bpl = N / RDX;
     const int total = nlines * bpl;
     const int tstride = N / (Ns * RDX);
@@ -192,12 +196,46 @@ constexpr bool radix8() { return vpt<CT>() == 8; }
 template <typename CT>
 constexpr int plane_threads() { return vpt<CT>() == 4 ? 512 : kThreads; }
 
+// Radix of stage s of the plan make_fft_plan builds for N (0 past the last stage).
+constexpr int plan_radix(int N, bool allow8, int s) {
+    const int pref[5] = {8, 4, 2, 5, 3};
+    int r = N, k = 0;
+    for (int i = 0; i < 5; ++i) {
+        const int f = pref[i];
+        if (f == 8 && !allow8) continue;
+        while (r % f == 0) {
+            if (k == s) return f;
+            r /= f;
+            ++k;
+        }
+    }
+    return 0;
+}
+
+// The stages of a compile-time plan for line length NC, from stage S on (Ns = NS).
+template <typename R, int NC, int S = 0, int NS = 1>
+__device__ __forceinline__ void fft_stages_c(cx<R> *b, int nl, int ls, int es, const cx<R> *tw, int sg) {
+    constexpr int RDX = plan_radix(NC, radix8<R>(), S);
+    if constexpr (RDX != 0) {
+        fft_stage<R, RDX, vpt<R>(), NC, NS>(b, nl, ls, es, NC, NS, tw, sg);
+        fft_stages_c<R, NC, S + 1, NS * RDX>(b, nl, ls, es, tw, sg);
+    }
+}
+
 // In-place FFT of `nlines` lines (line stride ls, element stride es) by the whole block.
-// sg = -1: forward (e^{-i...}); sg = +1: inverse without 1/N.
-template <typename R>
+// sg = -1: forward (e^{-i...}); sg = +1: inverse without 1/N.  NC > 0: the plan of a line of
+// NC points unrolled at compile time (plan.N must equal NC); NC = 0: the runtime plan.
+template <typename R, int NC = 0>
 __device__ void fft_lines(cx<R> *buf, int nlines, int ls, int es, const FFTPlan &plan, const cx<R> *tw, int sg) {
     constexpr int kVPT = vpt<R>();
-    const int N = plan.N;
+    const int N = NC ? NC : plan.N;
+    if constexpr (NC > 0) {
+        int lpg = (int)(blockDim.x * kVPT) / N;
+        if (lpg < 1) lpg = 1;
+        for (int l0 = 0; l0 < nlines; l0 += lpg)
+            fft_stages_c<R, NC>(buf + l0 * ls, min(lpg, nlines - l0), ls, es, tw, sg);
+        return;
+    }
     int lpg = (int)(blockDim.x * kVPT) / N;
     if (lpg < 1) lpg = 1;
     for (int l0 = 0; l0 < nlines; l0 += lpg) {
@@ -228,13 +266,13 @@ __device__ __forceinline__ cx<CT> to_ct(cx<R> v) {
     else return mkc<CT>((CT)v.x, (CT)v.y);
 }
 
-template <typename R, typename CT = R>
+template <typename R, typename CT = R, int NC = 0>
 __global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int Py, int ny0m,
          const int *__restrict__ plane_begin, const int2 *__restrict__ yrange, const int *__restrict__ gmap,
          const cx<R> *__restrict__ twg, int zc_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = plan.N;
+    const int N = NC ? NC : plan.N;
     cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
     cx<CT> *A = tw + N;
     cx<CT> *L = A + Py * N;
@@ -249,7 +287,7 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan 
     for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) A[gmap[g]] = to_ct<CT>(Xb[g]);
     __syncthreads();
     const int2 yr = yrange[px];
-    fft_lines<CT>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, 1);
+    fft_lines<CT, NC>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, 1);
     cx<CT> *out = T2 + ((size_t)b * Px + px) * (size_t)N * N;  // [z][y]
     for (int z0 = 0; z0 < N; z0 += zc_max) {
         const int nz = min(zc_max, N - z0);
@@ -260,7 +298,7 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan 
             L[zc * lsL + iy] = (py < Py) ? A[py * N + z0 + zc] : zero;
         }
         __syncthreads();
-        fft_lines<CT>(L, nz, lsL, 1, plan, tw, 1);
+        fft_lines<CT, NC>(L, nz, lsL, 1, plan, tw, 1);
         for (int i = threadIdx.x; i < nz * N; i += blockDim.x) {
             const int zc = i / N, iy = i - zc * N;
             out[(size_t)(z0 + zc) * N + iy] = L[zc * lsL + iy];
@@ -269,12 +307,12 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan 
     }
 }
 
-template <typename R, typename CT = R>
+template <typename R, typename CT = R, int NC = 0>
 __global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__restrict__ vt,
          const cx<R> *__restrict__ twg, int yc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = plan.N;
+    const int N = NC ? NC : plan.N;
     cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
     cx<CT> *L = tw + N;
     const int lsL = N + 1;
@@ -293,14 +331,14 @@ k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__res
         L[yy * lsL + ix] = base[(size_t)px * NN + yy];
     }
     __syncthreads();
-    fft_lines<CT>(L, ny, lsL, 1, plan, tw, 1);
+    fft_lines<CT, NC>(L, ny, lsL, 1, plan, tw, 1);
     const R *vz = vt + (size_t)z * NN + y0;
     for (int i = threadIdx.x; i < ny * N; i += blockDim.x) {
         const int ix = i / ny, yy = i - ix * ny;
         L[yy * lsL + ix] = (CT)vz[(size_t)ix * N + yy] * L[yy * lsL + ix];
     }
     __syncthreads();
-    fft_lines<CT>(L, ny, lsL, 1, plan, tw, -1);
+    fft_lines<CT, NC>(L, ny, lsL, 1, plan, tw, -1);
     for (int i = threadIdx.x; i < Px * ny; i += blockDim.x) {
         const int px = i / ny, yy = i - px * ny;
         int ix = nx0m + px;
@@ -309,14 +347,14 @@ k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__res
     }
 }
 
-template <typename R, typename CT = R>
+template <typename R, typename CT = R, int NC = 0>
 __global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_c(const cx<CT> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx<R> *__restrict__ X, int ldx,
          const R *__restrict__ kin, FFTPlan plan, int Px, int Py, int ny0m, const int *__restrict__ plane_begin,
          const int2 *__restrict__ yrange, const int *__restrict__ gmap, const cx<R> *__restrict__ twg,
          int zc_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = plan.N;
+    const int N = NC ? NC : plan.N;
     cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
     cx<CT> *A = tw + N;
     cx<CT> *L = A + Py * N;
@@ -332,7 +370,7 @@ k_pass_c(const cx<CT> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx
             L[zc * lsL + iy] = in[(size_t)(z0 + zc) * N + iy];
         }
         __syncthreads();
-        fft_lines<CT>(L, nz, lsL, 1, plan, tw, -1);
+        fft_lines<CT, NC>(L, nz, lsL, 1, plan, tw, -1);
         for (int i = threadIdx.x; i < nz * Py; i += blockDim.x) {
             const int zc = i % nz, py = i / nz;
             int iy = py + ny0m;
@@ -342,7 +380,7 @@ k_pass_c(const cx<CT> *__restrict__ T2, cx<R> *__restrict__ Y, int ldy, const cx
         __syncthreads();
     }
     const int2 yr = yrange[px];
-    fft_lines<CT>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, -1);
+    fft_lines<CT, NC>(A + yr.x * N, yr.y - yr.x + 1, N, 1, plan, tw, -1);
     const int g0 = plane_begin[px], g1 = plane_begin[px + 1];
     cx<R> *Yb = Y + (size_t)b * ldy;
     const cx<R> *Xb = X + (size_t)b * ldx;
@@ -450,10 +488,11 @@ size_t fft_smem_need(const FFTGeom &g) {
 
 namespace {
 
-// The three passes over batches of bands; CT is the compute type (see k_pass_a).
-template <typename R, typename CT>
-int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
-               const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
+// The three passes over batches of bands; CT is the compute type (see k_pass_a); NC > 0: the
+// kernels compiled for that grid edge.
+template <typename R, typename CT, int NC>
+int fft_passes_n(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
+                 const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
     const int N = g.N;
     const int zc = pick_zc<R>(g);
     if (zc == 0) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT grid too large for shared memory");
@@ -463,9 +502,9 @@ int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, c
     static std::atomic<bool> attr_set{false};
     if (!attr_set.load()) {
         const int lim = max_dyn_smem();
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_a<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_b<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_c<R, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_a<R, CT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_b<R, CT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        LG_CUDA_TRY(cudaFuncSetAttribute(k_pass_c<R, CT, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         attr_set.store(true);
     }
     const int ny0m = ((g.ny0 % N) + N) % N;
@@ -474,16 +513,32 @@ int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, c
         const int nbb = std::min(nbatch, nb - b0);
         const cx<R> *Xb = X + (size_t)b0 * ldx;
         cx<R> *Yb = Y + (size_t)b0 * ldy;
-        k_pass_a<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
+        k_pass_a<R, CT, NC><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
                                                              g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass A"));
-        k_pass_b<R, CT><<<dim3((N + yc - 1) / yc, N, nbb), plane_threads<CT>(), sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
+        k_pass_b<R, CT, NC><<<dim3((N + yc - 1) / yc, N, nbb), plane_threads<CT>(), sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
         LG_TRY(check_launch("fft pass B"));
-        k_pass_c<R, CT><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
+        k_pass_c<R, CT, NC><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
                                                              g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass C"));
     }
     return LOBPCG_OK;
+}
+
+// Grid edges of the benchmark cells get their own double-FP32 kernels (compile-time plan).
+template <typename R, typename CT>
+int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
+               const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
+    if constexpr (std::is_same<CT, df64>::value) {
+        switch (g.N) {
+            case 72: return fft_passes_n<R, CT, 72>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+            case 96: return fft_passes_n<R, CT, 96>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+            case 120: return fft_passes_n<R, CT, 120>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+            case 160: return fft_passes_n<R, CT, 160>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+            default: break;
+        }
+    }
+    return fft_passes_n<R, CT, 0>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
 }
 
 // rho += scale sum_b f_b |psi_b|^2 over batches of bands: pass A then the density pass.
