@@ -133,4 +133,48 @@ struct alignas(8) df64 {
 
 static_assert(sizeof(df64) == 8, "df64 is two floats");
 
+// The same pair with the "sloppy" double-word sum (one TwoSum on the high parts, the low parts
+// added, one renormalisation: 11 instead of 20 FP32 operations).  Its error is bounded by a few
+// units of 2^-48 of |a| + |b| rather than of |a + b|: enough wherever the error analysis is
+// norm-wise, as in the butterflies of an FFT, whose outputs carry errors relative to the
+// transform's norm anyway.  Multiplication and the conversions are df64's.
+struct alignas(8) df64f {
+    float hi, lo;
+
+    df64f() = default;
+    __host__ __device__ __forceinline__ df64f(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ __forceinline__ df64f(float f) : hi(f), lo(0.f) {}
+    __host__ __device__ __forceinline__ df64f(int i) : df64f((double)i) {}
+    __host__ __device__ __forceinline__ df64f(double d) {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+    }
+    __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+
+    friend __device__ __forceinline__ df64f operator-(df64f a) { return df64f(-a.hi, -a.lo); }
+    friend __device__ __forceinline__ df64f operator+(df64f a, df64f b) {
+        float s, e;
+        df64::two_sum(a.hi, b.hi, s, e);
+        e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+        df64f r;
+        df64::fast_two_sum(s, e, r.hi, r.lo);
+        return r;
+    }
+    friend __device__ __forceinline__ df64f operator-(df64f a, df64f b) { return a + (-b); }
+    friend __device__ __forceinline__ df64f operator*(df64f a, df64f b) {
+        const float p = __fmul_rn(a.hi, b.hi);
+        float e = __fmaf_rn(a.hi, b.hi, -p);
+        e = __fmaf_rn(a.hi, b.lo, e);
+        e = __fmaf_rn(a.lo, b.hi, e);
+        df64f r;
+        df64::fast_two_sum(p, e, r.hi, r.lo);
+        return r;
+    }
+    friend __device__ __forceinline__ df64f &operator+=(df64f &a, df64f b) { return a = a + b; }
+    friend __device__ __forceinline__ df64f &operator-=(df64f &a, df64f b) { return a = a - b; }
+    friend __device__ __forceinline__ df64f &operator*=(df64f &a, df64f b) { return a = a * b; }
+};
+
+static_assert(sizeof(df64f) == 8, "df64f is two floats");
+
 }  // namespace lg

@@ -529,7 +529,7 @@ int fft_passes_n(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx,
 template <typename R, typename CT>
 int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
                const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
-    if constexpr (std::is_same<CT, df64>::value) {
+    if constexpr (std::is_same<CT, df64f>::value) {
         switch (g.N) {
             case 72: return fft_passes_n<R, CT, 72>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
             case 96: return fft_passes_n<R, CT, 96>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
@@ -586,7 +586,7 @@ int fft_density(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, 
         if (df) {
             FFTPlan p4;
             if (!make_fft_plan(g.N, p4, false)) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plan");
-            return density_passes<R, df64>(g, p4, X, ldx, nb, tw, f, scale, rho, reinterpret_cast<cx<df64> *>(T2),
+            return density_passes<R, df64f>(g, p4, X, ldx, nb, tw, f, scale, rho, reinterpret_cast<cx<df64f> *>(T2),
                                            nbatch, s);
         }
     }
@@ -609,7 +609,7 @@ int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
         if (df) {  // FP64 data transformed in double-FP32 (the half box holds pairs of floats)
             FFTPlan p4;
             if (!make_fft_plan(g.N, p4, false)) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plan");
-            return fft_passes<R, df64>(g, p4, X, ldx, Y, ldy, nb, kin, vt, tw, reinterpret_cast<cx<df64> *>(T2),
+            return fft_passes<R, df64f>(g, p4, X, ldx, Y, ldy, nb, kin, vt, tw, reinterpret_cast<cx<df64f> *>(T2),
                                        nbatch, s);
         }
     }
