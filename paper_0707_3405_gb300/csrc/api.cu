@@ -261,6 +261,7 @@ struct lobpcg_ctx {
     std::vector<KPoint> kp;
     FFTPlan plan;
     double *vt64 = nullptr;
+    float2 *vtdf = nullptr;   // vt64 as (hi, lo) FP32 pairs, for the double-FP32 FFT passes
     float *vt32 = nullptr;
     z64 *tw64 = nullptr;
     c32 *tw32 = nullptr;
@@ -444,7 +445,8 @@ int apply_H_dev(lobpcg_ctx *c, Lane &L, int k, const cx<R> *X, int ldx, cx<R> *Y
                           std::ceil((double)nb / nbatch) * sizeof(R) * (double)g.N * g.N * g.N;
         PhaseScope ps(prof, LOBPCG_PH_FFT, nb * fft_flops_per_band(g), by, f64 && !df);
         LG_TRY(fft_vloc_apply<R>(g, c->plan, X, ldx, Y, ldy, nb, Tables<R>::kin(K), Tables<R>::vt(c),
-                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(L.T2.p), nbatch, L.stream, df));
+                                 Tables<R>::tw(c), reinterpret_cast<cx<R> *>(L.T2.p), nbatch, L.stream, df,
+                                 df ? c->vtdf : nullptr));
     }
     if (c->nproj > 0) {
         if (!K.has_beta) return fail(LOBPCG_ERR_ARG, "projectors of this k-point were not given");
@@ -1437,6 +1439,14 @@ static int create_impl(lobpcg_ctx *c, const lobpcg_cell *cell, int nk, const dou
                 vt32[reg32 ? ((size_t)y * N + x) * N + z : ((size_t)z * N + x) * N + y] = (float)v;
             }
     LG_TRY(upload(c, &c->vt64, vt.data(), N3));
+    {   // the same table as (hi, lo) FP32 pairs for the double-FP32 passes
+        std::vector<float2> vp(N3);
+        for (size_t i = 0; i < N3; ++i) {
+            const float hi = (float)vt[i];
+            vp[i] = make_float2(hi, (float)(vt[i] - (double)hi));
+        }
+        LG_TRY(upload(c, &c->vtdf, vp.data(), N3));
+    }
     LG_TRY(upload(c, &c->vt32, vt32.data(), N3));
     // twiddles e^{-2 pi i t/N}, FP64 on the host, rounded for FP32
     std::vector<z64> tw(N);

@@ -181,10 +181,12 @@ bool make_fft_plan(int N, FFTPlan &plan, bool allow8 = true);
 //   T2:   scratch of at least nbatch * Px * N * N cx<R>
 //   df:   complex128 only: transform in double-FP32 arithmetic (FP32 pairs, ~2^-48 per
 //         operation) instead of FP64
+//   vt_pair: optional, with df: vt as (hi, lo) FP32 pairs in vt's layout (read instead of
+//         converting vt on the fly)
 template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy,
                    int nb, const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch,
-                   cudaStream_t s, bool df = false);
+                   cudaStream_t s, bool df = false, const float2 *vt_pair = nullptr);
 // FP32 register-resident variant of the three passes for the grid edges it is
 // compiled for (8, 12, 16, 20, 24, 36, 48, 64, 72, 96, 120, 128, 160).  Its scratch is laid out T2[b][px][y][z]
 // and its potential table vt as [y][x][z] (pre-scaled by 1/N^3);

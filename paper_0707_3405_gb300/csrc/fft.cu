@@ -310,7 +310,7 @@ k_pass_a(const cx<R> *__restrict__ X, int ldx, cx<CT> *__restrict__ T2, FFTPlan 
 template <typename R, typename CT = R, int NC = 0>
 __global__ void __launch_bounds__(plane_threads<CT>())
 k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__restrict__ vt,
-         const cx<R> *__restrict__ twg, int yc) {
+         const CT *__restrict__ vtc, const cx<R> *__restrict__ twg, int yc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NC ? NC : plan.N;
     cx<CT> *tw = reinterpret_cast<cx<CT> *>(smem_raw);
@@ -332,10 +332,13 @@ k_pass_b(cx<CT> *__restrict__ T2, FFTPlan plan, int Px, int nx0m, const R *__res
     }
     __syncthreads();
     fft_lines<CT, NC>(L, ny, lsL, 1, plan, tw, 1);
+    // V in the compute type: from vtc when given (no conversion), else converted here
     const R *vz = vt + (size_t)z * NN + y0;
+    const CT *vcz = vtc ? vtc + (size_t)z * NN + y0 : nullptr;
     for (int i = threadIdx.x; i < ny * N; i += blockDim.x) {
         const int ix = i / ny, yy = i - ix * ny;
-        L[yy * lsL + ix] = (CT)vz[(size_t)ix * N + yy] * L[yy * lsL + ix];
+        const CT vv = vcz ? vcz[(size_t)ix * N + yy] : (CT)vz[(size_t)ix * N + yy];
+        L[yy * lsL + ix] = vv * L[yy * lsL + ix];
     }
     __syncthreads();
     fft_lines<CT, NC>(L, ny, lsL, 1, plan, tw, -1);
@@ -492,7 +495,7 @@ namespace {
 // kernels compiled for that grid edge.
 template <typename R, typename CT, int NC>
 int fft_passes_n(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
-                 const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
+                 const R *kin, const R *vt, const CT *vtc, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
     const int N = g.N;
     const int zc = pick_zc<R>(g);
     if (zc == 0) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT grid too large for shared memory");
@@ -516,7 +519,7 @@ int fft_passes_n(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx,
         k_pass_a<R, CT, NC><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(Xb, ldx, T2, plan, g.Px, g.Py, ny0m, g.plane_begin,
                                                              g.plane_yrange, g.gmap, tw, zc);
         LG_TRY(check_launch("fft pass A"));
-        k_pass_b<R, CT, NC><<<dim3((N + yc - 1) / yc, N, nbb), plane_threads<CT>(), sm_b, s>>>(T2, plan, g.Px, nx0m, vt, tw, yc);
+        k_pass_b<R, CT, NC><<<dim3((N + yc - 1) / yc, N, nbb), plane_threads<CT>(), sm_b, s>>>(T2, plan, g.Px, nx0m, vt, vtc, tw, yc);
         LG_TRY(check_launch("fft pass B"));
         k_pass_c<R, CT, NC><<<dim3(g.Px, nbb), plane_threads<CT>(), sm_ac, s>>>(T2, Yb, ldy, Xb, ldx, kin, plan, g.Px, g.Py, ny0m,
                                                              g.plane_begin, g.plane_yrange, g.gmap, tw, zc);
@@ -528,17 +531,17 @@ int fft_passes_n(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx,
 // Grid edges of the benchmark cells get their own double-FP32 kernels (compile-time plan).
 template <typename R, typename CT>
 int fft_passes(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
-               const R *kin, const R *vt, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
+               const R *kin, const R *vt, const CT *vtc, const cx<R> *tw, cx<CT> *T2, int nbatch, cudaStream_t s) {
     if constexpr (std::is_same<CT, df64f>::value) {
         switch (g.N) {
-            case 72: return fft_passes_n<R, CT, 72>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
-            case 96: return fft_passes_n<R, CT, 96>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
-            case 120: return fft_passes_n<R, CT, 120>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
-            case 160: return fft_passes_n<R, CT, 160>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+            case 72: return fft_passes_n<R, CT, 72>(g, plan, X, ldx, Y, ldy, nb, kin, vt, vtc, tw, T2, nbatch, s);
+            case 96: return fft_passes_n<R, CT, 96>(g, plan, X, ldx, Y, ldy, nb, kin, vt, vtc, tw, T2, nbatch, s);
+            case 120: return fft_passes_n<R, CT, 120>(g, plan, X, ldx, Y, ldy, nb, kin, vt, vtc, tw, T2, nbatch, s);
+            case 160: return fft_passes_n<R, CT, 160>(g, plan, X, ldx, Y, ldy, nb, kin, vt, vtc, tw, T2, nbatch, s);
             default: break;
         }
     }
-    return fft_passes_n<R, CT, 0>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+    return fft_passes_n<R, CT, 0>(g, plan, X, ldx, Y, ldy, nb, kin, vt, vtc, tw, T2, nbatch, s);
 }
 
 // rho += scale sum_b f_b |psi_b|^2 over batches of bands: pass A then the density pass.
@@ -601,7 +604,8 @@ template int fft_density<double>(const FFTGeom &, const FFTPlan &, const z64 *, 
 
 template <typename R>
 int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ldx, cx<R> *Y, int ldy, int nb,
-                   const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch, cudaStream_t s, bool df) {
+                   const R *kin, const R *vt, const cx<R> *tw, cx<R> *T2, int nbatch, cudaStream_t s, bool df,
+                   const float2 *vt_pair) {
     if (nb <= 0) return LOBPCG_OK;
     if constexpr (std::is_same<R, float>::value) {
         if (fft_reg_supported(g.N)) return fft_reg_apply(g, X, ldx, Y, ldy, nb, kin, vt, T2, nbatch, s);
@@ -609,17 +613,21 @@ int fft_vloc_apply(const FFTGeom &g, const FFTPlan &plan, const cx<R> *X, int ld
         if (df) {  // FP64 data transformed in double-FP32 (the half box holds pairs of floats)
             FFTPlan p4;
             if (!make_fft_plan(g.N, p4, false)) return fail(LOBPCG_ERR_UNSUPPORTED, "FFT plan");
-            return fft_passes<R, df64f>(g, p4, X, ldx, Y, ldy, nb, kin, vt, tw, reinterpret_cast<cx<df64f> *>(T2),
+            return fft_passes<R, df64f>(g, p4, X, ldx, Y, ldy, nb, kin, vt,
+                                        reinterpret_cast<const df64f *>(vt_pair), tw, reinterpret_cast<cx<df64f> *>(T2),
                                        nbatch, s);
         }
     }
-    return fft_passes<R, R>(g, plan, X, ldx, Y, ldy, nb, kin, vt, tw, T2, nbatch, s);
+    (void)vt_pair;
+    return fft_passes<R, R>(g, plan, X, ldx, Y, ldy, nb, kin, vt, nullptr, tw, T2, nbatch, s);
 }
 
 template int fft_vloc_apply<float>(const FFTGeom &, const FFTPlan &, const c32 *, int, c32 *, int, int,
-                                   const float *, const float *, const c32 *, c32 *, int, cudaStream_t, bool);
+                                   const float *, const float *, const c32 *, c32 *, int, cudaStream_t, bool,
+                                   const float2 *);
 template int fft_vloc_apply<double>(const FFTGeom &, const FFTPlan &, const z64 *, int, z64 *, int, int,
-                                    const double *, const double *, const z64 *, z64 *, int, cudaStream_t, bool);
+                                    const double *, const double *, const z64 *, z64 *, int, cudaStream_t, bool,
+                                    const float2 *);
 template size_t fft_smem_need<float>(const FFTGeom &);
 template size_t fft_smem_need<double>(const FFTGeom &);
 
