@@ -427,6 +427,8 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
       ``fp64class_gemm_df32``, the double-FP32 CUDA-core engine at the same shape;
     * ``gram_3xtf32``: the 3xTF32 tensor-core A^H B Gram of a block's [R W P] (3m x 3m x npw,
       complex64), tensor flops 3 x 8 m n K against the TF32 rate (measured BF16 x 1.1 / 2.25);
+    * ``update_3xtf32``: the 3xTF32 A B of a block's update P = [W P] C (npw x m x 2m, complex64),
+      the same flop count and ceiling;
     * ``fft_c64``: the FP32 FFT passes A, B, C of H psi for one block (m bands) on a handle of the
       same cell without projectors, algorithmic bytes (half box written, read + written, read;
       sphere in and out, kinetic table; V once per band batch) against the HBM copy rate.
@@ -439,7 +441,7 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
         stream = torch.cuda.current_stream()
     except Exception as e:  # no device: every entry records the error
         return {k: {"error": f"{type(e).__name__}: {e}"}
-                for k in ("fp64class_gemm", "fp64class_gemm_df32", "gram_3xtf32", "fft_c64")}
+                for k in ("fp64class_gemm", "fp64class_gemm_df32", "gram_3xtf32", "update_3xtf32", "fft_c64")}
     hbm = pk.get("hbm_gbs", FALLBACK["hbm_gbs"])
     tf32 = pk.get("bf16_tflops", FALLBACK["bf16_tflops"]) * TF32_PER_BF16
     m = w.block
@@ -486,6 +488,22 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
         del A, B, C
     except Exception as e:
         out["gram_3xtf32"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        k2 = 2 * m
+        A = torch.randn((k2, npw), dtype=torch.complex64, device="cuda")
+        B = torch.randn((m, k2), dtype=torch.complex64, device="cuda")
+        D = torch.empty((m, npw), dtype=torch.complex64, device="cuda")
+        lg.set_gemm_mode(0)
+        t = _event_time(lambda: lg.gemm_nn(A, B, D=D), max(reps, 5), stream)
+        fl = 3.0 * 8.0 * npw * m * k2
+        out["update_3xtf32"] = {
+            "kernel": f"k_tc_nn<{128 if m > 64 else 64}>", "shape": [npw, m, k2], "bound": "tensor",
+            "unit": "TFLOP/s", "ms": t * 1e3, "achieved": fl / t / 1e12, "peak": tf32, "frac": fl / t / 1e12 / tf32,
+            "work_per_launch": f"{fl:.4g} tensor flops (3 x 8 M n k)",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio 1.1/2.25"}
+        del A, B, D
+    except Exception as e:
+        out["update_3xtf32"] = {"error": f"{type(e).__name__}: {e}"}
     try:
         import dataclasses
         wl = dataclasses.replace(w, proj_E=np.zeros(0), kpts=w.kpts[:1])

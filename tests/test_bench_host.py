@@ -145,6 +145,6 @@ def test_kernel_rooflines_never_raise():
     if torch.cuda.is_available():
         pytest.skip("CPU-only check")
     out = bench.kernel_rooflines(synth.make_workload("gamma24"), 925, 16, {"hbm_gbs": 1.0, "bf16_tflops": 1.0})
-    assert set(out) == {"fp64class_gemm", "fp64class_gemm_df32", "gram_3xtf32", "fft_c64"}
+    assert set(out) == {"fp64class_gemm", "fp64class_gemm_df32", "gram_3xtf32", "update_3xtf32", "fft_c64"}
     assert all("error" in v for v in out.values())
     assert bench.roofline_of(out)["frac"] is None
