@@ -70,7 +70,7 @@ def parse():
                     help="skip the Gamma-point real-orbital solve of a Gamma cell (reported beside the headline)")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the warm-up and timed steps of --mode, no other legs")
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply", "apply_df32", "fp64gemm"],
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "solve", "apply", "apply_df32", "fp64gemm", "tf32gemm"],
                     help="with --ncu: LOBPCG sweeps, full solves to --tol, standalone apply_H, the "
                          "double-FP32 apply_H of the FP64-class H X, or the FP64-class tensor-core A B "
                          "(npw x nb x nb; nb = --nb, default the solve's band count)")
@@ -106,6 +106,27 @@ def ncu_run(args):
         torch.cuda.synchronize()
         lg.check_timeouts()
         print(json.dumps({"ncu_run": True, "mode": args.mode, "shape": [M, nb, nb], "launches": lg.launch_count(),
+                          "s": time.perf_counter() - t0}))
+        return 0
+    if args.mode == "tf32gemm":
+        # the 3xTF32 A B of a block update at the bench shape (npw x m x 2m, complex64)
+        lg.load()
+        import dataclasses
+        s0 = solver_for(dataclasses.replace(w, proj_E=np.zeros(0), kpts=w.kpts[:1]), "mixed")
+        M = s0.npw(0)
+        s0.close()
+        m = w.block
+        A = torch.randn((2 * m, M), dtype=torch.complex64, device="cuda")
+        B = torch.randn((m, 2 * m), dtype=torch.complex64, device="cuda")
+        D = torch.empty((m, M), dtype=torch.complex64, device="cuda")
+        lg.set_gemm_mode(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.warmup + args.steps):
+            lg.gemm_nn(A, B, D=D)
+        torch.cuda.synchronize()
+        lg.check_timeouts()
+        print(json.dumps({"ncu_run": True, "mode": args.mode, "shape": [M, m, 2 * m], "launches": lg.launch_count(),
                           "s": time.perf_counter() - t0}))
         return 0
     if args.mode == "solve":
@@ -397,9 +418,10 @@ FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 DF32_INSTR_PER_CMAC = 48.0
 TF32_PER_BF16 = 1.1 / 2.25        # nominal dense TF32 / BF16 tensor rates
 OZ_PAIRS = 21                     # digit-slice products per real product of the FP64-class tensor-core GEMM
-# Dominant kernel family of the mixed solve on the benchmark cells (launch lists in profiles/):
-# the FP64-class GEMMs, timed here at the sweep-end rotation's shape.
-DOMINANT = "fp64class_gemm"
+# Dominant kernel of the mixed solve on the benchmark cell (launch list in profiles/): the 3xTF32
+# A B of the block updates, k_tc_nn<128> (14% of device time), timed here at a block update's
+# shape; the FP64-class tensor GEMMs (22% as a family) are reported beside it under kernels.
+DOMINANT = "update_3xtf32"
 
 
 def _event_time(fn, reps, stream):
@@ -529,7 +551,8 @@ def kernel_rooflines(w, npw, nbands, pk, reps=3):
 
 # DRAM bytes per launch (read + write) from one ncu capture, by kernel entry and shape; valid only
 # while the kernel is unchanged since the capture (the summary names the command).
-TRAFFIC = {("fp64class_gemm", (113081, 1152, 1152)): (1.905e10, "profiles/fp64class_tensor_gemm_traffic_gamma120.md")}
+TRAFFIC = {("fp64class_gemm", (113081, 1152, 1152)): (1.905e10, "profiles/fp64class_tensor_gemm_traffic_gamma120.md"),
+           ("update_3xtf32", (113081, 128, 256)): (3.16e8, "profiles/tc_nn_3xtf32_update_gamma120.md")}
 
 
 def roofline_of(kr, dominant=DOMINANT):

@@ -98,7 +98,7 @@ def test_roofline_reports_the_dominant_kernel():
                              "ms": 2.0, "achieved": 40.0, "peak": 80.0, "frac": 0.5, "work_per_launch": "x",
                              "peak_source": "MEASURED_PEAKS.json bf16_tflops"},
           "fft_c64": {"error": "boom"}}
-    roof = bench.roofline_of(kr)
+    roof = bench.roofline_of(kr, "fp64class_gemm")
     assert roof["bound"] == "tensor" and roof["frac"] == 0.5 and roof["achieved"] == 40.0
     assert roof["traffic"] is None and "of measured" in roof["peak_source"]
     bad = bench.roofline_of(kr, "fft_c64")
