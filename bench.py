@@ -658,16 +658,13 @@ def main():
                   tol=args.tol, timing=False, nbuf=nbuf, use_graph=True)
 
     # end to end through the same public call: start vectors in pinned host memory
-    Xh0 = [x.cpu().pin_memory() for x in X0]
-    Xh = [torch.empty_like(x).pin_memory() for x in Xh0]
-    n_e2e = 1
+    # (the host buffers are filled before the clock starts: the solve overwrites them with the
+    # result, and refilling them is a host-to-host copy of the caller's, not part of the call)
+    Xh = [x.cpu().pin_memory() for x in X0]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(n_e2e):
-        for xh, x0 in zip(Xh, Xh0):
-            xh.copy_(x0)
-        s.solve(Xh)
-    t_e2e = max_over_ranks(time.perf_counter() - t0, ws) / n_e2e
+    s.solve(Xh)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
     nb_bytes = sum(16 * s.npw(i) * w.nbands for i in range(len(mine)))
     e2e = {"value": t_e2e, "unit": UNIT, "h2d_bytes_per_step": nb_bytes,
            "d2h_bytes_per_step": nb_bytes + 16 * w.nbands * len(mine)}
