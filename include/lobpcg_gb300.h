@@ -135,9 +135,9 @@ typedef struct {
                             tensor cores as in 3, the rest double-FP32; FP64: native FP64), 1 = native
                             FP64, 2 = double-FP32 on the FP32 units (about 2^-47 relative per operation)
                             on both schedules, 3 = like 2 but the tall GEMMs on the tensor cores with
-                            exact BF16 digit slices (the LOBPCG_C128_TC arithmetic).  The serial
-                            recurrences (multisection, inverse iteration, back-transformation) stay
-                            FP64. */
+                            exact BF16 digit slices (the LOBPCG_C128_TC arithmetic).  With 2 and 3
+                            the fine multisection rounds and the back-transformation run in
+                            double-FP32 as well; inverse iteration's serial recurrences stay FP64. */
     int    gamma_real;   /* 1: k-points at Gamma (k = 0) are solved in the real-orbital form (the
                             Gamma-point trick of plane-wave codes; the paper expands complex orbitals,
                             Sec. 2.1): eigenvectors with c(-G) = conj(c(G)), stored packed on the half

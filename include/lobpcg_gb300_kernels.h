@@ -104,19 +104,20 @@ int lobpcg_k_rayleigh_ritz(int n, int m, const void *S, const void *A, double dr
  * The same Rayleigh-Ritz step with the parts that one SM's FP64 units limit on
  * this GPU in double-FP32 arithmetic (the LOBPCG_C128_DF32 scheme above): the
  * Cholesky diagonal blocks, the column work of the Householder
- * tridiagonalisation and the small dense products.  The serial recurrences
- * (multisection, inverse iteration, back-transformation) stay FP64.  Same
- * arguments, layout and errors as lobpcg_k_rayleigh_ritz; results agree with
- * it to about 1e-13 relative.
+ * tridiagonalisation, the small dense products, the fine multisection rounds
+ * and the back-transformation.  Inverse iteration's serial recurrences stay
+ * FP64.  Same arguments, layout and errors as lobpcg_k_rayleigh_ritz; results
+ * agree with it to about 1e-13 relative.
  */
 int lobpcg_k_rayleigh_ritz_df32(int n, int m, const void *S, const void *A, double drop_tol,
                                 double *theta, void *C, int *ndropped, void *stream);
 
 /*
  * The same Rayleigh-Ritz step in FP32 arithmetic: S, A and C are complex64
- * (n x n and n x m, column-major), theta is float.  The mixed-precision
- * schedule uses it inside the block iterations, where only the search
- * subspace, not the final eigenvalues, depends on it.
+ * (n x n and n x m, column-major), theta is float.  A building block only:
+ * the mixed-precision schedule solves its Rayleigh-Ritz steps in FP64 class
+ * (an FP32 pencil there loses the nearly dependent directions of converged
+ * bands).
  */
 int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double drop_tol,
                              float *theta, void *C, int *ndropped, void *stream);
@@ -125,8 +126,9 @@ int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double 
  * Hermitian eigen-decomposition in FP64: A = V diag(w) V^H, eigenvalues ascending.
  *   A   (device, n x n complex128, ld n; lower triangle used, not modified),
  *   w   (device, n doubles), V (device, n x n complex128, ld n).
- * Householder tridiagonalisation, bisection and inverse iteration on the
- * tridiagonal matrix, back-transformation.
+ * Householder tridiagonalisation (in one thread-block cluster's shared memory
+ * up to n = 416, else one cooperative grid), multisection and inverse iteration
+ * on the tridiagonal matrix, compact-WY back-transformation.
  */
 int lobpcg_k_heev(int n, const void *A, double *w, void *V, void *stream);
 
