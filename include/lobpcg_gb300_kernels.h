@@ -115,9 +115,8 @@ int lobpcg_k_rayleigh_ritz_df32(int n, int m, const void *S, const void *A, doub
 /*
  * The same Rayleigh-Ritz step in FP32 arithmetic: S, A and C are complex64
  * (n x n and n x m, column-major), theta is float.  A building block only:
- * the mixed-precision schedule solves its Rayleigh-Ritz steps in FP64 class
- * (an FP32 pencil there loses the nearly dependent directions of converged
- * bands).
+ * the mixed-precision schedule assembles its pencils from FP32 Gram blocks
+ * but solves them in FP64 class.
  */
 int lobpcg_k_rayleigh_ritz32(int n, int m, const void *S, const void *A, double drop_tol,
                              float *theta, void *C, int *ndropped, void *stream);
