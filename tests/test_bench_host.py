@@ -148,3 +148,16 @@ def test_kernel_rooflines_never_raise():
     assert set(out) == {"fp64class_gemm", "fp64class_gemm_df32", "gram_3xtf32", "update_3xtf32", "fft_c64"}
     assert all("error" in v for v in out.values())
     assert bench.roofline_of(out)["frac"] is None
+
+
+def test_roofline_traffic_only_at_the_captured_shape():
+    sys.path.insert(0, ROOT)
+    import bench
+    entry = {"kernel": "k_tc_nn<128>", "bound": "tensor", "unit": "TFLOP/s", "ms": 0.33, "achieved": 267.0,
+             "peak": 924.0, "frac": 0.29, "work_per_launch": "x", "peak_source": "MEASURED_PEAKS.json bf16_tflops"}
+    at = bench.roofline_of({"update_3xtf32": dict(entry, shape=[113081, 128, 256])}, "update_3xtf32")
+    assert at["traffic"] == bench.TRAFFIC[("update_3xtf32", (113081, 128, 256))][0]
+    assert at["traffic_source"].startswith("profiles/")
+    other = bench.roofline_of({"update_3xtf32": dict(entry, shape=[57925, 64, 128])}, "update_3xtf32")
+    assert other["traffic"] is None
+    assert bench.DOMINANT in ("update_3xtf32", "fp64class_gemm", "gram_3xtf32", "fft_c64")
