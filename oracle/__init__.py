@@ -23,7 +23,7 @@ What it computes (Bottin, Leroux, Knyazev, Zerah 2007):
 * ``checks``      -- residual norms, orthonormality and cluster-projector
                      distances used to compare any solver against the oracle.
 
-For the next rows of the path (no GPU counterpart yet):
+For the rows beside the LOBPCG path:
 
 * ``density``     -- rho(r) = sum_n f_n |psi_n(r)|^2 on the grid (first step
                      of the SC loop, Sec. 2.1; by FFT, Sec. 2.2 item iii),
@@ -37,13 +37,17 @@ For the next rows of the path (no GPU counterpart yet):
                      so it is pinned only through convergence.
 
 Pins (tests/test_oracle_*.py): V=0 closed form and cubic-lattice shell counts,
-constant-V shift, rank-one KB secular equation, direct DFT vs analytic Fourier
-coefficients, Hermiticity, translation invariance, time reversal, Jacobi vs
-LAPACK, Courant-Fischer bounds, LOBPCG vs dense diagonalisation, the
-Teter-Payne-Allan ratio's small- and large-x expansions and the band kinetic
-energy it is scaled by (tests/test_oracle_next.py: density Parseval,
-plane-wave closed forms, translation and unitary invariance; real form
-unitary, real, same spectrum; PCG line minimum vs brute force, exact
-two-plane-wave step, monotone Rayleigh quotient, dense and free-electron
-limits).
+lattice-point counts with points on the sphere's edge, constant-V shift,
+rank-one KB secular equation, direct DFT vs analytic Fourier coefficients,
+Hermiticity, translation invariance, time reversal, Jacobi vs LAPACK,
+Courant-Fischer bounds, LOBPCG vs dense diagonalisation, the block constraint
+against exact eigenvectors, the first two LOBPCG steps as Rayleigh-Ritz on
+block Krylov spaces, the Teter-Payne-Allan ratio's small- and large-x
+expansions and the band kinetic energy it is scaled by
+(tests/test_oracle_next.py: density Parseval, plane-wave closed forms,
+translation and unitary invariance; real form unitary, real, same spectrum;
+PCG line minimum vs brute force, exact two-plane-wave step, monotone Rayleigh
+quotient, dense and free-electron limits).  tests/test_oracle_mutants.py
+plants one plausible mistake at a time in these modules and checks that a pin
+fails for each.
 """

@@ -50,6 +50,18 @@ def test_sphere_brute_force_tiny():
     assert got == want
 
 
+def test_sphere_keeps_lattice_points_on_the_edge():
+    """The cutoff is inclusive (1/2 |k+G|^2 <= Ecut): with a = 2 pi and Ecut = R/2 the sphere at
+    k = 0 is every integer point with |n|^2 <= R, whose count is the number of cubic-lattice
+    points in a ball of squared radius R, sum_{j <= R} r_3(j) (r_3(j): ways of writing j as a
+    sum of three squares): 1, 7, 19, 27, 33, 57, 81, 81, 93, 123, 147 for R = 0 ... 10."""
+    counts = [1, 7, 19, 27, 33, 57, 81, 81, 93, 123, 147]
+    for R, want in enumerate(counts):
+        n = basis.sphere(2.0 * math.pi, 16, R / 2.0, [0.0, 0.0, 0.0])
+        assert n.shape[0] == want, R
+        assert np.all(np.einsum("ij,ij->i", n, n) <= R)
+
+
 def test_sphere_too_large_raises():
     with pytest.raises(ValueError):
         basis.sphere(5.0, 8, 40.0, [0, 0, 0])

@@ -113,6 +113,76 @@ def test_lobpcg_workload_gamma24_matches_dense():
     assert r.converged and np.abs(r.eig - ref).max() < 1e-10
 
 
+def test_lobpcg_block_stays_orthogonal_to_the_earlier_blocks():
+    """Sec. 3.2 multiband-by-multiband: with the constraint block Y spanning the m lowest exact
+    eigenvectors, a block visit returns a block orthogonal to Y, and by Courant-Fischer on the
+    complement of Y its k-th Ritz value is at least the (m + k)-th eigenvalue."""
+    w, H = _tiny(nb=8, m=4)
+    ev, V = np.linalg.eigh(H.dense())
+    Y = V[:, :4]
+    X0 = w.x0(H.npw)[:, 4:8]
+    Xb, _, theta = lobpcg.block_lobpcg(H, X0, H.T, Y, nline=4)
+    assert np.abs(Y.conj().T @ Xb).max() < 1e-12
+    assert np.all(theta >= ev[4:8] - 1e-10)
+    assert np.all(theta < ev[4:8] + 0.5 * (ev[8] - ev[4]))    # and it made progress
+
+
+class _Dense:
+    def __init__(self, A):
+        self.A = A
+
+    def apply(self, X):
+        return self.A @ X
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_lobpcg_first_two_steps_are_block_krylov_rayleigh_ritz(m):
+    """With a preconditioner that is a multiple of the identity (all kinetic energies equal, so
+    the Teter ratio is K(1) everywhere), span[X, W] after the first step and span[X, W, P] after
+    the second are the block Krylov spaces span[X0, H X0] and span[X0, H X0, H^2 X0] (P holds
+    the previous step's W and P parts, Alg. 1 step 5). So the Ritz values after one and two
+    iterations are the lowest Ritz values of H on those Krylov spaces, and the block returned
+    after the second is the matching orthonormal Ritz block: it lies in the third Krylov space
+    and its residual is orthogonal to it (the Galerkin condition). Dropping P, mixing up the
+    coefficient blocks, or taking W from anything but the residual breaks one of these."""
+    rng = np.random.default_rng(21 + m)
+    n = 40
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = 0.5 * (A + A.conj().T) + np.diag(np.arange(n, dtype=float))
+    X0 = rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))
+    trace = []
+    X2, _, theta = lobpcg.block_lobpcg(_Dense(A), X0, np.ones(n), None, nline=2, trace=trace)
+
+    def krylov(p):
+        blocks, B = [], X0
+        for _ in range(p):
+            blocks.append(B)
+            B = A @ B
+        Q, _ = np.linalg.qr(np.hstack(blocks))
+        return Q, np.linalg.eigvalsh(Q.conj().T @ A @ Q)[:m]
+
+    assert np.abs(trace[0] - krylov(1)[1]).max() < 1e-10
+    assert np.abs(trace[1] - krylov(2)[1]).max() < 1e-10
+    Q3, ritz3 = krylov(3)
+    assert np.abs(trace[2] - ritz3).max() < 1e-10
+    assert np.all(trace[2] < trace[1] - 1e-6)
+    assert np.abs(X2.conj().T @ X2 - np.eye(m)).max() < 1e-10
+    assert np.abs(X2 - Q3 @ (Q3.conj().T @ X2)).max() < 1e-10
+    assert np.abs(Q3.conj().T @ (A @ X2 - X2 * theta[None, :])).max() < 1e-9
+
+
+def test_residuals_are_taken_on_unit_columns():
+    """||H x - eps x|| of the normalised column: zero for a scaled eigenvector, and the same for
+    a block and any positive multiple of it."""
+    w, H = _tiny()
+    ev, V = np.linalg.eigh(H.dense())
+    assert checks.residuals(H, 3.7 * V[:, :3], ev[:3]).max() < 1e-12
+    X = w.x0(H.npw)[:, :3]
+    r1 = checks.residuals(H, X, ev[:3])
+    np.testing.assert_allclose(checks.residuals(H, 5.0 * X, ev[:3]), r1, rtol=1e-12)
+    assert np.all(r1 > 1e-3)
+
+
 def test_projector_distance_detects_wrong_subspace():
     rng = np.random.default_rng(0)
     Q, _ = np.linalg.qr(rng.standard_normal((20, 6)) + 1j * rng.standard_normal((20, 6)))
