@@ -154,6 +154,43 @@ def _stream_handle(stream) -> int | None:
     return stream.cuda_stream
 
 
+def _dev_mats(*ops):
+    """Raise unless every ``(name, tensor, dtype, shape)`` names a contiguous CUDA tensor of that
+    dtype and shape: the dense building blocks take device pointers with sizes derived from the
+    other operands.  Types and shapes are checked for all operands before residency."""
+    import torch
+    for name, t, dtype, shape in ops:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, not {t.dtype}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t, _, _ in ops:
+        if not t.is_cuda:
+            raise TypeError(f"{name} must be on a CUDA device")
+
+
+def _band_block(name: str, x, npw: int):
+    """Raise unless ``x`` (numpy array or torch tensor, host or device) is a C-contiguous
+    complex128 (rows, npw) block."""
+    if isinstance(x, np.ndarray):
+        ok_type, contig = x.dtype == np.complex128, x.flags.c_contiguous
+    elif hasattr(x, "is_contiguous"):
+        import torch
+        ok_type, contig = x.dtype == torch.complex128, x.is_contiguous()
+    else:
+        raise TypeError(f"{name} must be a numpy array or a torch tensor")
+    if not ok_type:
+        raise TypeError(f"{name} must be complex128")
+    if x.ndim != 2 or x.shape[1] != npw:
+        raise ValueError(f"{name} must have shape (rows, {npw}), not {tuple(x.shape)}")
+    if not contig:
+        raise ValueError(f"{name} must be contiguous")
+
+
 def default_options() -> Options:
     o = Options()
     _check(load().lobpcg_default_options(ctypes.byref(o)), None)
@@ -278,6 +315,9 @@ class Solver:
             X = np.ascontiguousarray(X)
             if Y is None:
                 Y = np.empty_like(X)
+            elif not (isinstance(Y, np.ndarray) and Y.dtype == X.dtype and Y.shape == X.shape
+                      and Y.flags.c_contiguous):
+                raise TypeError("Y must be a contiguous numpy array with the shape and dtype of X")
         else:
             prec = C128 if X.dtype == torch.complex128 else C64
             if X.dtype not in (torch.complex128, torch.complex64):
@@ -286,6 +326,11 @@ class Solver:
                 raise ValueError("X must be contiguous")
             if Y is None:
                 Y = torch.empty_like(X)
+            elif not (isinstance(Y, torch.Tensor) and Y.dtype == X.dtype and Y.shape == X.shape
+                      and Y.device == X.device and Y.is_contiguous()):
+                raise TypeError("Y must be a contiguous tensor with the shape, dtype and device of X")
+        if X.ndim != 2:
+            raise ValueError("X must be an (nb, npw_k) block")
         nb = 0 if X.shape[0] == 0 else int(X.shape[0])
         if nb and X.shape[-1] != self.npw(k):
             raise ValueError("X must have shape (nb, npw_k)")
@@ -345,7 +390,11 @@ class Solver:
             X = [X]
         if len(X) != self.nk:
             raise ValueError("one start block per k-point is needed")
-        M = int(X[0].shape[0]) if nbands is None else nbands
+        for k, x in enumerate(X):
+            _band_block(f"X[{k}]", x, self.npw(k))
+        M = int(X[0].shape[0]) if nbands is None else int(nbands)
+        if any(x.shape[0] < M for x in X):
+            raise ValueError(f"every start block needs at least nbands = {M} rows")
         ptrs = (ctypes.c_void_p * self.nk)(*[ctypes.c_void_p(_ptr(x)) for x in X])
         eig = np.zeros((self.nk, M))
         res = np.zeros((self.nk, M))
@@ -397,6 +446,8 @@ def check_timeouts():
 
 def _prec128(dtype, df32, tc):
     import torch
+    if dtype not in (torch.complex128, torch.complex64):
+        raise TypeError("operands must be complex64 or complex128")
     prec = C128 if dtype == torch.complex128 else C64
     if df32 or tc:
         if prec != C128:
@@ -413,10 +464,13 @@ def gemm_cn(A, B, alpha=1.0, beta=0.0, C=None, stream=None, df32=False, tc=False
     import torch
     lib = load()
     prec = _prec128(A.dtype, df32, tc)
+    if A.dim() != 2 or B.dim() != 2:
+        raise ValueError("A and B must be matrices")
     m, K = A.shape
     n = B.shape[0]
     if C is None:
         C = torch.zeros((n, m), dtype=A.dtype, device=A.device)
+    _dev_mats(("A", A, A.dtype, (m, K)), ("B", B, A.dtype, (n, K)), ("C", C, A.dtype, (n, m)))
     _check(lib.lobpcg_k_gemm_cn(prec, m, n, K, alpha, _ptr(A), K, _ptr(B), K, beta, _ptr(C), m,
                                 _stream_handle(stream)), None, kernels=True)
     return C
@@ -434,6 +488,8 @@ def gram_lower(A, B, C=None, stream=None, df32=False, tc=False):
         raise ValueError("gram_lower: A and B must be complex128 of the same shape")
     if C is None:
         C = torch.zeros((n, n), dtype=A.dtype, device=A.device)
+    _dev_mats(("A", A, torch.complex128, (n, K)), ("B", B, torch.complex128, (n, K)),
+              ("C", C, torch.complex128, (n, n)))
     _check(lib.lobpcg_k_gram_lower(C128_TC if tc else (C128_DF32 if df32 else C128), n, K, _ptr(A), K, _ptr(B), K, _ptr(C), n,
                                    _stream_handle(stream)), None, kernels=True)
     return C
@@ -445,10 +501,14 @@ def gemm_nn(A, B, alpha=1.0, beta=0.0, C=None, D=None, stream=None, df32=False, 
     import torch
     lib = load()
     prec = _prec128(A.dtype, df32, tc)
+    if A.dim() != 2 or B.dim() != 2:
+        raise ValueError("A and B must be matrices")
     k, M = A.shape
     n = B.shape[0]
     if D is None:
         D = torch.empty((n, M), dtype=A.dtype, device=A.device)
+    ops = [("A", A, A.dtype, (k, M)), ("B", B, A.dtype, (n, k)), ("D", D, A.dtype, (n, M))]
+    _dev_mats(*(ops + ([("C", C, A.dtype, (n, M))] if C is not None else [])))
     _check(lib.lobpcg_k_gemm_nn(prec, M, n, k, alpha, _ptr(A), M, _ptr(B), k, beta,
                                 _ptr(C) if C is not None else None, M, _ptr(D), M, _stream_handle(stream)),
            None, kernels=True)
@@ -463,6 +523,7 @@ def rayleigh_ritz(S, A, m, drop_tol=1e-12, stream=None, df32=False):
     import torch
     lib = load()
     n = S.shape[0]
+    _dev_mats(("S", S, torch.complex128, (n, n)), ("A", A, torch.complex128, (n, n)))
     theta = torch.empty(m, dtype=torch.float64, device=S.device)
     C = torch.empty((m, n), dtype=torch.complex128, device=S.device)
     nd = torch.zeros(1, dtype=torch.int32, device=S.device)
@@ -477,6 +538,7 @@ def rayleigh_ritz32(S, A, m, drop_tol=1e-3, stream=None):
     import torch
     lib = load()
     n = S.shape[0]
+    _dev_mats(("S", S, torch.complex64, (n, n)), ("A", A, torch.complex64, (n, n)))
     theta = torch.empty(m, dtype=torch.float32, device=S.device)
     C = torch.empty((m, n), dtype=torch.complex64, device=S.device)
     nd = torch.zeros(1, dtype=torch.int32, device=S.device)
@@ -491,6 +553,7 @@ def heev(A, stream=None):
     import torch
     lib = load()
     n = A.shape[0]
+    _dev_mats(("A", A, torch.complex128, (n, n)))
     w = torch.empty(n, dtype=torch.float64, device=A.device)
     V = torch.empty((n, n), dtype=torch.complex128, device=A.device)
     _check(lib.lobpcg_k_heev(n, _ptr(A), _ptr(w), _ptr(V), _stream_handle(stream)), None, kernels=True)
