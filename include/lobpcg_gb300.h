@@ -87,9 +87,11 @@ extern "C" {
 
 /* Precision schedule of lobpcg_solve (lobpcg_options.precision). */
 #define LOBPCG_FP64  0              /* every step in FP64 */
-#define LOBPCG_MIXED 1              /* FP32 FFTs / reduced-precision GEMMs for W and P,
-                                       FP64 for X, HX, the XX Gram block, Cholesky,
-                                       Rayleigh-Ritz and residuals */
+#define LOBPCG_MIXED 1              /* FP32 FFTs / 3xTF32 tensor-core GEMMs for W and P;
+                                       X, HX and the residuals stored in FP64; the X block
+                                       start, Cholesky, Rayleigh-Ritz and X updates in FP64
+                                       class (arithmetic chosen by lobpcg_options.fp64_gemm);
+                                       residual norms and convergence in FP64 */
 
 typedef struct lobpcg_ctx lobpcg_ctx;   /* opaque handle */
 
