@@ -62,6 +62,10 @@ MUTANTS = [
     ("residual_wrong_sign", "oracle.lobpcg", "R = HX - X * theta[None, :]", "R = HX + X * theta[None, :]"),
     ("search_direction_drops_p", "oracle.lobpcg", "Pn, HPn = Pn + P @ Cp, HPn + HP @ Cp", "Pn, HPn = Pn, HPn"),
     ("final_rr_not_applied_to_hx", "oracle.lobpcg", "X, HX = X @ C, HX @ C\n        nrm", "X, HX = X @ C, HX\n        nrm"),
+    ("ritz_pairs_from_the_top", "oracle.lobpcg", "return theta[:m], C", "return theta[-m:], d[:, None] * (B @ Q[:, -m:])"),
+    ("constraint_misses_the_previous_block", "oracle.lobpcg", "Y = X[:, :b * block] if b else None",
+     "Y = X[:, :(b - 1) * block] if b > 1 else None"),
+    ("converged_on_the_smallest_residual", "oracle.lobpcg", "if rc.max() <= tol:", "if rc.min() <= tol:"),
     # density (Sec. 2.1)
     ("density_direct_wrong_sign", "oracle.density", "np.exp(2j * np.pi * (j @ n.T) / N)", "np.exp(-2j * np.pi * (j @ n.T) / N)"),
     ("density_direct_wrong_volume", "oracle.density", "reshape(N, N, N) / a ** 3", "reshape(N, N, N) / a ** 2"),
@@ -80,9 +84,13 @@ MUTANTS = [
     ("line_uses_the_wrong_diagonal", "oracle.pcg", "B = float(np.real(np.vdot(dh, hd)))", "B = float(np.real(np.vdot(dh, dh)))"),
     ("line_wrong_coupling_sign", "oracle.pcg", "C = float(np.real(np.vdot(x, hd)))", "C = -float(np.real(np.vdot(x, hd)))"),
     ("pcg_direction_not_constrained", "oracle.pcg", "eta = project_out(Y, eta)", "eta = eta"),
+    ("pcg_step_wrong_sign", "oracle.pcg", "x, hx = c * x + s * dh, c * hx + s * hd", "x, hx = c * x - s * dh, c * hx - s * hd"),
+    ("pcg_constraint_misses_the_previous_band", "oracle.pcg", "X[:, :n] if n else None", "X[:, :n - 1] if n > 1 else None"),
     # comparisons
     ("projector_distance_unconjugated", "oracle.checks", "A - B @ (B.conj().T @ A)", "A - B @ (B.T @ A)"),
     ("residuals_not_normalised", "oracle.checks", "X = X / np.linalg.norm(X, axis=0)[None, :]", "X = X"),
+    ("miller_map_unsorted", "oracle.checks", "return order[pos]", "return pos"),
+    ("clusters_split_inside_the_gap", "oracle.checks", "eig[i] - eig[i - 1] > gap", "eig[i] - eig[i - 1] >= 10 * gap"),
 ]
 
 

@@ -183,6 +183,30 @@ def test_residuals_are_taken_on_unit_columns():
     assert np.all(r1 > 1e-3)
 
 
+def test_map_by_miller_recovers_a_permutation():
+    """The index map between two orders of the same plane-wave set is the permutation that
+    reorders one into the other (brute force over a shuffled sphere); different sets raise."""
+    mil = basis.sphere(6.0, 12, synth.default_ecut(6.0, 12), [0.25, 0.125, -0.375])
+    rng = np.random.default_rng(3)
+    p_src, p_dst = rng.permutation(len(mil)), rng.permutation(len(mil))
+    src, dst = mil[p_src], mil[p_dst]
+    p = checks.map_by_miller(src, dst)
+    assert np.array_equal(src[p], dst)
+    assert np.array_equal(p, np.argsort(p_src)[p_dst])
+    other = dst.copy()
+    other[0] = [99, 0, 0]
+    with pytest.raises(ValueError):
+        checks.map_by_miller(src, other)
+
+
+def test_clusters_split_where_the_gap_is_exceeded():
+    eig = np.array([0.0, 1e-8, 2e-8, 1.0, 2.0, 2.0 + 5e-7])
+    assert checks.clusters(eig, 1e-6) == [(0, 3), (3, 4), (4, 6)]
+    assert checks.clusters(eig, 1e-9) == [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6)]
+    assert checks.clusters(np.array([3.0]), 1e-6) == [(0, 1)]
+    assert checks.clusters(np.array([0.0, 3e-6, 3.5e-6]), 1e-6) == [(0, 1), (1, 3)]
+
+
 def test_projector_distance_detects_wrong_subspace():
     rng = np.random.default_rng(0)
     Q, _ = np.linalg.qr(rng.standard_normal((20, 6)) + 1j * rng.standard_normal((20, 6)))
