@@ -61,6 +61,7 @@ MUTANTS = [
     ("coefficients_swapped", "oracle.lobpcg", "Cx, Cw = C[:m], C[m:2 * m]", "Cx, Cw = C[m:2 * m], C[:m]"),
     ("residual_wrong_sign", "oracle.lobpcg", "R = HX - X * theta[None, :]", "R = HX + X * theta[None, :]"),
     ("search_direction_drops_p", "oracle.lobpcg", "Pn, HPn = Pn + P @ Cp, HPn + HP @ Cp", "Pn, HPn = Pn, HPn"),
+    ("p_is_the_previous_w", "oracle.lobpcg", "P, HP = Pn, HPn", "P, HP = W, HW"),
     ("final_rr_not_applied_to_hx", "oracle.lobpcg", "X, HX = X @ C, HX @ C\n        nrm", "X, HX = X @ C, HX\n        nrm"),
     ("ritz_pairs_from_the_top", "oracle.lobpcg", "return theta[:m], C", "return theta[-m:], d[:, None] * (B @ Q[:, -m:])"),
     ("constraint_misses_the_previous_block", "oracle.lobpcg", "Y = X[:, :b * block] if b else None",

@@ -171,6 +171,31 @@ def test_lobpcg_first_two_steps_are_block_krylov_rayleigh_ritz(m):
     assert np.abs(Q3.conj().T @ (A @ X2 - X2 * theta[None, :])).max() < 1e-9
 
 
+@pytest.mark.parametrize("m", [1, 3])
+def test_lobpcg_p_spans_what_the_previous_iterate_spans(m):
+    """Sec. 3.1: replacing the previous iterate X^(i-1) by P^(i) in the basis of the subspace does
+    not change the subspace. So at every later iteration the Ritz values the oracle records equal
+    the lowest Ritz values of H on span[X^(i), W^(i), X^(i-1)], built here from the iterates of
+    shorter runs from the same start (the iteration is deterministic)."""
+    rng = np.random.default_rng(31 + m)
+    n = 40
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = 0.5 * (A + A.conj().T) + np.diag(np.arange(n, dtype=float))
+    X0 = rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))
+    T = np.ones(n)
+    iters, trace = [X0], []
+    for nl in range(1, 4):
+        iters.append(lobpcg.block_lobpcg(_Dense(A), X0, T, None, nline=nl)[0])
+    lobpcg.block_lobpcg(_Dense(A), X0, T, None, nline=4, trace=trace)
+    for i in (2, 3):
+        Xi, Xp = iters[i], iters[i - 1]
+        th = np.real(np.diag(Xi.conj().T @ A @ Xi))
+        Wi = A @ Xi - Xi * th[None, :]          # a multiple of K(R) when all kinetic energies are equal
+        Q, _ = np.linalg.qr(np.hstack([Xi, Wi, Xp]))
+        ritz = np.linalg.eigvalsh(Q.conj().T @ A @ Q)[:m]
+        assert np.abs(trace[i + 1] - ritz).max() < 1e-9, i
+
+
 def test_residuals_are_taken_on_unit_columns():
     """||H x - eps x|| of the normalised column: zero for a scaled eigenvector, and the same for
     a block and any positive multiple of it."""
