@@ -149,6 +149,22 @@ def test_time_reversal():
     assert np.abs(e1 - e0).max() < 1e-11
 
 
+def test_each_kpoint_of_a_multi_k_cell_has_its_own_hamiltonian():
+    """The Hamiltonian of k-point j of a cell with several k-points is the one of the same cell
+    with j as its only k-point: sphere, kinetic energies and projectors all follow k_j."""
+    import dataclasses
+    ks = np.array([[0.25, 0.125, -0.375], [0.0, 0.0, 0.0], [0.5, 0.25, 0.0]])
+    w = dataclasses.replace(synth.tiny_workload(a=6.0, N=12, natoms=2), kpts=ks)
+    for j in range(len(ks)):
+        wj = dataclasses.replace(w, kpts=ks[j:j + 1])
+        Hj, H1 = hamiltonian.for_workload(w, j), hamiltonian.for_workload(wj, 0)
+        assert Hj.npw == H1.npw
+        np.testing.assert_allclose(np.linalg.eigvalsh(Hj.dense()), np.linalg.eigvalsh(H1.dense()),
+                                   rtol=0, atol=1e-11)
+    e = [np.linalg.eigvalsh(hamiltonian.for_workload(w, j).dense())[:20] for j in range(len(ks))]
+    assert np.abs(e[0] - e[1]).max() > 1e-3 and np.abs(e[0] - e[2]).max() > 1e-3
+
+
 def test_kb_rank_one_secular_equation():
     """V = 0 and one projector of energy E: every eigenvalue below the lowest
     kinetic energy solves 1 = E sum_n |beta(n)|^2 / (eps - T_n)."""

@@ -45,6 +45,9 @@ MUTANTS = [
     ("fft_route_unconjugated_projector", "oracle.hamiltonian", "B = self.beta.conj().T @ X", "B = self.beta.T @ X"),
     ("apply_drops_kinetic", "oracle.hamiltonian", "Y = self.T[:, None] * X + self.apply_local(X)", "Y = self.apply_local(X)"),
     ("apply_wrong_kb_sign", "oracle.hamiltonian", "+ self.apply_nonlocal(X)", "- self.apply_nonlocal(X)"),
+    ("kpoint_always_the_first", "oracle.hamiltonian", "kpt = w.kpts[k_index]", "kpt = w.kpts[0]"),
+    ("projectors_of_the_first_kpoint", "oracle.hamiltonian", "beta = w.beta(miller, k_index) if w.nproj",
+     "beta = w.beta(miller, 0) if w.nproj"),
     # Jacobi rotations
     ("jacobi_wrong_rotation_sign", "oracle.jacobi", "u_qp, u_qq = -s * np.conj(ph)", "u_qp, u_qq = s * np.conj(ph)"),
     ("jacobi_conjugated_phase", "oracle.jacobi", "ph = np.where(act, b / np.where", "ph = np.where(act, np.conj(b) / np.where"),
@@ -79,6 +82,9 @@ MUTANTS = [
     ("from_half_unconjugated", "oracle.gamma", "c[minus] = np.conj(h[1:])", "c[minus] = h[1:]"),
     ("half_inner_drops_the_pair_factor", "oracle.gamma", "2.0 * np.real(ha[1:]", "np.real(ha[1:]"),
     ("real_H_unconjugated", "oracle.gamma", "y = self.U.conj().T @ self.H.apply", "y = self.U.T @ self.H.apply"),
+    ("to_half_takes_the_other_half", "oracle.gamma", "c[zero:zero + 1], c[plus]]", "c[zero:zero + 1], c[minus]]"),
+    ("real_kinetic_unconjugated", "oracle.gamma", "np.einsum(\"gi,g,gi->i\", self.U.conj(), H.T, self.U)",
+     "np.einsum(\"gi,g,gi->i\", self.U, H.T, self.U)"),
     # band-by-band PCG (Sec. 3.3)
     ("line_minimum_finds_the_maximum", "oracle.pcg", "np.arctan2(-2.0 * C, B - A)", "np.arctan2(2.0 * C, B - A)"),
     ("line_energy_drops_the_factor", "oracle.pcg", "2.0 * C * s * c", "C * s * c"),

@@ -121,6 +121,15 @@ def test_real_form_of_H_is_real_with_the_same_spectrum():
     assert np.abs(np.linalg.eigvalsh(Hr.real) - np.linalg.eigvalsh(Hc)).max() < 1e-12 * scale
 
 
+def test_real_basis_kinetic_energies_are_those_of_the_plane_waves():
+    """u_G and v_G combine e_G and e_-G, which have the same kinetic energy at Gamma, so the
+    kinetic diagonal in the real basis is the plane waves' 1/2 |G|^2, each value once per
+    plane wave (the preconditioner of the real-form solve is built on it)."""
+    _, H = _gamma_H()
+    RH = gamma.RealHamiltonian(H)
+    np.testing.assert_allclose(np.sort(RH.T), np.sort(H.T), rtol=1e-14, atol=1e-14)
+
+
 def test_half_storage_inner_products_and_round_trip():
     mil = _sphere()
     rng = np.random.default_rng(6)
