@@ -603,6 +603,8 @@ def main():
     nbuf = nbuf_of(w, args.nbuf)
     pk, pk_kind = peaks()
     sharded = w.nk > 1 and ws > 1
+    if sharded and ws > w.nk:
+        raise SystemExit(f"{w.name} has {w.nk} k-points: k-point sharding runs on at most {w.nk} ranks")
     mine = kshard.partition(w.nk, ws)[rank] if sharded else list(range(w.nk))
 
     # the autotuner runs in the first warm-up solve (its time is reported apart)
