@@ -22,7 +22,8 @@ and so on):
   (113081 plane waves, 108 atoms, 432 KB projectors): the oracle's block LOBPCG
   with 128 buffer bands to max residual 1e-10 Ha on the 1024.  The Lanczos
   route for it takes hours, so it runs apart on the stored file:
-  ``python tests/golden/make_golden.py confirm gamma120``.
+  ``python tests/golden/make_golden.py confirm gamma120`` (agreement 8.7e-13 Ha
+  over all 1024, 11344 s on 8 host cores).
 """
 import os
 import sys
