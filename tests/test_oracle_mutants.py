@@ -97,6 +97,8 @@ MUTANTS = [
     ("projector_distance_unconjugated", "oracle.checks", "A - B @ (B.conj().T @ A)", "A - B @ (B.T @ A)"),
     ("residuals_not_normalised", "oracle.checks", "X = X / np.linalg.norm(X, axis=0)[None, :]", "X = X"),
     ("miller_map_unsorted", "oracle.checks", "return order[pos]", "return pos"),
+    ("orthonormality_smallest_deviation", "oracle.checks", "np.eye(X.shape[1])).max())", "np.eye(X.shape[1])).min())"),
+    ("orthonormality_unconjugated", "oracle.checks", "np.abs(X.conj().T @ X - np.eye", "np.abs(X.T @ X - np.eye"),
     ("clusters_split_inside_the_gap", "oracle.checks", "eig[i] - eig[i - 1] > gap", "eig[i] - eig[i - 1] >= 10 * gap"),
 ]
 

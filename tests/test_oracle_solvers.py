@@ -208,6 +208,22 @@ def test_residuals_are_taken_on_unit_columns():
     assert np.all(r1 > 1e-3)
 
 
+def test_orthonormality_error_is_the_largest_gram_deviation():
+    """max |X^H X - I|: zero for an orthonormal complex block; scaling one column by (1 + e)
+    gives exactly (1 + e)^2 - 1 on its diagonal, and mixing one column into another by a
+    complex amount c gives |c| off the diagonal (Gram matrix of [q0, q1 + c q0])."""
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 5)) + 1j * rng.standard_normal((30, 5)))
+    assert checks.orthonormality_error(Q) < 1e-14
+    Q1 = Q.copy()
+    Q1[:, 2] *= 1.0 + 1e-3
+    assert checks.orthonormality_error(Q1) == pytest.approx((1.0 + 1e-3) ** 2 - 1.0, rel=1e-9)
+    c = 0.02 - 0.05j
+    Q2 = Q.copy()
+    Q2[:, 1] = Q[:, 1] + c * Q[:, 0]
+    assert checks.orthonormality_error(Q2) == pytest.approx(max(abs(c), abs(c) ** 2), rel=1e-9)
+
+
 def test_map_by_miller_recovers_a_permutation():
     """The index map between two orders of the same plane-wave set is the permutation that
     reorders one into the other (brute force over a shuffled sphere); different sets raise."""
