@@ -259,7 +259,7 @@ def golden_eigs(w):
     tests/golden/make_golden.py from the oracle); empty when none is stored."""
     out = {}
     names = {"gamma24": {0: "gamma24_eig.txt"}, "k96": {0: "k96_eig.txt"}, "gamma120": {0: "gamma120_eig.txt"},
-             "mp72x10": {0: "mp72x10_k0_eig.txt", 1: "mp72x10_k1_eig.txt"}}.get(w.name, {})
+             "mp72x10": {k: f"mp72x10_k{k}_eig.txt" for k in range(10)}}.get(w.name, {})
     for k, f in names.items():
         path = os.path.join(GOLDEN_DIR, f)
         if os.path.exists(path):

@@ -17,7 +17,8 @@ and so on):
   with 64 buffer bands to max residual 1e-10 Ha on the 256, confirmed by the
   oracle's Lanczos route (ARPACK) to 1e-10 Ha.
 * mp72x10_k0_eig.txt, mp72x10_k1_eig.txt -- the 128 lowest eigenvalues of the
-  first two k-points of the 10-k-point 72^3 cell, same two routes.
+  first two k-points of the 10-k-point 72^3 cell, same two routes
+  (``mp72x10``); ``mp72x10_k<j>`` writes the file of k-point j the same way.
 * gamma120_eig.txt -- the 1024 lowest eigenvalues of the 120^3 Gamma cell
   (113081 plane waves, 108 atoms, 432 KB projectors): the oracle's block LOBPCG
   with 128 buffer bands to max residual 1e-10 Ha on the 1024.  The Lanczos
@@ -72,9 +73,9 @@ def full_size(which):
         np.savetxt(os.path.join(HERE, "k96_eig.txt"), _lobpcg_eigs(w, 0, 256, 64, True), fmt="%.17e",
                    header="256 lowest eigenvalues (Ha), cell a=20 N=96 k=(1/4,1/4,1/4), 64 atoms + 256 KB, seed 1002; "
                           "oracle block LOBPCG (64 buffer bands, resid <= 1e-10) confirmed by oracle Lanczos")
-    elif which == "mp72x10":
+    elif which == "mp72x10" or which.startswith("mp72x10_k"):
         w = synth.make_workload("mp72x10")
-        for k in (0, 1):
+        for k in ((0, 1) if which == "mp72x10" else (int(which[len("mp72x10_k"):]),)):
             np.savetxt(os.path.join(HERE, f"mp72x10_k{k}_eig.txt"), _lobpcg_eigs(w, k, 128, 64, True), fmt="%.17e",
                        header=f"128 lowest eigenvalues (Ha), cell a=16 N=72 k-point {k} = {tuple(w.kpts[k])}, 32 atoms + "
                               f"128 KB, seed 1004; oracle block LOBPCG (64 buffer bands, resid <= 1e-10) confirmed by "
