@@ -48,6 +48,9 @@ MUTANTS = [
     ("kpoint_always_the_first", "oracle.hamiltonian", "kpt = w.kpts[k_index]", "kpt = w.kpts[0]"),
     ("projectors_of_the_first_kpoint", "oracle.hamiltonian", "beta = w.beta(miller, k_index) if w.nproj",
      "beta = w.beta(miller, 0) if w.nproj"),
+    # the Lanczos route
+    ("lanczos_largest_instead_of_smallest", "oracle.lanczos", 'which="SA"', 'which="LA"'),
+    ("lanczos_descending_order", "oracle.lanczos", "order = np.argsort(w)", "order = np.argsort(-w)"),
     # Jacobi rotations
     ("jacobi_wrong_rotation_sign", "oracle.jacobi", "u_qp, u_qq = -s * np.conj(ph)", "u_qp, u_qq = s * np.conj(ph)"),
     ("jacobi_conjugated_phase", "oracle.jacobi", "ph = np.where(act, b / np.where", "ph = np.where(act, np.conj(b) / np.where"),

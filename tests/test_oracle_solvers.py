@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import basis, checks, hamiltonian, jacobi, lobpcg
+from oracle import basis, checks, hamiltonian, jacobi, lanczos, lobpcg
 
 
 def _rand_herm(n, seed):
@@ -54,6 +54,22 @@ def test_lobpcg_matches_dense(kpt):
     assert np.abs(r.eig - ref).max() < 1e-10
     assert checks.orthonormality_error(r.X) < 1e-12
     assert checks.residuals(H, r.X, r.eig).max() < 1e-10
+
+
+@pytest.mark.parametrize("kpt", [(0.0, 0.0, 0.0), (0.25, 0.125, -0.375)])
+def test_lanczos_route_matches_dense(kpt):
+    """The second route to the lowest eigenpairs (ARPACK's Lanczos on the matrix-free H, used to
+    confirm the full-size goldens) against the dense H diagonalised by LAPACK: the lowest 12
+    eigenvalues in ascending order, unit eigenvectors with small residuals, the right spectral
+    projectors."""
+    w, H = _tiny(kpt)
+    ev, V = np.linalg.eigh(H.dense())
+    el, X = lanczos.lowest(H, 12)
+    assert np.abs(el - ev[:12]).max() < 1e-10
+    assert np.all(np.diff(el) >= 0.0)
+    assert np.abs(np.linalg.norm(X, axis=0) - 1.0).max() < 1e-12
+    assert checks.residuals(H, X, el).max() < 1e-8
+    assert checks.projector_distance(X, V[:, :12], ev[:12]) < 1e-8
 
 
 def test_lobpcg_single_block_is_plain_rayleigh_ritz_iteration():
