@@ -73,6 +73,8 @@ MUTANTS = [
     ("constraint_misses_the_previous_block", "oracle.lobpcg", "Y = X[:, :b * block] if b else None",
      "Y = X[:, :(b - 1) * block] if b > 1 else None"),
     ("converged_on_the_smallest_residual", "oracle.lobpcg", "if rc.max() <= tol:", "if rc.min() <= tol:"),
+    ("convergence_looks_at_the_buffer_bands", "oracle.lobpcg", "rc = r if nconv is None else r[:nconv]",
+     "rc = r if nconv is None else r[nconv:]"),
     # density (Sec. 2.1)
     ("density_direct_wrong_sign", "oracle.density", "np.exp(2j * np.pi * (j @ n.T) / N)", "np.exp(-2j * np.pi * (j @ n.T) / N)"),
     ("density_direct_wrong_volume", "oracle.density", "reshape(N, N, N) / a ** 3", "reshape(N, N, N) / a ** 2"),

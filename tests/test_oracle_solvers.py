@@ -88,6 +88,20 @@ def test_lobpcg_block_size_one_band_by_band():
     assert r.converged and np.abs(r.eig - ref).max() < 1e-10
 
 
+def test_lobpcg_with_buffer_bands_converges_the_wanted_ones():
+    """Buffer bands: 8 wanted bands plus one block of 4 iterated along. The convergence test
+    looks at the wanted bands only; they match the dense eigenvalues and meet the tolerance,
+    and the buffer bands still bound the next eigenvalues from above (Courant-Fischer)."""
+    w, H = _tiny(nb=12, m=4)
+    ev = np.linalg.eigvalsh(H.dense())
+    r = lobpcg.solve(H, w.x0(H.npw, M=12), block=4, nline=4, tol=1e-10, nconv=8)
+    assert r.converged
+    assert np.abs(r.eig[:8] - ev[:8]).max() < 1e-10
+    assert r.resid[:8].max() <= 1e-10
+    assert r.history[-1] == pytest.approx(r.resid[:8].max(), rel=1e-12)
+    assert np.all(r.eig[8:] >= ev[8:12] - 1e-10)
+
+
 def test_lobpcg_ritz_values_bound_and_decrease():
     """Courant-Fischer: the k-th Ritz value of the first block is >= the k-th
     eigenvalue, and within a block visit it never increases."""
