@@ -300,6 +300,22 @@ def test_golden_files_reproduce():
     assert np.abs(np.loadtxt(os.path.join(here, "tiny_kb_eig.txt")) - ev).max() < 1e-12
 
 
+def test_multi_k_goldens_respect_time_reversal():
+    """Each stored golden of the 10-k-point 72^3 cell comes from its own LOBPCG run from its own
+    start vectors. Where two of its k-points are time-reversal partners (k_i + k_j a reciprocal
+    lattice vector; real V and KB projectors), the spectra must coincide: eps(k) = eps(-k)."""
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    w = synth.make_workload("mp72x10")
+    pairs = [(i, j) for i in range(w.nk) for j in range(i + 1, w.nk)
+             if np.allclose(w.kpts[i] + w.kpts[j], np.round(w.kpts[i] + w.kpts[j]))]
+    assert pairs
+    for i, j in pairs:
+        ei = np.loadtxt(os.path.join(here, f"mp72x10_k{i}_eig.txt"))
+        ej = np.loadtxt(os.path.join(here, f"mp72x10_k{j}_eig.txt"))
+        assert np.abs(ei - ej).max() < 1e-11, (i, j)
+
+
 def test_teter_preconditioner_limits_and_shape():
     """The Teter-Payne-Allan ratio K(x) passes low-energy components unchanged to fourth order,
     K = 1 - (16/27) x^4 + (32/81) x^5 + O(x^6), and acts like the inverse kinetic energy at high
