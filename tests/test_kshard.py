@@ -38,6 +38,7 @@ def test_partition_balances_uneven_costs():
     loads = [sum(cost[k] for k in p) for p in parts]
     assert 9 in parts[0]                         # heaviest first, to rank 0
     assert abs(loads[0] - loads[1]) <= max(cost)
+    assert all(p == sorted(p) for p in parts)    # each rank's list ascending whatever the deal order
     with pytest.raises(ValueError):
         kshard.partition(3, 2, [1.0, 2.0])
 
@@ -73,6 +74,34 @@ def test_gather_reassembles_in_k_order_gloo(tmp_path, ws):
         for k in range(nk):
             assert np.array_equal(eig[k], 1000.0 * k + np.arange(M))
             assert np.all(res[k] == -k)
+
+
+def _dup_worker(rank, ws, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_0707_3405_gb300 import kshard as ks
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    local = {0: ([1.0], [0.0])}                   # both ranks claim k-point 0; k-point 1 is absent
+    if rank == 1:
+        local[1] = ([2.0], [0.0])
+    try:
+        ks.gather_results(local, 2, ws)
+        msg = ""
+    except RuntimeError as e:
+        msg = str(e)
+    with open(os.path.join(out_dir, f"d{rank}.txt"), "w") as f:
+        f.write(msg)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gather_rejects_a_kpoint_solved_twice_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_dup_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        assert "two ranks" in (tmp_path / f"d{r}.txt").read_text()
 
 
 def test_gather_rejects_missing_and_duplicate_kpoints():
