@@ -1,10 +1,11 @@
-"""pytest plugin that plants one mistake in the oracle before its pins run (CPU only; test
-infrastructure for tests/test_oracle_mutants.py).
+"""pytest plugin that plants one mistake in a Python module before the tests that pin it run
+(CPU only; test infrastructure for tests/test_oracle_mutants.py and tests/test_host_mutants.py).
 
 ``ORACLE_MUTANT`` holds a JSON list ``[module, old, new]``: the module's source is executed again
 in its own namespace with the single occurrence of ``old`` replaced by ``new``, and the oracle
 modules already imported are reloaded so that names they took from it see the planted version.
-Without the variable the plugin does nothing.
+Child processes the tests spawn import the module afresh and do not see the mistake.  Without
+the variable the plugin does nothing.
 """
 import importlib
 import json
