@@ -1,5 +1,6 @@
 """The host-side tests catch plausible mistakes in the host logic around the library: the
-k-point partition (Sec. 5.2) and the bench's rate, extrapolation and roofline arithmetic.  Each
+k-point partition (Sec. 5.2), the bench's rate, extrapolation and roofline arithmetic, and the
+binding's operand checks.  Each
 case plants one mistake with the plugin tests/_oracle_mutant.py and runs the in-process tests
 that pin that logic in a child process, which must end with a failed assertion."""
 import json
@@ -13,6 +14,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 KSHARD = ("tests/test_kshard.py", "partition")
 BENCH = ("tests/test_bench_host.py", "not reference_arm and not replica")
+BINDING = ("tests/test_binding_checks.py", "check")
 
 # (name, module, text, planted replacement, (test file, -k expression))
 HOST_MUTANTS = [
@@ -30,6 +32,15 @@ HOST_MUTANTS = [
      "nblk = w.nbands // w.block", BENCH),
     ("traffic_at_any_shape", "bench", 'TRAFFIC.get((dominant, tuple(d["shape"])), (None, None))',
      'TRAFFIC.get((dominant, (113081, 128, 256)), (None, None))', BENCH),
+    ("binding_skips_the_residency_check", "paper_0707_3405_gb300", "    for name, t, _, _ in ops:\n        if not t.is_cuda:",
+     "    for name, t, _, _ in ops[:0]:\n        if not t.is_cuda:", BINDING),
+    ("binding_skips_the_plane_wave_count", "paper_0707_3405_gb300", "if x.ndim != 2 or x.shape[1] != npw:",
+     "if x.ndim != 2:", BINDING),
+    ("binding_skips_the_band_count", "paper_0707_3405_gb300", "        if any(x.shape[0] < M for x in X):",
+     "        if False:", BINDING),
+    ("binding_skips_the_output_shape", "paper_0707_3405_gb300",
+     "elif not (isinstance(Y, np.ndarray) and Y.dtype == X.dtype and Y.shape == X.shape",
+     "elif not (isinstance(Y, np.ndarray) and Y.dtype == X.dtype", BINDING),
 ]
 
 
@@ -48,22 +59,23 @@ def _run(case):
 
 @pytest.fixture(scope="module")
 def runs():
-    cases = [KSHARD, BENCH] + HOST_MUTANTS
+    cases = [KSHARD, BENCH, BINDING] + HOST_MUTANTS
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         out = list(ex.map(_run, cases))
-    names = ["clean_kshard", "clean_bench"] + [m[0] for m in HOST_MUTANTS]
+    names = ["clean_kshard", "clean_bench", "clean_binding"] + [m[0] for m in HOST_MUTANTS]
     return dict(zip(names, out))
 
 
 def test_every_planted_text_occurs_once():
+    import importlib.util
+    sys.path.insert(0, ROOT)
     for name, mod, old, new, _ in HOST_MUTANTS:
-        path = os.path.join(ROOT, *mod.split(".")) + ".py"
-        with open(path) as f:
+        with open(importlib.util.find_spec(mod).origin) as f:
             assert f.read().count(old) == 1, name
 
 
 def test_host_tests_pass_as_they_are(runs):
-    for key in ("clean_kshard", "clean_bench"):
+    for key in ("clean_kshard", "clean_bench", "clean_binding"):
         rc, out = runs[key]
         assert rc == 0, out[-3000:]
 
