@@ -6,8 +6,9 @@ mistake here is the mathematics the pins check (closed forms, the direct DFT, de
 diagonalisation, Courant-Fischer bounds, invariances, brute force).
 
 Mistakes that change only how fast an iteration converges, not what it converges to (the sign
-of the PCG conjugacy ratio, the choice of half set, the dropping threshold), are not listed:
-the pins fix results, not speed.
+of the PCG conjugacy ratio, the choice of half set, the dropping threshold), and rewrites that
+compute the same thing (a wider enumeration margin around the sphere, another valid round-robin
+order), are not listed: the pins fix results, not speed or form.
 """
 import json
 import os
@@ -54,6 +55,7 @@ MUTANTS = [
     # Jacobi rotations
     ("jacobi_wrong_rotation_sign", "oracle.jacobi", "u_qp, u_qq = -s * np.conj(ph)", "u_qp, u_qq = s * np.conj(ph)"),
     ("jacobi_conjugated_phase", "oracle.jacobi", "ph = np.where(act, b / np.where", "ph = np.where(act, np.conj(b) / np.where"),
+    ("jacobi_stop_test_inverted", "oracle.jacobi", "if off <= tol * scale:", "if off >= tol * scale:"),
     # block LOBPCG (Algorithm 1, Sec. 3.2) and the Teter ratio
     ("teter_wrong_power", "oracle.lobpcg", "p / (p + 16.0 * x ** 4)", "p / (p + 16.0 * x ** 3)"),
     ("teter_wrong_coefficient", "oracle.lobpcg", "12.0 + 8.0 * x", "12.0 + 6.0 * x"),
@@ -62,6 +64,7 @@ MUTANTS = [
     ("gram_unconjugated", "oracle.lobpcg", "A = Z.conj().T @ HZ", "A = Z.T @ HZ"),
     ("gram_symmetrised_without_conjugate", "oracle.lobpcg", "S = 0.5 * (S + S.conj().T)", "S = 0.5 * (S + S.T)"),
     ("ritz_vectors_miss_the_scaling", "oracle.lobpcg", "C = d[:, None] * (B @ Q[:, :m])", "C = B @ Q[:, :m]"),
+    ("rr_basis_not_orthonormalised", "oracle.lobpcg", "B = U[:, keep] / np.sqrt(mu[keep])[None, :]", "B = U[:, keep]"),
     ("block_not_constrained", "oracle.lobpcg", "X = orthonormalize(project_out(Y, X))", "X = orthonormalize(X)"),
     ("direction_not_constrained", "oracle.lobpcg", "W = project_out(Y, W)", "W = W"),
     ("coefficients_swapped", "oracle.lobpcg", "Cx, Cw = C[:m], C[m:2 * m]", "Cx, Cw = C[m:2 * m], C[:m]"),
@@ -86,6 +89,8 @@ MUTANTS = [
     ("real_basis_wrong_norm", "oracle.gamma", "s = 1.0 / np.sqrt(2.0)", "s = 0.5"),
     ("from_half_unconjugated", "oracle.gamma", "c[minus] = np.conj(h[1:])", "c[minus] = h[1:]"),
     ("half_inner_drops_the_pair_factor", "oracle.gamma", "2.0 * np.real(ha[1:]", "np.real(ha[1:]"),
+    ("half_inner_drops_g0", "oracle.gamma", "return np.outer(ha[0].real, hb[0].real) + 2.0",
+     "return 0.0 * np.outer(ha[0].real, hb[0].real) + 2.0"),
     ("real_H_unconjugated", "oracle.gamma", "y = self.U.conj().T @ self.H.apply", "y = self.U.T @ self.H.apply"),
     ("to_half_takes_the_other_half", "oracle.gamma", "c[zero:zero + 1], c[plus]]", "c[zero:zero + 1], c[minus]]"),
     ("real_kinetic_unconjugated", "oracle.gamma", "np.einsum(\"gi,g,gi->i\", self.U.conj(), H.T, self.U)",
