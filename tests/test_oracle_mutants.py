@@ -84,7 +84,11 @@ MUTANTS = [
     ("density_drops_occupation", "oracle.density", "rho += float(f[b]) * (", "rho += ("),
     ("density_wrong_modulus", "oracle.density", "psi.real ** 2 + psi.imag ** 2", "psi.real ** 2 - psi.imag ** 2"),
     ("electron_count_wrong_cell", "oracle.density", "* a ** 3 / N ** 3", "* a ** 3 / N ** 2"),
+    ("density_fft_route_wrong_volume", "oracle.density", "return rho / a ** 3", "return rho / a ** 2"),
+    ("density_fft_route_conjugated_band", "oracle.density", "box[idx] = C[:, b]", "box[idx] = np.conj(C[:, b])"),
     # Gamma-point real form
+    ("half_set_misses_the_z_axis", "oracle.gamma", "if x > 0 or (x == 0 and (y > 0 or (y == 0 and z > 0))):",
+     "if x > 0 or (x == 0 and y > 0):"),
     ("real_basis_wrong_sign", "oracle.gamma", "U[minus, 1 + h + cols] = -1j * s", "U[minus, 1 + h + cols] = 1j * s"),
     ("real_basis_wrong_norm", "oracle.gamma", "s = 1.0 / np.sqrt(2.0)", "s = 0.5"),
     ("from_half_unconjugated", "oracle.gamma", "c[minus] = np.conj(h[1:])", "c[minus] = h[1:]"),
@@ -96,6 +100,8 @@ MUTANTS = [
     ("real_kinetic_unconjugated", "oracle.gamma", "np.einsum(\"gi,g,gi->i\", self.U.conj(), H.T, self.U)",
      "np.einsum(\"gi,g,gi->i\", self.U, H.T, self.U)"),
     # band-by-band PCG (Sec. 3.3)
+    ("line_angle_not_halved", "oracle.pcg", "theta = 0.5 * np.arctan2(-2.0 * C, B - A)", "theta = np.arctan2(-2.0 * C, B - A)"),
+    ("pcg_band_not_normalised", "oracle.pcg", "x = x / np.linalg.norm(x)\n    hx = H.apply(x)", "hx = H.apply(x)"),
     ("line_minimum_finds_the_maximum", "oracle.pcg", "np.arctan2(-2.0 * C, B - A)", "np.arctan2(2.0 * C, B - A)"),
     ("line_energy_drops_the_factor", "oracle.pcg", "2.0 * C * s * c", "C * s * c"),
     ("line_uses_the_wrong_diagonal", "oracle.pcg", "B = float(np.real(np.vdot(dh, hd)))", "B = float(np.real(np.vdot(dh, dh)))"),
